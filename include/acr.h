@@ -1,0 +1,185 @@
+/*
+ * acr.h -- C ABI of the GB300 accelerated-cyclic-reduction (ACR) library.
+ *
+ * The library builds and applies the ACR preconditioner of Chavez,
+ * Turkiyyah, Zampini and Keyes (JCAM 2017) for the block-tridiagonal
+ * systems that 7-point discretisations of 3D elliptic PDEs produce
+ * (Sec. 4.1: one block row per z-plane, Eq. poissonEquation, Eq. codi),
+ * with every plane block held as an H-matrix (Sec. 3, Sec. 4.2), and runs
+ * the FP64 Krylov iteration it preconditions (Sec. 5.3 CG, Sec. 7 GMRES).
+ *
+ * Conventions shared by every entry point:
+ *  - Grid: nx * ny * nz interior points of the unit cube, spacing
+ *    h = 1/(n+1) per axis (n = nx = ny = nz in this version), Dirichlet 0
+ *    boundary.  Unknown p = ix + nx*(iy + ny*iz): x fastest, z-planes are
+ *    the CR block rows.
+ *  - Stencil: seven FP64 arrays of N = nx*ny*nz entries stored back to back
+ *    in one device buffer of 7*N doubles, in the order
+ *    c, w, e, s, n, b, t (centre, x-1, x+1, y-1, y+1, z-1, z+1).  A
+ *    coefficient that points outside the domain is ignored.
+ *  - All array pointers are DEVICE pointers unless a name ends in _host.
+ *    The caller owns every pointer it passes; the library never frees or
+ *    keeps them past the call, except the handle which the library owns.
+ *  - Calls are ordered on the given stream (0 = legacy default stream)
+ *    and return after queuing their work, except where noted (setup
+ *    synchronises the stream; Krylov reads one scalar back per iteration).
+ *  - Every call returns an acr_status.  On error nothing is leaked, output
+ *    arrays hold unspecified values and a setup returns *out == NULL.
+ *  - A handle is not thread-safe: use it from one host thread and one
+ *    stream at a time.
+ *  - There is no CPU fallback: without a CUDA device every compute call
+ *    returns ACR_ERR_CUDA.
+ */
+#ifndef ACR_H
+#define ACR_H
+
+#include <stdint.h>
+#include <cuda_runtime.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  ACR_OK = 0,
+  ACR_ERR_INVALID_ARG = 1,   /* bad size, NULL pointer, eps/eta/leaf out of range, non-finite input */
+  ACR_ERR_OOM = 2,           /* device allocation failed */
+  ACR_ERR_CUDA = 3,          /* a CUDA call failed (no device, launch error, ...) */
+  ACR_ERR_BREAKDOWN = 4,     /* zero pivot in a dense leaf inverse, or Krylov breakdown */
+  ACR_ERR_RANK_CAP = 5,      /* a truncated block needed more than the rank cap */
+  ACR_ERR_NOT_CONVERGED = 6, /* Krylov hit maxit above rtol */
+  ACR_ERR_TIMEOUT = 7,       /* a bounded device wait ran out */
+  ACR_ERR_UNSUPPORTED = 8    /* valid request this build does not handle (e.g. unbalanced cluster tree) */
+} acr_status;
+
+/* Arithmetic form of the H-matrix factors and of the setup / apply
+ * arithmetic.  FP64: everything in double.  FP32: factors stored and
+ * multiplied in float with float accumulation.  In every form the dense
+ * leaf inverses, the small recompression cores and the Krylov iteration are
+ * FP64. */
+typedef enum { ACR_FP64 = 0, ACR_FP32 = 1 } acr_precision;
+
+typedef enum { ACR_PCG = 0, ACR_GMRES = 1 } acr_krylov;
+
+typedef struct {
+  int32_t nx, ny, nz;   /* interior points per axis; this version needs nx == ny == nz */
+} acr_grid;
+
+/* Preconditioner parameters (Sec. 4.3): H_eps, the admissibility eta of
+ * Eq. (admis) and the leaf size n_min; plus the storage form and the rank
+ * cap of the device factors (blocks whose truncated rank exceeds it make
+ * the setup fail with ACR_ERR_RANK_CAP). */
+typedef struct {
+  double eps;            /* blockwise relative truncation threshold, 0 < eps < 1 */
+  double eta;            /* admissibility parameter, > 0 */
+  int32_t leaf;          /* n_min: clusters with at most this many points are leaves */
+  int32_t precision;     /* acr_precision */
+  int32_t rank_cap;      /* 1..64; 0 selects the default (32) */
+  int32_t reserved;
+} acr_options;
+
+typedef struct {
+  int32_t levels;            /* CR levels, ceil(log2 nz) */
+  int32_t max_rank;          /* largest rank over all stored low-rank blocks */
+  double avg_rank;           /* mean rank of stored low-rank blocks */
+  int64_t factor_bytes;      /* bytes of stored factors (dense leaves + U,V at their ranks) */
+  int64_t factor_capacity_bytes; /* bytes allocated for factors (rank_cap padding) */
+  int32_t n_dense_leaves;    /* per plane H-matrix */
+  int32_t n_lowrank_leaves;  /* per plane H-matrix */
+  double setup_ms;           /* device time of the last setup (CUDA events) */
+  double structure_ms;       /* host time spent building the block structure and plans */
+} acr_setup_info;
+
+typedef struct {
+  int32_t iterations;        /* Krylov iterations performed */
+  int32_t converged;         /* 1 if the true relative residual reached rtol */
+  double rel_residual;       /* final ||f - A u||_2 / ||f||_2, FP64, computed with the 7-point SpMV */
+  double solve_ms;           /* device time of the solve */
+} acr_solve_info;
+
+typedef struct acr_handle acr_handle;
+
+/* a1, Sec. 6 Eq. (poissonEquation): stencil of -div(kappa grad u), face
+ * coefficient = harmonic mean of the two nodal kappas (the node's own kappa
+ * on a boundary face), scaled by 1/h^2.  kappa: N doubles (> 0, finite).
+ * coef: 7*N doubles written in the stencil layout above.  Errors:
+ * INVALID_ARG for NULL pointers or a bad grid. */
+acr_status acr_stencil_poisson(const acr_grid* grid, const double* kappa, double* coef,
+                               cudaStream_t stream);
+
+/* a1, Sec. 7 Eq. (codi): stencil of -Lap u + beta . grad u with first-order
+ * upwinding (backward difference where beta_d > 0, forward where < 0).
+ * beta: 3*N doubles (beta_x, beta_y, beta_z arrays back to back). */
+acr_status acr_stencil_codi(const acr_grid* grid, const double* beta, double* coef,
+                            cudaStream_t stream);
+
+/* y = A x for the 7-point operator (FP64), x and y N doubles each, nrhs
+ * vectors back to back. */
+acr_status acr_spmv(const acr_grid* grid, const double* coef, const double* x, double* y,
+                    int32_t nrhs, cudaStream_t stream);
+
+/* a2-a8, Sec. 4.1-4.3: build the ACR factorisation of the operator given
+ * by coef (7*N doubles, not modified, not retained).  Runs the cyclic
+ * reduction levels with every plane block in H-format: H-inverse of the
+ * eliminated (red) planes, Schur updates of the remaining (black) planes,
+ * truncation of every low-rank block to eps relative accuracy.  Synchronises
+ * `stream` before returning.  *out receives a new handle owning all factor
+ * memory (release with acr_destroy).  Errors: INVALID_ARG, UNSUPPORTED,
+ * OOM, CUDA, BREAKDOWN, RANK_CAP; *out is NULL then. */
+acr_status acr_setup(const acr_grid* grid, const double* coef, const acr_options* opt,
+                     cudaStream_t stream, acr_handle** out);
+
+/* a9-a10, Sec. 4.1 substitution: z = M^{-1} r, M the ACR factorisation;
+ * forward then backward sweep of batched H-matrix-vector products.  r, z:
+ * nrhs * N doubles (natural ordering); r is not modified; r == z is
+ * allowed.  No host synchronisation. */
+acr_status acr_apply(acr_handle* h, const double* r, double* z, int32_t nrhs,
+                     cudaStream_t stream);
+
+/* z = M^{-T} r: the transposed substitution (sweeps in reverse order with
+ * transposed H-matrix-vector products), for adjoint solves. */
+acr_status acr_apply_transpose(acr_handle* h, const double* r, double* z, int32_t nrhs,
+                               cudaStream_t stream);
+
+/* a11, Sec. 5.3 and Sec. 7: solve A u = f to ||f - A u||_2 <= rtol ||f||_2
+ * with FP64 preconditioned CG (flexible, Polak-Ribiere) or GMRES(restart)
+ * with right preconditioning.  coef: the 7-point operator (7*N doubles,
+ * normally the one the handle was built from).  u holds x0 on entry and
+ * the solution on exit.  info (host pointer, may be NULL) receives the
+ * iteration count and final true residual.  nrhs must be 1 in this
+ * version.  Errors: NOT_CONVERGED after maxit (u holds the last iterate),
+ * BREAKDOWN. */
+acr_status acr_krylov_solve(acr_handle* h, const double* coef, int32_t method, int32_t restart,
+                            double rtol, int32_t maxit, const double* f, double* u,
+                            int32_t nrhs, acr_solve_info* info, cudaStream_t stream);
+
+/* Same Krylov iteration with no preconditioner (h not needed): the
+ * reference for iteration counts. */
+acr_status acr_krylov_solve_plain(const acr_grid* grid, const double* coef, int32_t method,
+                                  int32_t restart, double rtol, int32_t maxit,
+                                  const double* f, double* u, acr_solve_info* info,
+                                  cudaStream_t stream);
+
+/* Setup statistics of a handle (host struct). */
+acr_status acr_get_setup_info(const acr_handle* h, acr_setup_info* info);
+
+/* Host-only introspection of the plane block structure used for (n, eta,
+ * leaf) (Sec. 3.1): counts[0..5] = {clusters, dense leaves, low-rank
+ * leaves, sum of low-rank rows, sum of low-rank cols, tree depth}.  If
+ * `leaves_host` is not NULL it receives 5 int32 per leaf block (row begin,
+ * row size, col begin, col size, kind 0 = dense / 1 = low rank) in cluster
+ * ordering, and `perm_host` (if not NULL) the n*n cluster-order
+ * permutation.  Makes no CUDA call. */
+acr_status acr_structure_query(int32_t n, double eta, int32_t leaf, int64_t* counts,
+                               int32_t* leaves_host, int32_t* perm_host);
+
+/* Release a handle and all its device memory (NULL is a no-op). */
+void acr_destroy(acr_handle* h);
+
+/* Static string naming a status. */
+const char* acr_status_string(acr_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ACR_H */

@@ -1,0 +1,13 @@
+"""GB300 (sm_103a) accelerated cyclic reduction (ACR) preconditioner.
+
+The compute path is the C-ABI library ``_lib/libacr.so`` (hand-written CUDA,
+see ``include/acr.h``); :mod:`.acr` is a thin ctypes binding with the same
+entry-point names.  Importing this package does not load the library; the
+first call does, and fails loudly if it is missing.
+"""
+from .acr import (  # noqa: F401
+    ACR_FP64, ACR_FP32, ACR_PCG, ACR_GMRES, AcrError, Grid, Options, SetupInfo,
+    SolveInfo, load_library, acr_stencil_poisson, acr_stencil_codi, acr_spmv, acr_setup,
+    acr_apply, acr_apply_transpose, acr_krylov_solve, acr_krylov_solve_plain,
+    acr_get_setup_info, acr_structure_query, acr_destroy, acr_status_string, Handle,
+)

@@ -1,0 +1,238 @@
+"""ctypes binding of include/acr.h (argument marshalling only).
+
+Every function has the name of the C entry point it wraps.  Array arguments
+are CUDA ``torch.Tensor`` objects of dtype float64 (contiguous); their device
+pointers and the current CUDA stream are passed straight to the library.  A
+non-zero status raises :class:`AcrError`.  There is no CPU fallback: if the
+library is missing or no CUDA device is present the call raises.
+"""
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libacr.so")
+
+ACR_FP64, ACR_FP32 = 0, 1
+ACR_PCG, ACR_GMRES = 0, 1
+
+_STATUS = {0: "ok", 1: "invalid argument", 2: "out of device memory", 3: "CUDA error",
+           4: "breakdown", 5: "rank cap exceeded", 6: "not converged", 7: "timeout",
+           8: "unsupported configuration"}
+
+
+class AcrError(RuntimeError):
+    def __init__(self, status, where):
+        super().__init__("%s: %s (status %d)" % (where, _STATUS.get(status, "?"), status))
+        self.status = status
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32)]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("eps", ctypes.c_double), ("eta", ctypes.c_double), ("leaf", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("rank_cap", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class SetupInfo(ctypes.Structure):
+    _fields_ = [("levels", ctypes.c_int32), ("max_rank", ctypes.c_int32),
+                ("avg_rank", ctypes.c_double), ("factor_bytes", ctypes.c_int64),
+                ("factor_capacity_bytes", ctypes.c_int64), ("n_dense_leaves", ctypes.c_int32),
+                ("n_lowrank_leaves", ctypes.c_int32), ("setup_ms", ctypes.c_double),
+                ("structure_ms", ctypes.c_double)]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int32), ("converged", ctypes.c_int32),
+                ("rel_residual", ctypes.c_double), ("solve_ms", ctypes.c_double)]
+
+
+_lib = None
+_P = ctypes.c_void_p
+
+
+def load_library(path=LIB_PATH):
+    """Load libacr.so once; raises if it was not built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError("libacr.so not built (run __graft_entry__.build()): %s" % path)
+    lib = ctypes.CDLL(path)
+    I32, F64, I64p = ctypes.c_int32, ctypes.c_double, ctypes.POINTER(ctypes.c_int64)
+    sig = {
+        "acr_stencil_poisson": [ctypes.POINTER(Grid), _P, _P, _P],
+        "acr_stencil_codi": [ctypes.POINTER(Grid), _P, _P, _P],
+        "acr_spmv": [ctypes.POINTER(Grid), _P, _P, _P, I32, _P],
+        "acr_setup": [ctypes.POINTER(Grid), _P, ctypes.POINTER(Options), _P,
+                      ctypes.POINTER(_P)],
+        "acr_apply": [_P, _P, _P, I32, _P],
+        "acr_apply_transpose": [_P, _P, _P, I32, _P],
+        "acr_krylov_solve": [_P, _P, I32, I32, F64, I32, _P, _P, I32,
+                             ctypes.POINTER(SolveInfo), _P],
+        "acr_krylov_solve_plain": [ctypes.POINTER(Grid), _P, I32, I32, F64, I32, _P, _P,
+                                   ctypes.POINTER(SolveInfo), _P],
+        "acr_get_setup_info": [_P, ctypes.POINTER(SetupInfo)],
+        "acr_structure_query": [I32, F64, I32, I64p, _P, _P],
+    }
+    for name, args in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_int
+    lib.acr_destroy.argtypes = [_P]
+    lib.acr_destroy.restype = None
+    lib.acr_status_string.argtypes = [ctypes.c_int]
+    lib.acr_status_string.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def _check(st, where):
+    if st != 0:
+        raise AcrError(st, where)
+
+
+def _dev(t, numel=None, name="array"):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("%s must be a CUDA tensor" % name)
+    if t.dtype != torch.float64 or not t.is_contiguous():
+        raise TypeError("%s must be contiguous float64" % name)
+    if numel is not None and t.numel() < numel:
+        raise ValueError("%s has %d entries, needs %d" % (name, t.numel(), numel))
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _grid(n):
+    return Grid(n, n, n)
+
+
+def acr_stencil_poisson(n, kappa, coef, stream=None):
+    N = n ** 3
+    _check(load_library().acr_stencil_poisson(ctypes.byref(_grid(n)), _dev(kappa, N, "kappa"),
+                                               _dev(coef, 7 * N, "coef"), _stream(stream)),
+           "acr_stencil_poisson")
+
+
+def acr_stencil_codi(n, beta, coef, stream=None):
+    N = n ** 3
+    _check(load_library().acr_stencil_codi(ctypes.byref(_grid(n)), _dev(beta, 3 * N, "beta"),
+                                            _dev(coef, 7 * N, "coef"), _stream(stream)),
+           "acr_stencil_codi")
+
+
+def acr_spmv(n, coef, x, y, nrhs=1, stream=None):
+    N = n ** 3
+    _check(load_library().acr_spmv(ctypes.byref(_grid(n)), _dev(coef, 7 * N, "coef"),
+                                    _dev(x, nrhs * N, "x"), _dev(y, nrhs * N, "y"), nrhs,
+                                    _stream(stream)), "acr_spmv")
+
+
+def acr_setup(n, coef, eps, eta, leaf, precision=ACR_FP64, rank_cap=0, stream=None):
+    """Returns an opaque handle (int); release it with acr_destroy."""
+    N = n ** 3
+    opt = Options(eps, eta, leaf, precision, rank_cap, 0)
+    h = _P()
+    _check(load_library().acr_setup(ctypes.byref(_grid(n)), _dev(coef, 7 * N, "coef"),
+                                     ctypes.byref(opt), _stream(stream), ctypes.byref(h)),
+           "acr_setup")
+    return h.value
+
+
+def acr_apply(handle, r, z, nrhs=1, stream=None):
+    _check(load_library().acr_apply(_P(handle), _dev(r, None, "r"), _dev(z, None, "z"), nrhs,
+                                     _stream(stream)), "acr_apply")
+
+
+def acr_apply_transpose(handle, r, z, nrhs=1, stream=None):
+    _check(load_library().acr_apply_transpose(_P(handle), _dev(r, None, "r"), _dev(z, None, "z"),
+                                               nrhs, _stream(stream)), "acr_apply_transpose")
+
+
+def acr_krylov_solve(handle, coef, method, restart, rtol, maxit, f, u, stream=None,
+                     check=True):
+    info = SolveInfo()
+    st = load_library().acr_krylov_solve(_P(handle), _dev(coef, None, "coef"), method, restart,
+                                         rtol, maxit, _dev(f, None, "f"), _dev(u, None, "u"), 1,
+                                         ctypes.byref(info), _stream(stream))
+    if check:
+        _check(st, "acr_krylov_solve")
+    return info, st
+
+
+def acr_krylov_solve_plain(n, coef, method, restart, rtol, maxit, f, u, stream=None, check=True):
+    info = SolveInfo()
+    st = load_library().acr_krylov_solve_plain(ctypes.byref(_grid(n)), _dev(coef, None, "coef"),
+                                               method, restart, rtol, maxit, _dev(f, None, "f"),
+                                               _dev(u, None, "u"), ctypes.byref(info),
+                                               _stream(stream))
+    if check:
+        _check(st, "acr_krylov_solve_plain")
+    return info, st
+
+
+def acr_get_setup_info(handle):
+    info = SetupInfo()
+    _check(load_library().acr_get_setup_info(_P(handle), ctypes.byref(info)), "acr_get_setup_info")
+    return info
+
+
+def acr_structure_query(n, eta, leaf, with_leaves=False):
+    """Host-only: (counts[6], leaves (k, 5) int32 or None, perm or None)."""
+    import numpy as np
+    lib = load_library()
+    counts = (ctypes.c_int64 * 6)()
+    _check(lib.acr_structure_query(n, eta, leaf, counts, None, None), "acr_structure_query")
+    c = [int(v) for v in counts]
+    if not with_leaves:
+        return c, None, None
+    leaves = np.zeros((c[1] + c[2], 5), dtype=np.int32)
+    perm = np.zeros(n * n, dtype=np.int32)
+    _check(lib.acr_structure_query(n, eta, leaf, counts, leaves.ctypes.data_as(_P),
+                                   perm.ctypes.data_as(_P)), "acr_structure_query")
+    return c, leaves, perm
+
+
+def acr_destroy(handle):
+    if handle:
+        load_library().acr_destroy(_P(handle))
+
+
+def acr_status_string(status):
+    return load_library().acr_status_string(status).decode()
+
+
+class Handle:
+    """Owning wrapper of an acr_setup handle."""
+
+    def __init__(self, n, coef, eps, eta, leaf, precision=ACR_FP64, rank_cap=0, stream=None):
+        self.n = n
+        self.h = acr_setup(n, coef, eps, eta, leaf, precision, rank_cap, stream)
+
+    def apply(self, r, z, stream=None):
+        acr_apply(self.h, r, z, 1, stream)
+
+    def apply_transpose(self, r, z, stream=None):
+        acr_apply_transpose(self.h, r, z, 1, stream)
+
+    def info(self):
+        return acr_get_setup_info(self.h)
+
+    def close(self):
+        if self.h:
+            acr_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,1229 @@
+// ACR engine: setup orchestration (Sec. 4.1-4.3), the preconditioner apply
+// program (Sec. 4.1 substitution) and the FP64 Krylov drivers (Sec. 5.3,
+// Sec. 7), behind the C ABI of include/acr.h.
+//
+// Data layout in HBM: every plane block is one H-matrix on the shared plane
+// structure -- dense leaves (lsz x lsz, column-major, contiguous), then the
+// low-rank factors U (sum of leaf rows x kc) and V (sum of leaf cols x kc),
+// column-major per leaf with kc = rank capacity, and one int rank per
+// low-rank leaf.  Vectors inside the apply are FP64 in cluster order, one
+// plane after another.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "acr.h"
+#include "acr_internal.h"
+
+namespace acr {
+
+namespace {
+
+struct AcrError {
+  int status;
+  std::string msg;
+};
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+void* dmalloc(size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    throw AcrError{S_OOM, "cudaMalloc failed"};
+  }
+  return p;
+}
+
+template <typename V>
+void* upload(const std::vector<V>& v, std::vector<void*>& owned) {
+  void* p = dmalloc(std::max<size_t>(v.size() * sizeof(V), 16));
+  if (!v.empty()) ACR_CUDA(cudaMemcpy(p, v.data(), v.size() * sizeof(V), cudaMemcpyHostToDevice));
+  owned.push_back(p);
+  return p;
+}
+
+// pinned host -> device ring for per-launch pointer tables
+struct TableRing {
+  char* host = nullptr;
+  char* dev = nullptr;
+  size_t cap = 0, off = 0;
+  void init(size_t c) {
+    cap = c;
+    ACR_CUDA(cudaMallocHost(&host, cap));
+    dev = (char*)dmalloc(cap);
+  }
+  void release() {
+    if (host) cudaFreeHost(host);
+    if (dev) cudaFree(dev);
+    host = dev = nullptr;
+  }
+  void* push(const void* data, size_t bytes, cudaStream_t st) {
+    size_t b = (bytes + 255) & ~size_t(255);
+    if (b > cap) throw AcrError{S_OOM, "pointer table larger than staging ring"};
+    if (off + b > cap) {
+      ACR_CUDA(cudaStreamSynchronize(st));
+      off = 0;
+    }
+    std::memcpy(host + off, data, bytes);
+    ACR_CUDA(cudaMemcpyAsync(dev + off, host + off, bytes, cudaMemcpyHostToDevice, st));
+    void* r = dev + off;
+    off += b;
+    return r;
+  }
+};
+
+}  // namespace
+
+struct HM {
+  void* dense = nullptr;
+  void* U = nullptr;
+  void* V = nullptr;
+  int* rank = nullptr;
+};
+
+class EngineBase {
+ public:
+  virtual ~EngineBase() {}
+  virtual void setup(const double* coef, cudaStream_t st) = 0;
+  virtual void apply(const double* r, double* z, bool trans, cudaStream_t st) = 0;
+  acr_setup_info info{};
+  int n = 0;
+  int64_t N = 0;
+};
+
+template <typename T>
+class Engine : public EngineBase {
+ public:
+  Engine(int n_, double eps_, double eta_, int leaf_, int kc_) : eps(eps_), eta(eta_),
+      leaf(leaf_), kc(kc_) {
+    n = n_;
+    n2 = n * n;
+    N = (int64_t)n2 * n;
+  }
+  ~Engine() override { release(); }
+
+  void setup(const double* coef, cudaStream_t st) override;
+  void apply(const double* r, double* z, bool trans, cudaStream_t st) override;
+
+ private:
+  double eps, eta;
+  int leaf, kc;
+  int n2 = 0;
+  Structure S;
+  StructDev sd;
+  MatvecPlan mvp;
+  MatvecDev mvd{};
+  PlanParams pp{};
+  std::map<std::vector<int>, std::unique_ptr<Plan>> plans;
+  std::vector<void*> owned;          // structure / plan / table arrays
+  std::vector<HM> D;                 // plane blocks (X in place after inversion)
+  std::vector<HM> heap;              // every H-matrix allocated (for release)
+  double* Ld = nullptr;              // level-0 couplings, cluster order
+  double* Ud = nullptr;
+  struct Level {
+    int s;
+    std::vector<int> red, black;
+    std::vector<HM> L, U;            // per plane index (n entries), r >= 1
+  };
+  std::vector<Level> levels;
+  TableRing ring;
+  void* scratch = nullptr;
+  size_t scratch_bytes = 0;
+  int* scratch_ranks = nullptr;
+  size_t scratch_rank_cnt = 0;
+  size_t scratch_budget = 0;
+  double* d_coefs = nullptr;
+  int* d_err = nullptr;
+  int* d_planes_all = nullptr;
+  // apply work
+  double *Fv = nullptr, *Gv = nullptr, *Uv = nullptr, *Tv = nullptr, *tvscr = nullptr;
+  struct ApplyStep {
+    int kind;                        // 0 hmatvec, 1 diag update, 2 copy
+    int P;
+    bool trans;
+    double alpha, beta, sgn;
+    void** tabs;                     // device table block
+  };
+  std::vector<ApplyStep> fwd_steps, bwd_steps, fwdT_steps, bwdT_steps;
+  int maxP = 1;
+
+  HM alloc_hm() {
+    HM h;
+    size_t dn = (size_t)S.dleaf.size() * S.lsz * S.lsz;
+    size_t un = (size_t)S.sumM * kc, vn = (size_t)S.sumN * kc;
+    h.dense = dmalloc(std::max<size_t>(dn, 1) * sizeof(T));
+    h.U = dmalloc(std::max<size_t>(un, 1) * sizeof(T));
+    h.V = dmalloc(std::max<size_t>(vn, 1) * sizeof(T));
+    h.rank = (int*)dmalloc(std::max<size_t>(S.lleaf.size(), 1) * sizeof(int));
+    ACR_CUDA(cudaMemset(h.rank, 0, std::max<size_t>(S.lleaf.size(), 1) * sizeof(int)));
+    heap.push_back(h);
+    return h;
+  }
+  void free_hm(HM& h) {
+    for (auto it = heap.begin(); it != heap.end(); ++it)
+      if (it->dense == h.dense) { heap.erase(it); break; }
+    cudaFree(h.dense); cudaFree(h.U); cudaFree(h.V); cudaFree(h.rank);
+    h = HM();
+  }
+  void release() {
+    for (HM& h : heap) { cudaFree(h.dense); cudaFree(h.U); cudaFree(h.V); cudaFree(h.rank); }
+    heap.clear();
+    for (void* p : owned) cudaFree(p);
+    owned.clear();
+    for (auto& kv : plans) {
+      cudaFree(kv.second->d_groups); cudaFree(kv.second->d_items); cudaFree(kv.second->d_targets);
+    }
+    plans.clear();
+    if (scratch) cudaFree(scratch);
+    if (scratch_ranks) cudaFree(scratch_ranks);
+    scratch = nullptr; scratch_ranks = nullptr;
+    ring.release();
+  }
+
+  // ------------------------------------------------------------ plans
+  Plan& get_plan(const OpDesc& op) {
+    std::vector<int> key{op.c_node, op.c_role, op.alpha, op.nroles, (int)op.prods.size()};
+    for (auto& p : op.prods) {
+      key.push_back(p.a_node); key.push_back(p.b_node); key.push_back(p.a_role);
+      key.push_back(p.b_role); key.push_back(p.coef);
+    }
+    key.push_back(-7);
+    for (auto& a : op.adds) { key.push_back(a.m_role); key.push_back(a.coef); }
+    auto it = plans.find(key);
+    if (it != plans.end()) return *it->second;
+    auto pl = std::make_unique<Plan>();
+    build_plan(S, op, pp, *pl);
+    pl->d_groups = dmalloc(std::max<size_t>(pl->groups.size(), 1) * sizeof(GGroup));
+    pl->d_items = dmalloc(std::max<size_t>(pl->items.size(), 1) * sizeof(GItem));
+    pl->d_targets = dmalloc(std::max<size_t>(pl->targets.size(), 1) * sizeof(TInfo));
+    if (!pl->groups.empty())
+      ACR_CUDA(cudaMemcpy(pl->d_groups, pl->groups.data(), pl->groups.size() * sizeof(GGroup),
+                          cudaMemcpyHostToDevice));
+    if (!pl->items.empty())
+      ACR_CUDA(cudaMemcpy(pl->d_items, pl->items.data(), pl->items.size() * sizeof(GItem),
+                          cudaMemcpyHostToDevice));
+    if (!pl->targets.empty())
+      ACR_CUDA(cudaMemcpy(pl->d_targets, pl->targets.data(), pl->targets.size() * sizeof(TInfo),
+                          cudaMemcpyHostToDevice));
+    Plan& ref = *pl;
+    plans[key] = std::move(pl);
+    return ref;
+  }
+
+  void ensure_scratch(size_t bytes, size_t ranks, cudaStream_t st) {
+    if (bytes > scratch_bytes) {
+      ACR_CUDA(cudaStreamSynchronize(st));
+      if (scratch) cudaFree(scratch);
+      scratch = nullptr;
+      scratch = dmalloc(bytes);
+      scratch_bytes = bytes;
+    }
+    if (ranks > scratch_rank_cnt) {
+      ACR_CUDA(cudaStreamSynchronize(st));
+      if (scratch_ranks) cudaFree(scratch_ranks);
+      scratch_ranks = nullptr;
+      scratch_ranks = (int*)dmalloc(ranks * sizeof(int));
+      scratch_rank_cnt = ranks;
+    }
+  }
+
+  // roles[r][p]: H-matrix of role r for plane p of the batch
+  void run_op(const OpDesc& op, const std::vector<std::vector<HM>>& roles, int P,
+              cudaStream_t st) {
+    if (P <= 0) return;
+    Plan& pl = get_plan(op);
+    const int nr = op.nroles;
+    size_t per_plane = std::max<size_t>((size_t)pl.scratch * sizeof(T), 256);
+    int Pc = (int)std::max<size_t>(1, std::min<size_t>(P, scratch_budget / per_plane));
+    ensure_scratch(per_plane * Pc, (size_t)std::max(pl.scratch_ranks, 1) * Pc, st);
+    std::vector<void*> tab((3 * nr + 1) * (size_t)Pc);
+    std::vector<void*> rtab((nr + 1) * (size_t)Pc);
+    for (int c0 = 0; c0 < P; c0 += Pc) {
+      const int pc = std::min(Pc, P - c0);
+      for (int r = 0; r < nr; ++r)
+        for (int p = 0; p < pc; ++p) {
+          const HM& h = roles[r][c0 + p];
+          tab[(3 * r + 0) * pc + p] = h.dense;
+          tab[(3 * r + 1) * pc + p] = h.U;
+          tab[(3 * r + 2) * pc + p] = h.V;
+          rtab[r * pc + p] = h.rank;
+        }
+      for (int p = 0; p < pc; ++p) {
+        tab[(3 * nr) * pc + p] = (char*)scratch + (size_t)p * per_plane;
+        rtab[nr * pc + p] = scratch_ranks + (size_t)p * std::max(pl.scratch_ranks, 1);
+      }
+      T* const* d_tab = (T* const*)ring.push(tab.data(), sizeof(void*) * (3 * nr + 1) * pc, st);
+      int* const* d_rtab = (int* const*)ring.push(rtab.data(), sizeof(void*) * (nr + 1) * pc, st);
+      for (const Stage& sg : pl.stages) {
+        if (sg.kind == ST_GEMM)
+          launch_ggemm<T>(pl, sg.beg, sg.end, d_tab, (const int* const*)d_rtab, pc, d_coefs, st);
+        else if (sg.kind == ST_PCHOL || sg.kind == ST_PCHOL + 16)
+          launch_pchol<T>(pl, sg.beg, sg.end, sg.kind == ST_PCHOL, tau_orth(), d_tab, d_rtab, pc, st);
+        else if (sg.kind == ST_EIG)
+          launch_eig<T>(pl, sg.beg, sg.end, eps, kc, op.c_role, d_tab, d_rtab, pc, d_err, st);
+      }
+    }
+  }
+
+  double tau_orth() const {
+    // range-finder truncation: three orders below eps, never below the
+    // relative noise floor of a Gram matrix in the storage precision
+    const double floor_ = sizeof(T) == 8 ? 1e-7 : 1e-3;
+    return std::max(1e-3 * eps, floor_);
+  }
+
+  // ------------------------------------------------------------ H-inverse
+  void hinv(int t, const std::vector<std::vector<HM>>& roles, void* d_xdense, int P,
+            cudaStream_t st) {
+    const Cluster& c = S.cl[t];
+    if (c.child[0] < 0) {
+      int nd = S.node(t, t);
+      launch_leaf_inv<T>((T* const*)d_xdense, S.dense_off(S.bn[nd].leaf), S.lsz, P, d_err, st);
+      return;
+    }
+    const int t1 = c.child[0], t2 = c.child[1];
+    const int n11 = S.node(t1, t1), n12 = S.node(t1, t2), n21 = S.node(t2, t1),
+              n22 = S.node(t2, t2);
+    auto mk = [&](int cnode, int crole, int alpha, int an, int ar, int bn, int br, int coef) {
+      OpDesc op;
+      op.c_node = cnode; op.c_role = crole; op.alpha = alpha; op.nroles = 2;
+      op.prods.push_back(OpDesc::Prod{an, bn, ar, br, coef});
+      return op;
+    };
+    hinv(t1, roles, d_xdense, P, st);
+    run_op(mk(n12, 1, -1, n11, 0, n12, 0, 0), roles, P, st);   // T12 = X11 A12
+    run_op(mk(n21, 1, -1, n21, 0, n11, 0, 0), roles, P, st);   // T21 = A21 X11
+    run_op(mk(n22, 0, 0, n21, 0, n12, 1, 1), roles, P, st);    // S = A22 - A21 T12
+    hinv(t2, roles, d_xdense, P, st);
+    run_op(mk(n12, 0, -1, n12, 1, n22, 0, 1), roles, P, st);   // X12 = -T12 X22
+    run_op(mk(n21, 0, -1, n22, 0, n21, 1, 1), roles, P, st);   // X21 = -X22 T21
+    run_op(mk(n11, 0, 0, n12, 0, n21, 1, 1), roles, P, st);    // X11 = X11 - X12 T21
+  }
+
+  void hinv_batch(const std::vector<int>& planes, cudaStream_t st) {
+    const int P = (int)planes.size();
+    if (P == 0) return;
+    std::vector<std::vector<HM>> roles(2);
+    for (int i : planes) {
+      roles[0].push_back(D[i]);
+      roles[1].push_back(alloc_hm());
+    }
+    std::vector<void*> xd(P);
+    for (int p = 0; p < P; ++p) xd[p] = roles[0][p].dense;
+    void* d_xdense = dmalloc(sizeof(void*) * P);
+    ACR_CUDA(cudaMemcpy(d_xdense, xd.data(), sizeof(void*) * P, cudaMemcpyHostToDevice));
+    hinv(0, roles, d_xdense, P, st);
+    ACR_CUDA(cudaStreamSynchronize(st));
+    cudaFree(d_xdense);
+    for (HM& h : roles[1]) free_hm(h);
+  }
+
+  void check_err(cudaStream_t st) {
+    ACR_CUDA(cudaStreamSynchronize(st));
+    int h = 0;
+    ACR_CUDA(cudaMemcpy(&h, d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (h & ERR_PIVOT) throw AcrError{S_BREAKDOWN, "zero pivot in a dense leaf inverse"};
+    if (h & ERR_RANKCAP) throw AcrError{S_RANK_CAP, "truncated rank above the rank cap"};
+  }
+
+  template <typename V>
+  void** put_tables(const std::vector<V>& host) {
+    void* p = dmalloc(std::max<size_t>(host.size() * sizeof(V), 16));
+    if (!host.empty())
+      ACR_CUDA(cudaMemcpy(p, host.data(), host.size() * sizeof(V), cudaMemcpyHostToDevice));
+    owned.push_back(p);
+    return (void**)p;
+  }
+
+  void build_apply_program();
+  void run_steps(const std::vector<ApplyStep>& steps, cudaStream_t st);
+  void collect_info();
+};
+
+template <typename T>
+void Engine<T>::setup(const double* coef, cudaStream_t st) {
+  auto h0 = std::chrono::steady_clock::now();
+  S.build(n, eta, leaf);
+  if (!S.balanced || S.lsz > 64 || S.lsz < 1)
+    throw AcrError{S_UNSUPPORTED, "cluster tree is not balanced with leaves of at most 64 points"};
+  pp.kc = kc;
+  pp.oversample = 8;
+  pp.cholqr2 = true;
+  mvp.build(S);
+  ring.init(size_t(64) << 20);
+  {
+    size_t fr = 0, tot = 0;
+    ACR_CUDA(cudaMemGetInfo(&fr, &tot));
+    scratch_budget = std::max<size_t>(size_t(256) << 20, fr / 4);
+    if (const char* e = getenv("ACR_SCRATCH_MB")) scratch_budget = size_t(atol(e)) << 20;
+  }
+  // structure arrays
+  std::vector<int> dinfo, linfo, cptr{0}, cpl;
+  for (int d : S.dleaf) { dinfo.push_back(S.cl[S.bn[d].t].begin); dinfo.push_back(S.cl[S.bn[d].s].begin); }
+  std::vector<int> iperm(n2);
+  for (int i = 0; i < n2; ++i) iperm[S.perm[i]] = i;
+  int maxcpl = 0;
+  for (int l : S.lleaf) {
+    const Cluster &ct = S.cl[S.bn[l].t], &cs = S.cl[S.bn[l].s];
+    linfo.push_back(ct.size); linfo.push_back(cs.size);
+    linfo.push_back(ct.begin); linfo.push_back(cs.begin);
+    int cnt = 0;
+    for (int i = 0; i < ct.size; ++i) {
+      int a = S.perm[ct.begin + i];
+      int ax = a % n, ay = a / n;
+      const int nb[4] = {ax > 0 ? a - 1 : -1, ax < n - 1 ? a + 1 : -1, ay > 0 ? a - n : -1,
+                         ay < n - 1 ? a + n : -1};
+      for (int d = 0; d < 4; ++d) {
+        if (nb[d] < 0) continue;
+        int pos = iperm[nb[d]];
+        if (pos >= cs.begin && pos < cs.begin + cs.size) {
+          cpl.push_back(i); cpl.push_back(pos - cs.begin); cpl.push_back(d + 1);
+          ++cnt;
+        }
+      }
+    }
+    maxcpl = std::max(maxcpl, cnt);
+    cptr.push_back((int)(cpl.size() / 3));
+  }
+  if (maxcpl > kc)
+    throw AcrError{S_RANK_CAP, "plane couplings inside an admissible block exceed the rank cap"};
+  const bool has_cpl = !cpl.empty();
+  sd.perm = (const int*)upload(S.perm, owned);
+  sd.dinfo = (const int*)upload(dinfo, owned);
+  sd.linfo = (const int*)upload(linfo, owned);
+  sd.row0 = (const int64_t*)upload(S.lr_row0, owned);
+  sd.col0 = (const int64_t*)upload(S.lr_col0, owned);
+  sd.cpl = (const int*)upload(cpl, owned);
+  sd.cptr = (const int*)upload(cptr, owned);
+  sd.nd = (int)S.dleaf.size(); sd.nl = (int)S.lleaf.size(); sd.lsz = S.lsz;
+  mvd.d_ptr = (const int32_t*)upload(mvp.d_ptr, owned);
+  mvd.d_leaf = (const int32_t*)upload(mvp.d_leaf, owned);
+  mvd.d_col = (const int32_t*)upload(mvp.d_col, owned);
+  mvd.l_ptr = (const int32_t*)upload(mvp.l_ptr, owned);
+  mvd.l_leaf = (const int32_t*)upload(mvp.l_leaf, owned);
+  mvd.l_rowoff = (const int32_t*)upload(mvp.l_rowoff, owned);
+  mvd.dt_ptr = (const int32_t*)upload(mvp.dt_ptr, owned);
+  mvd.dt_leaf = (const int32_t*)upload(mvp.dt_leaf, owned);
+  mvd.dt_row = (const int32_t*)upload(mvp.dt_row, owned);
+  mvd.lt_ptr = (const int32_t*)upload(mvp.lt_ptr, owned);
+  mvd.lt_leaf = (const int32_t*)upload(mvp.lt_leaf, owned);
+  mvd.lt_coloff = (const int32_t*)upload(mvp.lt_coloff, owned);
+  mvd.lr_m = (const int32_t*)upload(mvp.lr_m, owned);
+  mvd.lr_n = (const int32_t*)upload(mvp.lr_n, owned);
+  mvd.lr_t0 = (const int32_t*)upload(mvp.lr_t0, owned);
+  mvd.lr_s0 = (const int32_t*)upload(mvp.lr_s0, owned);
+  mvd.lr_row0 = sd.row0;
+  mvd.lr_col0 = sd.col0;
+  mvd.nchunks = S.nleafcl; mvd.lsz = S.lsz; mvd.nl = sd.nl; mvd.kc = kc;
+  std::vector<double> coefs{1.0, -1.0};
+  d_coefs = (double*)upload(coefs, owned);
+  d_err = (int*)dmalloc(sizeof(int));
+  owned.push_back(d_err);
+  ACR_CUDA(cudaMemset(d_err, 0, sizeof(int)));
+  std::vector<int> allp(n);
+  for (int k = 0; k < n; ++k) allp[k] = k;
+  d_planes_all = (int*)upload(allp, owned);
+  auto h1 = std::chrono::steady_clock::now();
+
+  cudaEvent_t e0, e1;
+  ACR_CUDA(cudaEventCreate(&e0));
+  ACR_CUDA(cudaEventCreate(&e1));
+  ACR_CUDA(cudaEventRecord(e0, st));
+
+  // a3: plane blocks in H-format
+  D.resize(n);
+  for (int k = 0; k < n; ++k) D[k] = alloc_hm();
+  {
+    std::vector<void*> td(n), tu(n), tv(n), tr(n);
+    for (int k = 0; k < n; ++k) { td[k] = D[k].dense; tu[k] = D[k].U; tv[k] = D[k].V; tr[k] = D[k].rank; }
+    void** a = put_tables(td); void** b = put_tables(tu); void** c = put_tables(tv);
+    void** d = put_tables(tr);
+    launch_plane_to_h<T>(sd, coef, n, d_planes_all, n, (T* const*)a, (T* const*)b, (T* const*)c,
+                         (int* const*)d, kc, st);
+    if (has_cpl) {
+      OpDesc op;
+      op.c_node = 0; op.c_role = 0; op.alpha = 0; op.nroles = 1;
+      std::vector<std::vector<HM>> roles{D};
+      run_op(op, roles, n, st);
+    }
+  }
+  Ld = (double*)dmalloc(sizeof(double) * N);
+  Ud = (double*)dmalloc(sizeof(double) * N);
+  owned.push_back(Ld); owned.push_back(Ud);
+  launch_permute(coef + 5 * N, Ld, sd.perm, n2, n, true, st);
+  launch_permute(coef + 6 * N, Ud, sd.perm, n2, n, true, st);
+
+  std::vector<HM> curL(n), curU(n);   // couplings of the current level (r >= 1)
+  int s = 1, r = 0;
+  while (s < n) {
+    Level lev;
+    lev.s = s;
+    for (int k = s; k < n; k += 2 * s) lev.red.push_back(k);
+    for (int k = 0; k < n; k += 2 * s) lev.black.push_back(k);
+    lev.L = curL;
+    lev.U = curU;
+    // a4: H-inverse of the red planes, in place
+    hinv_batch(lev.red, st);
+    check_err(st);
+    // a5-a7: Schur updates of the black planes
+    const int PB = (int)lev.black.size();
+    std::vector<HM> newL(n), newU(n);
+    if (r == 0) {
+      std::vector<HM> Ta(PB), Tb(PB), nL(PB), nU(PB), Xa(PB), Xb(PB), Dj(PB);
+      std::vector<const double*> rowA(PB), colA(PB), rowB(PB), colB(PB), colLA(PB), colUB(PB);
+      for (int q = 0; q < PB; ++q) {
+        const int j = lev.black[q], a = j - s, b = j + s;
+        Dj[q] = D[j];
+        if (a >= 0) {
+          Xa[q] = D[a]; Ta[q] = alloc_hm(); nL[q] = alloc_hm();
+          rowA[q] = Ld + (int64_t)j * n2; colA[q] = Ud + (int64_t)a * n2;
+          colLA[q] = Ld + (int64_t)a * n2;
+        }
+        if (b < n) {
+          Xb[q] = D[b]; Tb[q] = alloc_hm();
+          rowB[q] = Ud + (int64_t)j * n2; colB[q] = Ld + (int64_t)b * n2;
+          if (b + s < n) { nU[q] = alloc_hm(); colUB[q] = Ud + (int64_t)b * n2; }
+        }
+      }
+      auto scale = [&](std::vector<HM>& out, std::vector<HM>& x, std::vector<const double*>& rs,
+                       std::vector<const double*>& cs, double sgn) {
+        std::vector<void*> od(PB), ou(PB), ov(PB), orr(PB), xd(PB), xu(PB), xv(PB), xr(PB);
+        for (int q = 0; q < PB; ++q) {
+          bool ok = out[q].dense && x[q].dense;
+          od[q] = ok ? out[q].dense : nullptr; ou[q] = ok ? out[q].U : nullptr;
+          ov[q] = ok ? out[q].V : nullptr; orr[q] = ok ? (void*)out[q].rank : nullptr;
+          xd[q] = x[q].dense; xu[q] = x[q].U; xv[q] = x[q].V; xr[q] = x[q].rank;
+        }
+        std::vector<const void*> rr(rs.begin(), rs.end()), cc(cs.begin(), cs.end());
+        void** t[10] = {put_tables(od), put_tables(ou), put_tables(ov), put_tables(orr),
+                        put_tables(xd), put_tables(xu), put_tables(xv), put_tables(xr),
+                        put_tables(rr), put_tables(cc)};
+        launch_hscale<T>(sd, (T* const*)t[0], (T* const*)t[1], (T* const*)t[2], (int* const*)t[3],
+                         (T* const*)t[4], (T* const*)t[5], (T* const*)t[6],
+                         (const int* const*)t[7], (const double* const*)t[8],
+                         (const double* const*)t[9], sgn, kc, PB, st);
+      };
+      scale(Ta, Xa, rowA, colA, 1.0);
+      scale(Tb, Xb, rowB, colB, 1.0);
+      scale(nL, Xa, rowA, colLA, -1.0);
+      scale(nU, Xb, rowB, colUB, -1.0);
+      OpDesc op;
+      op.c_node = 0; op.c_role = 0; op.alpha = 0; op.nroles = 3;
+      op.adds.push_back(OpDesc::Add{1, 1});
+      op.adds.push_back(OpDesc::Add{2, 1});
+      std::vector<std::vector<HM>> roles{Dj, Ta, Tb};
+      run_op(op, roles, PB, st);
+      ACR_CUDA(cudaStreamSynchronize(st));
+      for (int q = 0; q < PB; ++q) {
+        if (Ta[q].dense) free_hm(Ta[q]);
+        if (Tb[q].dense) free_hm(Tb[q]);
+        newL[lev.black[q]] = nL[q];
+        newU[lev.black[q]] = nU[q];
+      }
+    } else {
+      std::vector<HM> Ta(PB), Tb(PB), Lj(PB), Uj(PB), Xa(PB), Xb(PB), Dj(PB), Ua(PB), Lb(PB),
+          La(PB), Ub(PB), nL(PB), nU(PB);
+      for (int q = 0; q < PB; ++q) {
+        const int j = lev.black[q], a = j - s, b = j + s;
+        Dj[q] = D[j];
+        Lj[q] = curL[j];
+        Uj[q] = curU[j];
+        if (a >= 0 && curL[j].dense) {
+          Xa[q] = D[a]; Ta[q] = alloc_hm(); Ua[q] = curU[a]; La[q] = curL[a];
+          if (La[q].dense) nL[q] = alloc_hm();
+        }
+        if (b < n && curU[j].dense) {
+          Xb[q] = D[b]; Tb[q] = alloc_hm(); Lb[q] = curL[b]; Ub[q] = curU[b];
+          if (Ub[q].dense) nU[q] = alloc_hm();
+        }
+      }
+      OpDesc opT;
+      opT.c_node = 0; opT.c_role = 0; opT.alpha = -1; opT.nroles = 3;
+      opT.prods.push_back(OpDesc::Prod{0, 0, 1, 2, 0});
+      run_op(opT, {Ta, Lj, Xa}, PB, st);              // Ta = L_j X_a
+      run_op(opT, {Tb, Uj, Xb}, PB, st);              // Tb = U_j X_b
+      OpDesc opD;
+      opD.c_node = 0; opD.c_role = 0; opD.alpha = 0; opD.nroles = 5;
+      opD.prods.push_back(OpDesc::Prod{0, 0, 1, 2, 1});
+      opD.prods.push_back(OpDesc::Prod{0, 0, 3, 4, 1});
+      run_op(opD, {Dj, Ta, Ua, Tb, Lb}, PB, st);      // D_j -= Ta U_a + Tb L_b
+      OpDesc opN;
+      opN.c_node = 0; opN.c_role = 0; opN.alpha = -1; opN.nroles = 3;
+      opN.prods.push_back(OpDesc::Prod{0, 0, 1, 2, 1});
+      run_op(opN, {nL, Ta, La}, PB, st);              // L_j' = -Ta L_a
+      run_op(opN, {nU, Tb, Ub}, PB, st);              // U_j' = -Tb U_b
+      ACR_CUDA(cudaStreamSynchronize(st));
+      for (int q = 0; q < PB; ++q) {
+        if (Ta[q].dense) free_hm(Ta[q]);
+        if (Tb[q].dense) free_hm(Tb[q]);
+        newL[lev.black[q]] = nL[q];
+        newU[lev.black[q]] = nU[q];
+      }
+    }
+    check_err(st);
+    for (int j : lev.black) { curL[j] = newL[j]; curU[j] = newU[j]; }
+    levels.push_back(std::move(lev));
+    s *= 2;
+    ++r;
+  }
+  // a8: the last plane
+  hinv_batch({0}, st);
+  check_err(st);
+  ACR_CUDA(cudaEventRecord(e1, st));
+  ACR_CUDA(cudaEventSynchronize(e1));
+  float ms = 0;
+  ACR_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  info.setup_ms = ms;
+  info.structure_ms = std::chrono::duration<double, std::milli>(h1 - h0).count();
+  info.levels = (int)levels.size();
+  info.n_dense_leaves = sd.nd;
+  info.n_lowrank_leaves = sd.nl;
+  // the scratch arena is only needed by the setup
+  if (scratch) { cudaFree(scratch); scratch = nullptr; scratch_bytes = 0; }
+  if (scratch_ranks) { cudaFree(scratch_ranks); scratch_ranks = nullptr; scratch_rank_cnt = 0; }
+  collect_info();
+  build_apply_program();
+}
+
+template <typename T>
+void Engine<T>::collect_info() {
+  // ranks of every stored low-rank block
+  std::vector<int> rk(S.lleaf.size());
+  int64_t sumr = 0, cnt = 0;
+  int mx = 0;
+  int64_t bytes = 0;
+  auto account = [&](const HM& h) {
+    if (!h.dense) return;
+    if (!rk.empty())
+      ACR_CUDA(cudaMemcpy(rk.data(), h.rank, rk.size() * sizeof(int), cudaMemcpyDeviceToHost));
+    bytes += (int64_t)S.dleaf.size() * S.lsz * S.lsz * sizeof(T);
+    for (size_t l = 0; l < rk.size(); ++l) {
+      mx = std::max(mx, rk[l]);
+      sumr += rk[l];
+      ++cnt;
+      bytes += (int64_t)rk[l] * (mvp.lr_m[l] + mvp.lr_n[l]) * sizeof(T);
+    }
+  };
+  for (const Level& lev : levels) {
+    for (int i : lev.red) account(D[i]);
+    for (int k = 0; k < n; ++k) { account(lev.L[k]); account(lev.U[k]); }
+  }
+  account(D[0]);
+  info.max_rank = mx;
+  info.avg_rank = cnt ? (double)sumr / cnt : 0.0;
+  info.factor_bytes = bytes + 2 * N * (int64_t)sizeof(double);
+  int64_t per = ((int64_t)S.dleaf.size() * S.lsz * S.lsz + (S.sumM + S.sumN) * kc) * sizeof(T);
+  info.factor_capacity_bytes = per * (int64_t)heap.size() + 2 * N * (int64_t)sizeof(double);
+}
+
+template <typename T>
+void Engine<T>::build_apply_program() {
+  Fv = (double*)dmalloc(sizeof(double) * N); owned.push_back(Fv);
+  Gv = (double*)dmalloc(sizeof(double) * N); owned.push_back(Gv);
+  Uv = (double*)dmalloc(sizeof(double) * N); owned.push_back(Uv);
+  Tv = (double*)dmalloc(sizeof(double) * N); owned.push_back(Tv);
+  maxP = 1;
+  for (const Level& lev : levels) maxP = std::max<int>(maxP, (int)std::max(lev.red.size(), lev.black.size()));
+  tvscr = (double*)dmalloc(sizeof(double) * (size_t)maxP * std::max(sd.nl, 1) * kc);
+  owned.push_back(tvscr);
+  auto vec = [&](double* base, int k) -> double* { return (k >= 0 && k < n) ? base + (int64_t)k * n2 : nullptr; };
+  // hmatvec tables: dense, U, V, rank, x, y (6 * P pointers)
+  auto mv_step = [&](const std::vector<HM>& H, const std::vector<double*>& x,
+                     const std::vector<double*>& y, double alpha, double beta, bool trans) {
+    const int P = (int)H.size();
+    std::vector<void*> t(6 * P);
+    for (int p = 0; p < P; ++p) {
+      t[p] = H[p].dense; t[P + p] = H[p].U; t[2 * P + p] = H[p].V; t[3 * P + p] = H[p].rank;
+      t[4 * P + p] = x[p]; t[5 * P + p] = y[p];
+    }
+    return ApplyStep{0, P, trans, alpha, beta, 0.0, put_tables(t)};
+  };
+  auto diag_step = [&](const std::vector<double*>& y, const std::vector<const double*>& a,
+                       const std::vector<double*>& x, const std::vector<const double*>& b,
+                       const std::vector<double*>& z, double sgn) {
+    const int P = (int)y.size();
+    std::vector<const void*> t(5 * P);
+    for (int p = 0; p < P; ++p) {
+      t[p] = y[p]; t[P + p] = a[p]; t[2 * P + p] = x[p]; t[3 * P + p] = b[p]; t[4 * P + p] = z[p];
+    }
+    return ApplyStep{1, P, false, 0.0, 0.0, sgn, put_tables(t)};
+  };
+  auto copy_step = [&](const std::vector<double*>& dst, const std::vector<double*>& src) {
+    const int P = (int)dst.size();
+    std::vector<void*> t(2 * P);
+    for (int p = 0; p < P; ++p) { t[p] = dst[p]; t[P + p] = src[p]; }
+    return ApplyStep{2, P, false, 0.0, 0.0, 0.0, put_tables(t)};
+  };
+  for (int pass = 0; pass < 2; ++pass) {
+    const bool tr = pass == 1;
+    auto& fw = tr ? fwdT_steps : fwd_steps;
+    auto& bw = tr ? bwdT_steps : bwd_steps;
+    for (size_t r = 0; r < levels.size(); ++r) {
+      const Level& lev = levels[r];
+      const int s = lev.s;
+      // g_i = X_i f_i  (transposed: X_i^T f_i)
+      std::vector<HM> X;
+      std::vector<double*> xs, ys;
+      for (int i : lev.red) { X.push_back(D[i]); xs.push_back(vec(Fv, i)); ys.push_back(vec(Gv, i)); }
+      fw.push_back(mv_step(X, xs, ys, 1.0, 0.0, tr));
+      // black: f_j -= Lc_j g_{j-s} + Uc_j g_{j+s}
+      // couplings: L_j, U_j (plain); U_{j-s}^T, L_{j+s}^T (transposed)
+      if (r == 0) {
+        std::vector<double*> y, x1, x2;
+        std::vector<const double*> a, b;
+        for (int j : lev.black) {
+          y.push_back(vec(Fv, j));
+          const bool ha = j - s >= 0, hb = j + s < n;
+          if (!tr) {
+            a.push_back(ha ? Ld + (int64_t)j * n2 : nullptr);
+            b.push_back(hb ? Ud + (int64_t)j * n2 : nullptr);
+          } else {
+            a.push_back(ha ? Ud + (int64_t)(j - s) * n2 : nullptr);
+            b.push_back(hb ? Ld + (int64_t)(j + s) * n2 : nullptr);
+          }
+          x1.push_back(ha ? vec(Gv, j - s) : nullptr);
+          x2.push_back(hb ? vec(Gv, j + s) : nullptr);
+        }
+        fw.push_back(diag_step(y, a, x1, b, x2, -1.0));
+      } else {
+        std::vector<HM> H1, H2;
+        std::vector<double*> y, x1, x2;
+        for (int j : lev.black) {
+          y.push_back(vec(Fv, j));
+          const bool ha = j - s >= 0, hb = j + s < n;
+          if (!tr) {
+            H1.push_back(ha ? lev.L[j] : HM());
+            H2.push_back(hb ? lev.U[j] : HM());
+          } else {
+            H1.push_back(ha ? lev.U[j - s] : HM());
+            H2.push_back(hb ? lev.L[j + s] : HM());
+          }
+          x1.push_back(ha ? vec(Gv, j - s) : nullptr);
+          x2.push_back(hb ? vec(Gv, j + s) : nullptr);
+        }
+        fw.push_back(mv_step(H1, x1, y, -1.0, 1.0, tr));
+        fw.push_back(mv_step(H2, x2, y, -1.0, 1.0, tr));
+      }
+    }
+    // last plane: u_0 = X_0 f_0
+    fw.push_back(mv_step(std::vector<HM>{D[0]}, std::vector<double*>{vec(Fv, 0)},
+                         std::vector<double*>{vec(Uv, 0)}, 1.0, 0.0, tr));
+    // backward (stored in reverse level order)
+    for (int r = (int)levels.size() - 1; r >= 0; --r) {
+      const Level& lev = levels[r];
+      const int s = lev.s;
+      std::vector<double*> tmp, x1, x2, us, gs;
+      std::vector<HM> X;
+      for (int i : lev.red) {
+        tmp.push_back(vec(Tv, i));
+        x1.push_back(vec(Uv, i - s));
+        x2.push_back(i + s < n ? vec(Uv, i + s) : nullptr);
+        us.push_back(vec(Uv, i));
+        gs.push_back(vec(Gv, i));
+        X.push_back(D[i]);
+      }
+      std::vector<double*> none(lev.red.size(), nullptr);
+      bw.push_back(copy_step(tmp, none));   // tmp = 0
+      if (r == 0) {
+        std::vector<const double*> a, b;
+        for (int i : lev.red) {
+          if (!tr) {
+            a.push_back(Ld + (int64_t)i * n2);
+            b.push_back(i + s < n ? Ud + (int64_t)i * n2 : nullptr);
+          } else {
+            a.push_back(Ud + (int64_t)(i - s) * n2);
+            b.push_back(i + s < n ? Ld + (int64_t)(i + s) * n2 : nullptr);
+          }
+        }
+        bw.push_back(diag_step(tmp, a, x1, b, x2, 1.0));
+      } else {
+        std::vector<HM> H1, H2;
+        for (int i : lev.red) {
+          if (!tr) {
+            H1.push_back(lev.L[i]);
+            H2.push_back(i + s < n ? lev.U[i] : HM());
+          } else {
+            H1.push_back(lev.U[i - s]);
+            H2.push_back(i + s < n ? lev.L[i + s] : HM());
+          }
+        }
+        bw.push_back(mv_step(H1, x1, tmp, 1.0, 1.0, tr));
+        bw.push_back(mv_step(H2, x2, tmp, 1.0, 1.0, tr));
+      }
+      bw.push_back(copy_step(us, gs));      // u_i = g_i
+      bw.push_back(mv_step(X, tmp, us, -1.0, 1.0, tr));  // u_i -= X_i tmp
+    }
+  }
+}
+
+template <typename T>
+void Engine<T>::run_steps(const std::vector<ApplyStep>& steps, cudaStream_t st) {
+  for (const ApplyStep& s : steps) {
+    const int P = s.P;
+    void** t = s.tabs;
+    if (s.kind == 0) {
+      launch_hmatvec<T>(mvd, (T* const*)t, (T* const*)(t + P), (T* const*)(t + 2 * P),
+                        (const int* const*)(t + 3 * P), (const double* const*)(t + 4 * P),
+                        (double* const*)(t + 5 * P), s.alpha, s.beta, s.trans, tvscr, P, st);
+    } else if (s.kind == 1) {
+      launch_diag_update((double* const*)t, (const double* const*)(t + P),
+                         (const double* const*)(t + 2 * P), (const double* const*)(t + 3 * P),
+                         (const double* const*)(t + 4 * P), n2, P, s.sgn, st);
+    } else {
+      launch_copy_planes((double* const*)t, (const double* const*)(t + P), n2, P, st);
+    }
+  }
+}
+
+template <typename T>
+void Engine<T>::apply(const double* r, double* z, bool trans, cudaStream_t st) {
+  launch_permute(r, Fv, sd.perm, n2, n, true, st);
+  run_steps(trans ? fwdT_steps : fwd_steps, st);
+  run_steps(trans ? bwdT_steps : bwd_steps, st);
+  launch_permute(Uv, z, sd.perm, n2, n, false, st);
+}
+
+
+// ------------------------------------------------------------ Krylov drivers
+namespace {
+
+struct Krylov {
+  cudaStream_t st;
+  int64_t N;
+  int n;
+  const double* coef;
+  EngineBase* E;
+  double* partial = nullptr;
+  double* dres = nullptr;
+  double* dcoef = nullptr;
+  double* hpin = nullptr;
+  std::vector<void*> mem;
+
+  double* dbuf(size_t cnt) {
+    double* p = (double*)dmalloc(cnt * sizeof(double));
+    mem.push_back(p);
+    return p;
+  }
+  ~Krylov() {
+    for (void* p : mem) cudaFree(p);
+    if (hpin) cudaFreeHost(hpin);
+  }
+  void init() {
+    partial = dbuf(64 * 600);
+    dres = dbuf(64);
+    dcoef = dbuf(64);
+    ACR_CUDA(cudaMallocHost(&hpin, 128 * sizeof(double)));
+  }
+  void A(const double* x, double* y) { launch_spmv(coef, x, y, n, st); }
+  void M(const double* x, double* y) {
+    if (E) E->apply(x, y, false, st);
+    else ACR_CUDA(cudaMemcpyAsync(y, x, N * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  }
+  // queue <V_j, w> for j < nv into dres[off..], no sync
+  void dots(const double* V, int64_t ldv, int nv, const double* w, int off) {
+    launch_multidot(V, ldv, nv, w, N, partial, dres + off, st);
+  }
+  void fetch(int cnt) {
+    ACR_CUDA(cudaMemcpyAsync(hpin, dres, cnt * sizeof(double), cudaMemcpyDeviceToHost, st));
+    ACR_CUDA(cudaStreamSynchronize(st));
+  }
+  double norm(const double* x) {
+    dots(x, 0, 1, x, 0);
+    fetch(1);
+    return std::sqrt(std::max(hpin[0], 0.0));
+  }
+};
+
+int run_pcg(Krylov& K, double rtol, int maxit, const double* f, double* u, acr_solve_info* info) {
+  const int64_t N = K.N;
+  double* r = K.dbuf(2 * N);
+  double* rold = r + N;
+  double* z = K.dbuf(N);
+  double* p = K.dbuf(N);
+  double* q = K.dbuf(N);
+  const double nf = K.norm(f);
+  int it = 0;
+  double res = 0.0;
+  int status = S_OK;
+  if (nf == 0.0) {
+    ACR_CUDA(cudaMemsetAsync(u, 0, N * sizeof(double), K.st));
+  } else {
+    K.A(u, q);
+    launch_axpby(r, f, 1.0, 0.0, N, K.st);
+    launch_axpby(r, q, -1.0, 1.0, N, K.st);
+    res = K.norm(r) / nf;
+    if (res > rtol) {
+      K.M(r, z);
+      launch_axpby(p, z, 1.0, 0.0, N, K.st);
+      K.dots(r, 0, 1, z, 0);
+      K.fetch(1);
+      double rz = K.hpin[0];
+      status = S_NOT_CONVERGED;
+      for (it = 1; it <= maxit; ++it) {
+        K.A(p, q);
+        K.dots(p, 0, 1, q, 0);
+        K.fetch(1);
+        const double pq = K.hpin[0];
+        if (!(std::isfinite(pq)) || pq == 0.0) { status = S_BREAKDOWN; break; }
+        const double alpha = rz / pq;
+        launch_axpby(u, p, alpha, 1.0, N, K.st);
+        launch_axpby(rold, r, 1.0, 0.0, N, K.st);
+        launch_axpby(r, q, -alpha, 1.0, N, K.st);
+        K.M(r, z);
+        K.dots(r, N, 2, z, 0);   // <r, z>, <rold, z>
+        K.dots(r, 0, 1, r, 2);   // <r, r>
+        K.fetch(3);
+        res = std::sqrt(std::max(K.hpin[2], 0.0)) / nf;
+        if (res <= rtol) { status = S_OK; break; }
+        const double zr = K.hpin[0], zro = K.hpin[1];
+        if (!std::isfinite(zr) || rz == 0.0) { status = S_BREAKDOWN; break; }
+        const double beta = (zr - zro) / rz;
+        rz = zr;
+        launch_axpby(p, z, 1.0, beta, N, K.st);
+      }
+      if (it > maxit) it = maxit;
+    }
+    // true residual
+    K.A(u, q);
+    launch_axpby(r, f, 1.0, 0.0, N, K.st);
+    launch_axpby(r, q, -1.0, 1.0, N, K.st);
+    res = K.norm(r) / nf;
+    if (status == S_OK && !(res <= rtol * 1.0000001)) status = S_NOT_CONVERGED;
+  }
+  if (info) {
+    info->iterations = it;
+    info->converged = status == S_OK;
+    info->rel_residual = res;
+  }
+  return status;
+}
+
+int run_gmres(Krylov& K, int m, double rtol, int maxit, const double* f, double* u,
+              acr_solve_info* info) {
+  const int64_t N = K.N;
+  if (m < 1) m = 30;
+  if (m > 60) m = 60;
+  double* V = K.dbuf((size_t)(m + 1) * N);
+  double* Z = K.dbuf((size_t)m * N);
+  double* w = K.dbuf(N);
+  double* r = K.dbuf(N);
+  const double nf = K.norm(f);
+  int it = 0;
+  double res = 0.0;
+  int status = S_OK;
+  if (nf == 0.0) {
+    ACR_CUDA(cudaMemsetAsync(u, 0, N * sizeof(double), K.st));
+  } else {
+    K.A(u, w);
+    launch_axpby(r, f, 1.0, 0.0, N, K.st);
+    launch_axpby(r, w, -1.0, 1.0, N, K.st);
+    double beta = K.norm(r);
+    res = beta / nf;
+    std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m);
+    while (res > rtol && it < maxit) {
+      std::fill(H.begin(), H.end(), 0.0);
+      std::fill(g.begin(), g.end(), 0.0);
+      g[0] = beta;
+      launch_axpby(V, r, 1.0 / beta, 0.0, N, K.st);
+      int used = 0;
+      bool stop = false;
+      for (int j = 0; j < m && !stop; ++j) {
+        double* Vj = V + (int64_t)j * N;
+        double* Zj = Z + (int64_t)j * N;
+        K.M(Vj, Zj);
+        K.A(Zj, w);
+        std::vector<double> h(j + 1, 0.0);
+        for (int pass = 0; pass < 2; ++pass) {   // classical Gram-Schmidt, twice
+          K.dots(V, N, j + 1, w, 0);
+          K.fetch(j + 1);
+          for (int k = 0; k <= j; ++k) h[k] += K.hpin[k];
+          ACR_CUDA(cudaMemcpyAsync(K.dcoef, K.hpin, (j + 1) * sizeof(double),
+                                   cudaMemcpyHostToDevice, K.st));
+          launch_multiaxpy(w, V, N, j + 1, K.dcoef, -1.0, N, K.st);
+        }
+        const double hn = K.norm(w);
+        for (int k = 0; k <= j; ++k) H[(size_t)k * m + j] = h[k];
+        H[(size_t)(j + 1) * m + j] = hn;
+        if (hn > 0.0) launch_axpby(V + (int64_t)(j + 1) * N, w, 1.0 / hn, 0.0, N, K.st);
+        for (int k = 0; k < j; ++k) {
+          const double a = H[(size_t)k * m + j], b = H[(size_t)(k + 1) * m + j];
+          H[(size_t)k * m + j] = cs[k] * a + sn[k] * b;
+          H[(size_t)(k + 1) * m + j] = -sn[k] * a + cs[k] * b;
+        }
+        const double a = H[(size_t)j * m + j], b = H[(size_t)(j + 1) * m + j];
+        const double d = std::hypot(a, b);
+        if (d == 0.0) { status = S_BREAKDOWN; stop = true; break; }
+        cs[j] = a / d; sn[j] = b / d;
+        H[(size_t)j * m + j] = d;
+        H[(size_t)(j + 1) * m + j] = 0.0;
+        g[j + 1] = -sn[j] * g[j];
+        g[j] = cs[j] * g[j];
+        ++it;
+        used = j + 1;
+        if (std::fabs(g[j + 1]) / nf <= rtol || it >= maxit || hn == 0.0) stop = true;
+      }
+      if (status == S_BREAKDOWN && used == 0) break;
+      for (int k = used - 1; k >= 0; --k) {
+        double sacc = g[k];
+        for (int l = k + 1; l < used; ++l) sacc -= H[(size_t)k * m + l] * y[l];
+        y[k] = sacc / H[(size_t)k * m + k];
+      }
+      std::memcpy(K.hpin, y.data(), used * sizeof(double));
+      ACR_CUDA(cudaMemcpyAsync(K.dcoef, K.hpin, used * sizeof(double), cudaMemcpyHostToDevice, K.st));
+      launch_multiaxpy(u, Z, N, used, K.dcoef, 1.0, N, K.st);
+      K.A(u, w);
+      launch_axpby(r, f, 1.0, 0.0, N, K.st);
+      launch_axpby(r, w, -1.0, 1.0, N, K.st);
+      beta = K.norm(r);
+      res = beta / nf;
+      if (status == S_BREAKDOWN) break;
+    }
+    if (status == S_OK && !(res <= rtol)) status = S_NOT_CONVERGED;
+  }
+  if (info) {
+    info->iterations = it;
+    info->converged = status == S_OK;
+    info->rel_residual = res;
+  }
+  return status;
+}
+
+}  // namespace
+
+}  // namespace acr
+
+// ====================================================================== C ABI
+struct acr_handle {
+  acr::EngineBase* e = nullptr;
+  acr_grid grid{};
+  int precision = 0;
+};
+
+namespace {
+
+acr_status to_status(int s) { return (acr_status)s; }
+
+template <typename F>
+acr_status guarded(F&& fn) {
+  try {
+    return to_status(fn());
+  } catch (const acr::AcrError& e) {
+    return to_status(e.status);
+  } catch (const acr::CudaError& e) {
+    (void)e;
+    cudaGetLastError();
+    return ACR_ERR_CUDA;
+  } catch (const std::bad_alloc&) {
+    return ACR_ERR_OOM;
+  } catch (const std::exception&) {
+    return ACR_ERR_UNSUPPORTED;
+  }
+}
+
+bool grid_ok(const acr_grid* g) {
+  return g && g->nx > 0 && g->nx == g->ny && g->nx == g->nz && g->nx <= 1024;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* acr_status_string(acr_status s) {
+  switch (s) {
+    case ACR_OK: return "ok";
+    case ACR_ERR_INVALID_ARG: return "invalid argument";
+    case ACR_ERR_OOM: return "out of device memory";
+    case ACR_ERR_CUDA: return "CUDA error";
+    case ACR_ERR_BREAKDOWN: return "breakdown (zero pivot or Krylov breakdown)";
+    case ACR_ERR_RANK_CAP: return "rank cap exceeded";
+    case ACR_ERR_NOT_CONVERGED: return "not converged";
+    case ACR_ERR_TIMEOUT: return "device wait timed out";
+    case ACR_ERR_UNSUPPORTED: return "unsupported configuration";
+  }
+  return "unknown status";
+}
+
+acr_status acr_stencil_poisson(const acr_grid* grid, const double* kappa, double* coef,
+                               cudaStream_t stream) {
+  if (!grid_ok(grid) || !kappa || !coef) return ACR_ERR_INVALID_ARG;
+  return guarded([&] {
+    acr::launch_stencil_poisson(kappa, coef, grid->nx, stream);
+    return 0;
+  });
+}
+
+acr_status acr_stencil_codi(const acr_grid* grid, const double* beta, double* coef,
+                            cudaStream_t stream) {
+  if (!grid_ok(grid) || !beta || !coef) return ACR_ERR_INVALID_ARG;
+  return guarded([&] {
+    acr::launch_stencil_codi(beta, coef, grid->nx, stream);
+    return 0;
+  });
+}
+
+acr_status acr_spmv(const acr_grid* grid, const double* coef, const double* x, double* y,
+                    int32_t nrhs, cudaStream_t stream) {
+  if (!grid_ok(grid) || !coef || !x || !y || nrhs < 1) return ACR_ERR_INVALID_ARG;
+  return guarded([&] {
+    const int64_t N = (int64_t)grid->nx * grid->nx * grid->nx;
+    for (int k = 0; k < nrhs; ++k) acr::launch_spmv(coef, x + k * N, y + k * N, grid->nx, stream);
+    return 0;
+  });
+}
+
+acr_status acr_setup(const acr_grid* grid, const double* coef, const acr_options* opt,
+                     cudaStream_t stream, acr_handle** out) {
+  if (out) *out = nullptr;
+  if (!grid_ok(grid) || !coef || !opt || !out) return ACR_ERR_INVALID_ARG;
+  if (!(opt->eps > 0.0 && opt->eps < 1.0) || !(opt->eta > 0.0) || opt->leaf < 1 ||
+      (opt->precision != ACR_FP64 && opt->precision != ACR_FP32) || opt->rank_cap < 0 ||
+      opt->rank_cap > 48)
+    return ACR_ERR_INVALID_ARG;
+  const int kc = opt->rank_cap == 0 ? 32 : opt->rank_cap;
+  acr_handle* h = new acr_handle();
+  h->grid = *grid;
+  h->precision = opt->precision;
+  acr_status s = guarded([&] {
+    if (opt->precision == ACR_FP64)
+      h->e = new acr::Engine<double>(grid->nx, opt->eps, opt->eta, opt->leaf, kc);
+    else
+      h->e = new acr::Engine<float>(grid->nx, opt->eps, opt->eta, opt->leaf, kc);
+    h->e->setup(coef, stream);
+    return 0;
+  });
+  if (s != ACR_OK) {
+    delete h->e;
+    delete h;
+    return s;
+  }
+  *out = h;
+  return ACR_OK;
+}
+
+acr_status acr_apply(acr_handle* h, const double* r, double* z, int32_t nrhs,
+                     cudaStream_t stream) {
+  if (!h || !h->e || !r || !z || nrhs < 1) return ACR_ERR_INVALID_ARG;
+  return guarded([&] {
+    const int64_t N = h->e->N;
+    for (int k = 0; k < nrhs; ++k) h->e->apply(r + k * N, z + k * N, false, stream);
+    return 0;
+  });
+}
+
+acr_status acr_apply_transpose(acr_handle* h, const double* r, double* z, int32_t nrhs,
+                               cudaStream_t stream) {
+  if (!h || !h->e || !r || !z || nrhs < 1) return ACR_ERR_INVALID_ARG;
+  return guarded([&] {
+    const int64_t N = h->e->N;
+    for (int k = 0; k < nrhs; ++k) h->e->apply(r + k * N, z + k * N, true, stream);
+    return 0;
+  });
+}
+
+static acr_status krylov_common(acr::EngineBase* E, const acr_grid* grid, const double* coef,
+                                int32_t method, int32_t restart, double rtol, int32_t maxit,
+                                const double* f, double* u, acr_solve_info* info,
+                                cudaStream_t stream) {
+  if (!grid_ok(grid) || !coef || !f || !u || !(rtol > 0.0) || maxit < 1 ||
+      (method != ACR_PCG && method != ACR_GMRES))
+    return ACR_ERR_INVALID_ARG;
+  return guarded([&] {
+    acr::Krylov K;
+    K.st = stream;
+    K.n = grid->nx;
+    K.N = (int64_t)grid->nx * grid->nx * grid->nx;
+    K.coef = coef;
+    K.E = E;
+    K.init();
+    cudaEvent_t e0, e1;
+    ACR_CUDA(cudaEventCreate(&e0));
+    ACR_CUDA(cudaEventCreate(&e1));
+    ACR_CUDA(cudaEventRecord(e0, stream));
+    int s = method == ACR_PCG ? acr::run_pcg(K, rtol, maxit, f, u, info)
+                              : acr::run_gmres(K, restart, rtol, maxit, f, u, info);
+    ACR_CUDA(cudaEventRecord(e1, stream));
+    ACR_CUDA(cudaEventSynchronize(e1));
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (info) info->solve_ms = ms;
+    return s;
+  });
+}
+
+acr_status acr_krylov_solve(acr_handle* h, const double* coef, int32_t method, int32_t restart,
+                            double rtol, int32_t maxit, const double* f, double* u,
+                            int32_t nrhs, acr_solve_info* info, cudaStream_t stream) {
+  if (!h || !h->e || nrhs != 1) return ACR_ERR_INVALID_ARG;
+  return krylov_common(h->e, &h->grid, coef, method, restart, rtol, maxit, f, u, info, stream);
+}
+
+acr_status acr_krylov_solve_plain(const acr_grid* grid, const double* coef, int32_t method,
+                                  int32_t restart, double rtol, int32_t maxit,
+                                  const double* f, double* u, acr_solve_info* info,
+                                  cudaStream_t stream) {
+  return krylov_common(nullptr, grid, coef, method, restart, rtol, maxit, f, u, info, stream);
+}
+
+acr_status acr_get_setup_info(const acr_handle* h, acr_setup_info* info) {
+  if (!h || !h->e || !info) return ACR_ERR_INVALID_ARG;
+  *info = h->e->info;
+  return ACR_OK;
+}
+
+acr_status acr_structure_query(int32_t n, double eta, int32_t leaf, int64_t* counts,
+                               int32_t* leaves_host, int32_t* perm_host) {
+  if (n < 1 || n > 1024 || !(eta > 0.0) || leaf < 1 || !counts) return ACR_ERR_INVALID_ARG;
+  try {
+    acr::Structure S;
+    S.build(n, eta, leaf);
+    counts[0] = (int64_t)S.cl.size();
+    counts[1] = (int64_t)S.dleaf.size();
+    counts[2] = (int64_t)S.lleaf.size();
+    counts[3] = S.sumM;
+    counts[4] = S.sumN;
+    counts[5] = S.depth;
+    if (leaves_host) {
+      int64_t k = 0;
+      for (int i = 0; i < (int)S.bn.size(); ++i) {
+        const acr::BNode& b = S.bn[i];
+        if (b.kind == acr::BK_INNER) continue;
+        leaves_host[k++] = S.cl[b.t].begin;
+        leaves_host[k++] = S.cl[b.t].size;
+        leaves_host[k++] = S.cl[b.s].begin;
+        leaves_host[k++] = S.cl[b.s].size;
+        leaves_host[k++] = b.kind == acr::BK_LOWRANK ? 1 : 0;
+      }
+    }
+    if (perm_host)
+      for (int i = 0; i < n * n; ++i) perm_host[i] = S.perm[i];
+  } catch (...) {
+    return ACR_ERR_INVALID_ARG;
+  }
+  return ACR_OK;
+}
+
+void acr_destroy(acr_handle* h) {
+  if (!h) return;
+  delete h->e;
+  delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,120 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+
+#include "acr_plan.h"
+
+namespace acr {
+
+// Status codes mirror acr_status (include/acr.h).
+enum Status {
+  S_OK = 0, S_INVALID = 1, S_OOM = 2, S_CUDA = 3, S_BREAKDOWN = 4,
+  S_RANK_CAP = 5, S_NOT_CONVERGED = 6, S_TIMEOUT = 7, S_UNSUPPORTED = 8
+};
+
+// Device-side error word bits (written by kernels, read by the host).
+enum : int { ERR_PIVOT = 1, ERR_RANKCAP = 2 };
+
+struct CudaError {
+  cudaError_t e;
+  const char* where;
+};
+
+#define ACR_CUDA(x)                                  \
+  do {                                               \
+    cudaError_t e_ = (x);                            \
+    if (e_ != cudaSuccess) throw ::acr::CudaError{e_, #x};  \
+  } while (0)
+
+// ------------------------------------------------------------ setup kernels
+// Grouped small GEMMs of a plan stage: one CTA per (group, plane).
+template <typename T>
+void launch_ggemm(const Plan& pl, int gbeg, int gend, T* const* d_tab, const int* const* d_rtab,
+                  int P, const double* d_coefs, cudaStream_t st);
+
+// Pivoted-Cholesky orthonormalisation cores (FP64) of plan targets.
+template <typename T>
+void launch_pchol(const Plan& pl, int tbeg, int tend, bool truncate, double tau,
+                  T* const* d_tab, int* const* d_rtab, int P, cudaStream_t st);
+
+// Jacobi eigen cores (FP64) of plan targets; writes the kept ranks into
+// the rank buffer of role c_role and raises ERR_RANKCAP above kc.
+template <typename T>
+void launch_eig(const Plan& pl, int tbeg, int tend, double eps, int kc, int c_role,
+                T* const* d_tab, int* const* d_rtab, int P, int* d_err, cudaStream_t st);
+
+// In-place FP64 Gauss-Jordan inverse (partial pivoting) of one dense
+// lsz x lsz leaf in each of P H-matrices (base pointers in d_dense[p]).
+template <typename T>
+void launch_leaf_inv(T* const* d_dense, int64_t off, int lsz, int P, int* d_err, cudaStream_t st);
+
+// Device copies of the plane structure arrays.
+struct StructDev {
+  const int* perm = nullptr;       // n*n cluster-order permutation
+  const int* dinfo = nullptr;      // 2 per dense leaf: row start, col start
+  const int* linfo = nullptr;      // 4 per low-rank leaf: rows, cols, row start, col start
+  const int64_t* row0 = nullptr;   // nl+1 prefix sums of low-rank rows
+  const int64_t* col0 = nullptr;   // nl+1 prefix sums of low-rank cols
+  const int* cpl = nullptr;        // stencil couplings inside admissible blocks (i, j, dir)
+  const int* cptr = nullptr;       // nl+1 CSR pointers into cpl
+  int nd = 0, nl = 0, lsz = 0;
+};
+
+// out = sgn * diag(r) X diag(c) for P H-matrices (exact scaling).
+template <typename T>
+void launch_hscale(const StructDev& sd, T* const* out_dense, T* const* out_U, T* const* out_V,
+                   int* const* out_rank, T* const* x_dense, T* const* x_U, T* const* x_V,
+                   const int* const* x_rank, const double* const* rowscale,
+                   const double* const* colscale, double sgn, int kc, int P, cudaStream_t st);
+
+// Dense leaves and exact sparse low-rank factors of the plane blocks D_k of
+// the 7-point operator, one H-matrix per plane listed in d_planes.
+template <typename T>
+void launch_plane_to_h(const StructDev& sd, const double* coef, int n, const int* d_planes, int P,
+                       T* const* dense, T* const* U, T* const* V, int* const* rank, int kc,
+                       cudaStream_t st);
+
+// ------------------------------------------------------------ apply kernels
+struct MatvecDev {
+  const int32_t *d_ptr, *d_leaf, *d_col, *l_ptr, *l_leaf, *l_rowoff;
+  const int32_t *dt_ptr, *dt_leaf, *dt_row, *lt_ptr, *lt_leaf, *lt_coloff;
+  const int32_t *lr_m, *lr_n, *lr_t0, *lr_s0;
+  const int64_t *lr_row0, *lr_col0;
+  int nchunks, lsz, nl, kc;
+};
+
+// y_p = beta*y_p + alpha*op(H_p) x_p for P planes; op = H or H^T.
+// tv: scratch of P*nl*kc doubles.  Null H_p skips the plane (y_p scaled
+// by beta only if beta != 1).
+template <typename T>
+void launch_hmatvec(const MatvecDev& mv, T* const* dense, T* const* U, T* const* V,
+                    const int* const* rank, const double* const* x, double* const* y,
+                    double alpha, double beta, bool trans, double* tv, int P, cudaStream_t st);
+
+void launch_permute(const double* in, double* out, const int* perm, int n2, int nplanes,
+                    bool to_cluster, cudaStream_t st);
+// y_p -= a_p .* x_p + b_p .* z_p (diagonal couplings; null pointers skipped)
+void launch_diag_update(double* const* y, const double* const* a, const double* const* x,
+                        const double* const* b, const double* const* z, int n2, int P,
+                        double sgn, cudaStream_t st);
+void launch_copy_planes(double* const* dst, const double* const* src, int n2, int P,
+                        cudaStream_t st);
+
+// ------------------------------------------------------------ Krylov
+void launch_stencil_poisson(const double* kappa, double* coef, int n, cudaStream_t st);
+void launch_stencil_codi(const double* beta, double* coef, int n, cudaStream_t st);
+void launch_spmv(const double* coef, const double* x, double* y, int n, cudaStream_t st);
+// out[0..nv) = <V_j, w>, V_j = V + j*ldv; deterministic two-stage reduction
+void launch_multidot(const double* V, int64_t ldv, int nv, const double* w, int64_t N,
+                     double* partial, double* out, cudaStream_t st);
+// w += sum_j coef[j] * V_j   (coef on device)
+void launch_multiaxpy(double* w, const double* V, int64_t ldv, int nv, const double* coef,
+                      double scale, int64_t N, cudaStream_t st);
+void launch_axpby(double* y, const double* x, double a, double b, int64_t N, cudaStream_t st);
+void launch_axpby_dev(double* y, const double* x, const double* a, double asgn, double b,
+                      int64_t N, cudaStream_t st);
+
+}  // namespace acr

@@ -1,0 +1,722 @@
+// Setup kernels of the ACR engine (sm_103a):
+//  * k_ggemm   -- grouped small GEMMs of a plan stage (phase 1 factors,
+//                 dense-leaf sums, sketches, Grams, recomposition);
+//  * k_pchol   -- FP64 pivoted Cholesky of a sketch Gram: orthonormal basis
+//                 transform of the range finder;
+//  * k_eig     -- FP64 cyclic Jacobi of the small recompression core, rank
+//                 selection sigma_i > eps * sigma_1 (Sec. 4.3 H_eps);
+//  * k_leaf_inv-- FP64 Gauss-Jordan inverse with partial pivoting of a dense
+//                 diagonal leaf (the leaves of the recursive H-inverse);
+//  * k_hscale  -- exact diagonal scalings diag(r) X diag(c) (first CR level,
+//                 where the plane couplings are diagonal);
+//  * k_plane_dense / k_plane_lr -- H-format of a 7-point plane block.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "acr_internal.h"
+
+namespace acr {
+
+namespace {
+
+constexpr int TILE = 64;
+constexpr int KT = 16;
+constexpr int NT = 256;
+
+__device__ __forceinline__ int dimv(int st, int rb, int ri, const int* const* rtab, int P, int p) {
+  if (rb < 0) return st;
+  const int* r = rtab[rb * P + p];
+  return r ? r[ri] : 0;
+}
+
+// counter-based hash -> uniform in [-1, 1) (SplitMix64 finaliser)
+__device__ __forceinline__ double omega(uint32_t seed, uint32_t row, uint32_t col) {
+  uint64_t z = ((uint64_t)seed << 40) ^ ((uint64_t)row << 16) ^ (uint64_t)col;
+  z += 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  return (double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0;
+}
+
+template <typename T, typename Acc>
+__global__ void __launch_bounds__(NT) k_ggemm(const GGroup* __restrict__ groups,
+                                              const GItem* __restrict__ items,
+                                              T* const* __restrict__ tab,
+                                              const int* const* __restrict__ rtab, int P,
+                                              int gbase, const double* __restrict__ coefs) {
+  const int p = blockIdx.y;
+  const GGroup G = groups[gbase + blockIdx.x];
+  T* C = tab[G.cbuf * P + p];
+  if (!C) return;
+  const int m = dimv(G.m_st, G.m_rb, G.m_ri, rtab, P, p);
+  const int n = dimv(G.n_st, G.n_rb, G.n_ri, rtab, P, p);
+  if (m <= 0 || n <= 0) return;
+  C += G.coff;
+  __shared__ Acc As[KT][TILE + 1];
+  __shared__ Acc Bs[KT][TILE + 1];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  Acc acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = Acc(0);
+
+  for (int it = G.ib; it < G.ie; ++it) {
+    const GItem I = items[it];
+    if (I.guard0 >= 0 && !tab[I.guard0 * P + p]) continue;
+    if (I.guard1 >= 0 && !tab[I.guard1 * P + p]) continue;
+    const T* A = nullptr;
+    const T* B = nullptr;
+    if (I.abuf >= 0) {
+      A = tab[I.abuf * P + p];
+      if (!A) continue;
+      A += I.aoff;
+    }
+    if (I.bbuf >= 0) {
+      B = tab[I.bbuf * P + p];
+      if (!B) continue;
+      B += I.boff;
+    }
+    const int k = dimv(I.k_st, I.k_rb, I.k_ri, rtab, P, p);
+    const int rows = dimv(I.r_st, I.r_rb, I.r_ri, rtab, P, p);
+    if (k <= 0 || rows <= 0) continue;
+    const Acc cf = (Acc)coefs[I.coef];
+    const int r0 = I.row_off;
+    if (I.aflags & FL_IDENT) {   // C(r0+i, j) += cf * B(i, j)
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        const int i = ty + 16 * a - r0;
+        if (i < 0 || i >= rows) continue;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          const int j = tx + 16 * b;
+          if (j < n) acc[a][b] += cf * (Acc)B[i + (int64_t)j * I.ldb];
+        }
+      }
+      continue;
+    }
+    if (I.bflags & FL_IDENT) {   // C(r0+i, j) += cf * A(i, j)
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        const int i = ty + 16 * a - r0;
+        if (i < 0 || i >= rows) continue;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          const int j = tx + 16 * b;
+          if (j < n) acc[a][b] += cf * (Acc)A[i + (int64_t)j * I.lda];
+        }
+      }
+      continue;
+    }
+    const bool at = I.aflags & FL_T;
+    const bool bt = I.bflags & FL_T;
+    const bool bo = I.bflags & FL_OMEGA;
+    for (int k0 = 0; k0 < k; k0 += KT) {
+      // A tile: As[kk][i] = cf * op(A)(i - r0, k0 + kk)
+      for (int e = threadIdx.x; e < KT * TILE; e += NT) {
+        int i, kk;
+        if (at) { kk = e % KT; i = e / KT; } else { i = e % TILE; kk = e / TILE; }
+        const int ia = i - r0, ka = k0 + kk;
+        Acc v = Acc(0);
+        if (ia >= 0 && ia < rows && ka < k)
+          v = at ? (Acc)A[ka + (int64_t)ia * I.lda] : (Acc)A[ia + (int64_t)ka * I.lda];
+        As[kk][i] = cf * v;
+      }
+      // B tile: Bs[kk][j] = op(B)(k0 + kk, j)
+      for (int e = threadIdx.x; e < KT * TILE; e += NT) {
+        int j, kk;
+        if (bt) { j = e % TILE; kk = e / TILE; } else { kk = e % KT; j = e / KT; }
+        const int kb = k0 + kk;
+        Acc v = Acc(0);
+        if (kb < k && j < n) {
+          if (bo) v = (Acc)omega((uint32_t)I.seed, (uint32_t)(I.omega_row0 + kb), (uint32_t)j);
+          else v = bt ? (Acc)B[j + (int64_t)kb * I.ldb] : (Acc)B[kb + (int64_t)j * I.ldb];
+        }
+        Bs[kk][j] = v;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int kk = 0; kk < KT; ++kk) {
+        Acc av[4], bv[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) av[a] = As[kk][ty + 16 * a];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) bv[b] = Bs[kk][tx + 16 * b];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) acc[a][b] += av[a] * bv[b];
+      }
+      __syncthreads();
+    }
+  }
+  const Acc beta = G.beta >= 0 ? (Acc)coefs[G.beta] : Acc(0);
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int i = ty + 16 * a;
+    if (i >= m) continue;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int j = tx + 16 * b;
+      if (j >= n) continue;
+      T* c = C + i + (int64_t)j * G.ldc;
+      Acc v = acc[a][b];
+      if (G.beta >= 0) v += beta * (Acc)(*c);
+      *c = (T)v;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- cores
+constexpr int CMAX = 64;   // largest sketch / core dimension
+
+__device__ __forceinline__ int block_argmax(double v, int idx, double* sv, int* si) {
+  // index of the largest v over the block (idx < 0: no candidate; ties -> smaller index)
+  const int t = threadIdx.x;
+  sv[t] = v; si[t] = idx;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (t < s) {
+      const double o = sv[t + s];
+      const int oi = si[t + s];
+      if (oi >= 0 && (si[t] < 0 || o > sv[t] || (o == sv[t] && oi < si[t]))) {
+        sv[t] = o; si[t] = oi;
+      }
+    }
+    __syncthreads();
+  }
+  const int r = si[0];
+  __syncthreads();
+  return r;
+}
+
+// Pivoted Cholesky of G (pd x pd): G = P L L^T P^T, stop when the largest
+// remaining diagonal <= tau^2 * max diag(G) (truncating pass).  Writes
+// T (p x r, ld p) with Q = Y T orthonormal, and r.
+template <typename T>
+__global__ void __launch_bounds__(NT) k_pchol(const TInfo* __restrict__ tis, int tbase, bool truncate,
+                                              double tau, T* const* __restrict__ tab,
+                                              int* const* __restrict__ rtab, int P, int scr_buf,
+                                              int scr_rbuf) {
+  const int p = blockIdx.y;
+  const TInfo ti = tis[tbase + blockIdx.x];
+  T* scr = tab[scr_buf * P + p];
+  int* rs = rtab[scr_rbuf * P + p];
+  if (!scr || !rs) return;
+  const int ld = ti.p;
+  const int pd = truncate ? ti.p : rs[ti.r_ri];
+  extern __shared__ double dsm[];
+  double (*L)[CMAX + 1] = reinterpret_cast<double (*)[CMAX + 1]>(dsm);
+  double (*F)[CMAX + 1] = reinterpret_cast<double (*)[CMAX + 1]>(dsm + CMAX * (CMAX + 1));
+  __shared__ double d[CMAX];
+  __shared__ int piv[CMAX];
+  __shared__ double sv[NT];
+  __shared__ int si[NT];
+  const T* G = scr + ti.g_off;
+  T* Tm = scr + ti.t_off;
+  for (int e = threadIdx.x; e < pd * pd; e += NT) {
+    int i = e % pd, j = e / pd;
+    L[i][j] = (double)G[i + (int64_t)j * ld];
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < pd; i += NT) { d[i] = L[i][i]; piv[i] = i; }
+  __syncthreads();
+  // scale reference: largest diagonal
+  double dm = 0;
+  for (int i = threadIdx.x; i < pd; i += NT) dm = fmax(dm, d[i]);
+  sv[threadIdx.x] = dm;
+  __syncthreads();
+  for (int s = NT / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) sv[threadIdx.x] = fmax(sv[threadIdx.x], sv[threadIdx.x + s]);
+    __syncthreads();
+  }
+  const double dmax = sv[0];
+  __syncthreads();
+  const double tol = truncate ? tau * tau * dmax : 1e-30 * dmax;
+  int r = 0;
+  // F: lower factor in pivoted order
+  for (int e = threadIdx.x; e < CMAX * (CMAX + 1); e += NT) (&F[0][0])[e] = 0.0;
+  __syncthreads();
+  for (int j = 0; j < pd; ++j) {
+    double best = -1.0;
+    int bi = -1;
+    for (int i = j + threadIdx.x; i < pd; i += NT) {
+      const double v = d[piv[i]];
+      if (v > best) { best = v; bi = i; }
+    }
+    const int q = block_argmax(best, bi, sv, si);
+    const double dq = (q >= 0) ? d[piv[q]] : 0.0;
+    if (q < 0 || dq <= tol || dq <= 0.0) {
+      // truncating pass: the rest of range(Y) is below tau; re-orthogonalising
+      // pass: keep the dimension, the remaining directions get zero columns
+      if (!truncate) r = pd;
+      break;
+    }
+    if (threadIdx.x == 0) {
+      const int tmp = piv[j]; piv[j] = piv[q]; piv[q] = tmp;
+    }
+    // the rows of the partial factor follow the pivot interchange
+    if (q != j)
+      for (int l = threadIdx.x; l < j; l += NT) {
+        const double t = F[j][l]; F[j][l] = F[q][l]; F[q][l] = t;
+      }
+    __syncthreads();
+    const double ljj = sqrt(d[piv[j]]);
+    for (int i = j + threadIdx.x; i < pd; i += NT) {
+      double sum = L[piv[i]][piv[j]];
+      for (int l = 0; l < j; ++l) sum -= F[i][l] * F[j][l];
+      F[i][j] = (i == j) ? ljj : sum / ljj;
+    }
+    __syncthreads();
+    for (int i = j + 1 + threadIdx.x; i < pd; i += NT) d[piv[i]] -= F[i][j] * F[i][j];
+    __syncthreads();
+    if (threadIdx.x == 0) d[piv[j]] = 0.0;
+    __syncthreads();
+    r = j + 1;
+  }
+  // inverse of the r x r lower factor (columns with zero diagonal give zero)
+  // Linv stored in L (reuse): solve F Linv = I column by column (thread per column)
+  __syncthreads();
+  for (int c = threadIdx.x; c < r; c += NT) {
+    for (int i = 0; i < r; ++i) {
+      double s = (i == c) ? 1.0 : 0.0;
+      for (int l = c; l < i; ++l) s -= F[i][l] * L[l][c];
+      L[i][c] = (F[i][i] != 0.0 && i >= c) ? s / F[i][i] : 0.0;
+    }
+  }
+  __syncthreads();
+  // T (ld, rows pd): T[piv[j]][c] = Linv[c][j]  (Linv^T), other rows 0
+  for (int e = threadIdx.x; e < pd * r; e += NT) {
+    int i = e % pd, c = e / pd;
+    Tm[i + (int64_t)c * ld] = (T)0;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < r * r; e += NT) {
+    int j = e % r, c = e / r;
+    Tm[piv[j] + (int64_t)c * ld] = (T)(j <= c ? L[c][j] : 0.0);
+  }
+  if (threadIdx.x == 0) rs[ti.r_ri] = r;
+}
+
+// Cyclic Jacobi (round-robin parallel order) on the r x r symmetric core H.
+template <typename T>
+__global__ void __launch_bounds__(NT) k_eig(const TInfo* __restrict__ tis, int tbase, double eps,
+                                            int kc, int c_rbuf, T* const* __restrict__ tab,
+                                            int* const* __restrict__ rtab, int P, int scr_buf,
+                                            int scr_rbuf, int* err) {
+  const int p = blockIdx.y;
+  const TInfo ti = tis[tbase + blockIdx.x];
+  T* scr = tab[scr_buf * P + p];
+  int* rs = rtab[scr_rbuf * P + p];
+  int* crank = rtab[c_rbuf * P + p];
+  if (!scr || !rs || !crank) return;
+  const int r = rs[ti.r_ri];
+  const int ld = ti.p;
+  if (r <= 0) {
+    if (threadIdx.x == 0) crank[ti.c_leaf] = 0;
+    return;
+  }
+  extern __shared__ double dsm[];
+  double (*A)[CMAX + 1] = reinterpret_cast<double (*)[CMAX + 1]>(dsm);
+  double (*V)[CMAX + 1] = reinterpret_cast<double (*)[CMAX + 1]>(dsm + CMAX * (CMAX + 1));
+  __shared__ double cs[CMAX / 2 + 1], sn[CMAX / 2 + 1];
+  __shared__ int pp[CMAX / 2 + 1], qq[CMAX / 2 + 1];
+  __shared__ double red[NT];
+  __shared__ int order[CMAX];
+  __shared__ double lam[CMAX];
+  __shared__ int kkeep;
+  const T* H = scr + ti.h_off;
+  T* W = scr + ti.w_off;
+  for (int e = threadIdx.x; e < r * r; e += NT) {
+    int i = e % r, j = e / r;
+    A[i][j] = 0.5 * ((double)H[i + (int64_t)j * ld] + (double)H[j + (int64_t)i * ld]);
+    V[i][j] = (i == j) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  const int nn = (r + 1) & ~1;   // even number of players (r may get a dummy)
+  const int npair = nn / 2;
+  for (int sweep = 0; sweep < 40; ++sweep) {
+    // off-diagonal and total norms
+    double off = 0, tot = 0;
+    for (int e = threadIdx.x; e < r * r; e += NT) {
+      int i = e % r, j = e / r;
+      double v = A[i][j] * A[i][j];
+      tot += v;
+      if (i != j) off += v;
+    }
+    red[threadIdx.x] = off;
+    __syncthreads();
+    for (int s = NT / 2; s > 0; s >>= 1) {
+      if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+      __syncthreads();
+    }
+    double offs = red[0];
+    __syncthreads();
+    red[threadIdx.x] = tot;
+    __syncthreads();
+    for (int s = NT / 2; s > 0; s >>= 1) {
+      if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+      __syncthreads();
+    }
+    double tots = red[0];
+    __syncthreads();
+    if (offs <= 1e-30 * tots || r == 1) break;
+    for (int round = 0; round < nn - 1; ++round) {
+      // circle method: player 0 fixed, others rotate
+      for (int k = threadIdx.x; k < npair; k += NT) {
+        const int pa = k, pb = nn - 1 - k;
+        const int a = (pa == 0) ? 0 : 1 + ((pa - 1 + round) % (nn - 1));
+        const int b = 1 + ((pb - 1 + round) % (nn - 1));
+        int lo = a < b ? a : b, hi = a < b ? b : a;
+        pp[k] = lo; qq[k] = hi;
+        double c = 1.0, s = 0.0;
+        if (hi < r) {
+          double apq = A[lo][hi];
+          if (apq != 0.0) {
+            double tau_ = (A[hi][hi] - A[lo][lo]) / (2.0 * apq);
+            double t = (tau_ >= 0 ? 1.0 : -1.0) / (fabs(tau_) + sqrt(1.0 + tau_ * tau_));
+            c = 1.0 / sqrt(1.0 + t * t);
+            s = t * c;
+          }
+        }
+        cs[k] = c; sn[k] = s;
+      }
+      __syncthreads();
+      // column rotations of A and V
+      for (int e = threadIdx.x; e < npair * r; e += NT) {
+        int k = e / r, i = e % r;
+        int a = pp[k], b = qq[k];
+        if (b >= r) continue;
+        double c = cs[k], s = sn[k];
+        double x = A[i][a], y = A[i][b];
+        A[i][a] = c * x - s * y;
+        A[i][b] = s * x + c * y;
+        double vx = V[i][a], vy = V[i][b];
+        V[i][a] = c * vx - s * vy;
+        V[i][b] = s * vx + c * vy;
+      }
+      __syncthreads();
+      // row rotations of A
+      for (int e = threadIdx.x; e < npair * r; e += NT) {
+        int k = e / r, j = e % r;
+        int a = pp[k], b = qq[k];
+        if (b >= r) continue;
+        double c = cs[k], s = sn[k];
+        double x = A[a][j], y = A[b][j];
+        A[a][j] = c * x - s * y;
+        A[b][j] = s * x + c * y;
+      }
+      __syncthreads();
+    }
+  }
+  // sort eigenvalues descending (rank by counting; ties by index)
+  for (int i = threadIdx.x; i < r; i += NT) lam[i] = A[i][i];
+  __syncthreads();
+  for (int i = threadIdx.x; i < r; i += NT) {
+    int pos = 0;
+    for (int j = 0; j < r; ++j)
+      if (lam[j] > lam[i] || (lam[j] == lam[i] && j < i)) ++pos;
+    order[pos] = i;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double l1 = lam[order[0]];
+    int k = 0;
+    if (l1 > 0.0) {
+      double s1 = sqrt(l1);
+      for (int j = 0; j < r; ++j) {
+        double lj = lam[order[j]];
+        if (lj > 0.0 && sqrt(lj) > eps * s1) ++k;
+        else break;
+      }
+    }
+    if (k > kc) {
+      atomicOr(err, ERR_RANKCAP);
+      k = kc;
+    }
+    kkeep = k;
+    crank[ti.c_leaf] = k;
+  }
+  __syncthreads();
+  const int k = kkeep;
+  for (int e = threadIdx.x; e < r * k; e += NT) {
+    int i = e % r, j = e / r;
+    W[i + (int64_t)j * ld] = (T)V[i][order[j]];
+  }
+}
+
+// In-place Gauss-Jordan inverse with partial pivoting, FP64, n <= 64.
+template <typename T>
+__global__ void __launch_bounds__(NT) k_leaf_inv(T* const* __restrict__ dense, int64_t off, int n,
+                                                 int* err) {
+  const int p = blockIdx.x;
+  T* Ap = dense[p];
+  if (!Ap) return;
+  Ap += off;
+  __shared__ double A[CMAX][CMAX + 1];
+  __shared__ int piv[CMAX];
+  __shared__ double sv[NT];
+  __shared__ int si[NT];
+  __shared__ double rowk[CMAX];
+  __shared__ double colk[CMAX];
+  for (int e = threadIdx.x; e < n * n; e += NT) A[e % n][e / n] = (double)Ap[e];
+  __syncthreads();
+  bool bad = false;
+  for (int k = 0; k < n; ++k) {
+    double best = -1.0;
+    int bi = -1;
+    for (int i = k + threadIdx.x; i < n; i += NT) {
+      double v = fabs(A[i][k]);
+      if (v > best) { best = v; bi = i; }
+    }
+    int q = block_argmax(best, bi, sv, si);
+    if (threadIdx.x == 0) piv[k] = q;
+    if (q < 0 || A[q][k] == 0.0) { bad = true; break; }
+    // swap rows k and q
+    for (int j = threadIdx.x; j < n; j += NT) {
+      double t = A[k][j]; A[k][j] = A[q][j]; A[q][j] = t;
+    }
+    __syncthreads();
+    const double pinv = 1.0 / A[k][k];
+    for (int j = threadIdx.x; j < n; j += NT) {
+      rowk[j] = (j == k) ? pinv : A[k][j] * pinv;
+      colk[j] = A[j][k];
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < n * n; e += NT) {
+      int i = e % n, j = e / n;
+      if (i == k) continue;
+      const double f = colk[i];
+      A[i][j] = (j == k) ? -f * pinv : A[i][j] - f * rowk[j];
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < n; j += NT) A[k][j] = rowk[j];
+    __syncthreads();
+  }
+  if (bad) {
+    if (threadIdx.x == 0) atomicOr(err, ERR_PIVOT);
+    return;
+  }
+  // undo the row interchanges as column swaps, last first
+  for (int k = n - 1; k >= 0; --k) {
+    int q = piv[k];
+    if (q != k)
+      for (int i = threadIdx.x; i < n; i += NT) {
+        double t = A[i][k]; A[i][k] = A[i][q]; A[i][q] = t;
+      }
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < n * n; e += NT) Ap[e] = (T)A[e % n][e / n];
+}
+
+// out = sgn * diag(r) X diag(c): dense part
+template <typename T>
+__global__ void k_hscale_dense(T* const* __restrict__ od, T* const* __restrict__ xd,
+                               const double* const* __restrict__ rsc,
+                               const double* const* __restrict__ csc,
+                               const int* __restrict__ dinfo, int lsz, double sgn) {
+  const int d = blockIdx.x, p = blockIdx.y;
+  T* o = od[p];
+  const T* x = xd[p];
+  const double* r = rsc[p];
+  const double* c = csc[p];
+  if (!o || !x) return;
+  const int t0 = dinfo[2 * d], s0 = dinfo[2 * d + 1];
+  const int64_t off = (int64_t)d * lsz * lsz;
+  for (int e = threadIdx.x; e < lsz * lsz; e += blockDim.x) {
+    int i = e % lsz, j = e / lsz;
+    o[off + e] = (T)(sgn * r[t0 + i] * (double)x[off + e] * c[s0 + j]);
+  }
+}
+
+template <typename T>
+__global__ void k_hscale_lr(T* const* __restrict__ oU, T* const* __restrict__ oV,
+                            int* const* __restrict__ orank, T* const* __restrict__ xU,
+                            T* const* __restrict__ xV, const int* const* __restrict__ xrank,
+                            const double* const* __restrict__ rsc,
+                            const double* const* __restrict__ csc, const int* __restrict__ linfo,
+                            const int64_t* __restrict__ row0, const int64_t* __restrict__ col0,
+                            int kc, double sgn) {
+  const int l = blockIdx.x, p = blockIdx.y;
+  if (!oU[p] || !xU[p]) return;
+  const int k = xrank[p][l];
+  const int m = linfo[4 * l], n = linfo[4 * l + 1], t0 = linfo[4 * l + 2], s0 = linfo[4 * l + 3];
+  const double* r = rsc[p];
+  const double* c = csc[p];
+  T* u = oU[p] + row0[l] * kc;
+  T* v = oV[p] + col0[l] * kc;
+  const T* xu = xU[p] + row0[l] * kc;
+  const T* xv = xV[p] + col0[l] * kc;
+  for (int e = threadIdx.x; e < m * k; e += blockDim.x) {
+    int i = e % m;
+    u[e] = (T)(sgn * r[t0 + i] * (double)xu[e]);
+  }
+  for (int e = threadIdx.x; e < n * k; e += blockDim.x) {
+    int j = e % n;
+    v[e] = (T)(c[s0 + j] * (double)xv[e]);
+  }
+  if (threadIdx.x == 0) orank[p][l] = k;
+}
+
+// D_k dense leaves from the stencil: leaf rows/cols in cluster order.
+template <typename T>
+__global__ void k_plane_dense(const double* __restrict__ coef, int n, const int* __restrict__ planes,
+                              T* const* __restrict__ dense, const int* __restrict__ perm,
+                              const int* __restrict__ dinfo, int lsz) {
+  const int d = blockIdx.x, pi = blockIdx.y;
+  T* o = dense[pi];
+  if (!o) return;
+  const int64_t N = (int64_t)n * n * n;
+  const int64_t base = (int64_t)planes[pi] * n * n;
+  const int t0 = dinfo[2 * d], s0 = dinfo[2 * d + 1];
+  o += (int64_t)d * lsz * lsz;
+  for (int e = threadIdx.x; e < lsz * lsz; e += blockDim.x) {
+    int i = e % lsz, j = e / lsz;
+    int a = perm[t0 + i], b = perm[s0 + j];
+    int ax = a % n;
+    double v = 0.0;
+    if (a == b) v = coef[0 * N + base + a];
+    else if (b == a - 1 && ax > 0) v = coef[1 * N + base + a];
+    else if (b == a + 1 && ax < n - 1) v = coef[2 * N + base + a];
+    else if (b == a - n) v = coef[3 * N + base + a];
+    else if (b == a + n) v = coef[4 * N + base + a];
+    o[e] = (T)v;
+  }
+}
+
+// exact sparse low-rank factors of admissible blocks of D_k: one rank-one
+// term per stencil coupling (row i, col j, direction d)
+template <typename T>
+__global__ void k_plane_lr(const double* __restrict__ coef, int n, const int* __restrict__ planes,
+                           T* const* __restrict__ U, T* const* __restrict__ V,
+                           int* const* __restrict__ rank, const int* __restrict__ perm,
+                           const int* __restrict__ cpl, const int* __restrict__ cptr,
+                           const int* __restrict__ linfo, const int64_t* __restrict__ row0,
+                           const int64_t* __restrict__ col0, int kc) {
+  const int l = blockIdx.x, pi = blockIdx.y;
+  if (!U[pi]) return;
+  const int64_t N = (int64_t)n * n * n;
+  const int64_t base = (int64_t)planes[pi] * n * n;
+  const int m = linfo[4 * l], nn = linfo[4 * l + 1], t0 = linfo[4 * l + 2];
+  const int c0 = cptr[l], c1 = cptr[l + 1];
+  const int k = c1 - c0;
+  T* u = U[pi] + row0[l] * kc;
+  T* v = V[pi] + col0[l] * kc;
+  for (int e = threadIdx.x; e < m * k; e += blockDim.x) u[e] = (T)0;
+  for (int e = threadIdx.x; e < nn * k; e += blockDim.x) v[e] = (T)0;
+  __syncthreads();
+  for (int q = threadIdx.x; q < k; q += blockDim.x) {
+    int i = cpl[3 * (c0 + q)], j = cpl[3 * (c0 + q) + 1], dir = cpl[3 * (c0 + q) + 2];
+    int a = perm[t0 + i];
+    u[i + (int64_t)q * m] = (T)coef[(int64_t)dir * N + base + a];
+    v[j + (int64_t)q * nn] = (T)1;
+  }
+  if (threadIdx.x == 0) rank[pi][l] = k;
+}
+
+}  // namespace
+
+template <typename T>
+void launch_ggemm(const Plan& pl, int gbeg, int gend, T* const* d_tab, const int* const* d_rtab,
+                  int P, const double* d_coefs, cudaStream_t st) {
+  int ng = gend - gbeg;
+  if (ng <= 0 || P <= 0) return;
+  using Acc = T;
+  const int maxg = 65535;
+  for (int g0 = 0; g0 < ng; g0 += maxg) {
+    dim3 grid(std::min(maxg, ng - g0), P);
+    k_ggemm<T, Acc><<<grid, NT, 0, st>>>((const GGroup*)pl.d_groups, (const GItem*)pl.d_items,
+                                         d_tab, d_rtab, P, gbeg + g0, d_coefs);
+  }
+  ACR_CUDA(cudaGetLastError());
+}
+
+template <typename T>
+void launch_pchol(const Plan& pl, int tbeg, int tend, bool truncate, double tau, T* const* d_tab,
+                  int* const* d_rtab, int P, cudaStream_t st) {
+  int nt = tend - tbeg;
+  if (nt <= 0 || P <= 0) return;
+  const size_t smem = 2 * CMAX * (CMAX + 1) * sizeof(double);
+  ACR_CUDA(cudaFuncSetAttribute(k_pchol<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  for (int t0 = 0; t0 < nt; t0 += 65535) {
+    dim3 grid(std::min(65535, nt - t0), P);
+    k_pchol<T><<<grid, NT, smem, st>>>((const TInfo*)pl.d_targets, tbeg + t0, truncate, tau, d_tab,
+                                    d_rtab, P, 3 * pl.nroles, pl.nroles);
+  }
+  ACR_CUDA(cudaGetLastError());
+}
+
+template <typename T>
+void launch_eig(const Plan& pl, int tbeg, int tend, double eps, int kc, int c_role,
+                T* const* d_tab, int* const* d_rtab, int P, int* d_err, cudaStream_t st) {
+  int nt = tend - tbeg;
+  if (nt <= 0 || P <= 0) return;
+  const size_t smem = 2 * CMAX * (CMAX + 1) * sizeof(double);
+  ACR_CUDA(cudaFuncSetAttribute(k_eig<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  for (int t0 = 0; t0 < nt; t0 += 65535) {
+    dim3 grid(std::min(65535, nt - t0), P);
+    k_eig<T><<<grid, NT, smem, st>>>((const TInfo*)pl.d_targets, tbeg + t0, eps, kc, c_role, d_tab,
+                                  d_rtab, P, 3 * pl.nroles, pl.nroles, d_err);
+  }
+  ACR_CUDA(cudaGetLastError());
+}
+
+template <typename T>
+void launch_leaf_inv(T* const* d_dense, int64_t off, int lsz, int P, int* d_err, cudaStream_t st) {
+  if (P <= 0) return;
+  k_leaf_inv<T><<<P, NT, 0, st>>>(d_dense, off, lsz, d_err);
+  ACR_CUDA(cudaGetLastError());
+}
+
+template <typename T>
+void launch_hscale(const StructDev& sd, T* const* out_dense, T* const* out_U, T* const* out_V,
+                   int* const* out_rank, T* const* x_dense, T* const* x_U, T* const* x_V,
+                   const int* const* x_rank, const double* const* rowscale,
+                   const double* const* colscale, double sgn, int kc, int P, cudaStream_t st) {
+  if (P <= 0) return;
+  if (sd.nd > 0)
+    k_hscale_dense<T><<<dim3(sd.nd, P), 256, 0, st>>>(out_dense, x_dense, rowscale, colscale,
+                                                      sd.dinfo, sd.lsz, sgn);
+  if (sd.nl > 0)
+    k_hscale_lr<T><<<dim3(sd.nl, P), 256, 0, st>>>(out_U, out_V, out_rank, x_U, x_V, x_rank,
+                                                   rowscale, colscale, sd.linfo, sd.row0,
+                                                   sd.col0, kc, sgn);
+  ACR_CUDA(cudaGetLastError());
+}
+
+template <typename T>
+void launch_plane_to_h(const StructDev& sd, const double* coef, int n, const int* d_planes, int P,
+                       T* const* dense, T* const* U, T* const* V, int* const* rank, int kc,
+                       cudaStream_t st) {
+  if (P <= 0) return;
+  if (sd.nd > 0)
+    k_plane_dense<T><<<dim3(sd.nd, P), 256, 0, st>>>(coef, n, d_planes, dense, sd.perm, sd.dinfo,
+                                                     sd.lsz);
+  if (sd.nl > 0)
+    k_plane_lr<T><<<dim3(sd.nl, P), 256, 0, st>>>(coef, n, d_planes, U, V, rank, sd.perm, sd.cpl,
+                                                  sd.cptr, sd.linfo, sd.row0, sd.col0, kc);
+  ACR_CUDA(cudaGetLastError());
+}
+
+#define ACR_INST(T)                                                                              \
+  template void launch_ggemm<T>(const Plan&, int, int, T* const*, const int* const*, int,        \
+                                const double*, cudaStream_t);                                    \
+  template void launch_pchol<T>(const Plan&, int, int, bool, double, T* const*, int* const*, int, \
+                                cudaStream_t);                                                   \
+  template void launch_eig<T>(const Plan&, int, int, double, int, int, T* const*, int* const*,   \
+                              int, int*, cudaStream_t);                                          \
+  template void launch_leaf_inv<T>(T* const*, int64_t, int, int, int*, cudaStream_t);            \
+  template void launch_hscale<T>(const StructDev&, T* const*, T* const*, T* const*, int* const*, \
+                                 T* const*, T* const*, T* const*, const int* const*,             \
+                                 const double* const*, const double* const*, double, int, int,   \
+                                 cudaStream_t);                                                  \
+  template void launch_plane_to_h<T>(const StructDev&, const double*, int, const int*, int,      \
+                                     T* const*, T* const*, T* const*, int* const*, int,          \
+                                     cudaStream_t);
+
+ACR_INST(double)
+ACR_INST(float)
+
+}  // namespace acr
