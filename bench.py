@@ -1,0 +1,371 @@
+"""Benchmark: ACR setup + preconditioned Krylov solve to relative residual 1e-8.
+
+Workload (default): the nonsymmetric convection-diffusion operator
+-Lap u + beta . grad u at n = 128 (2,097,152 unknowns), beta =
+(50,50,50)(1 + 0.5 sin 2 pi x sin 2 pi y), first-order upwind, f ~ U(-1,1)
+(seed 20); ACR with eps = 1e-2, eta = 2, leaf 64, factors in FP32 (the mixed
+form: FP64 leaf inverses, recompression cores and Krylov); FP64
+GMRES(30), right-preconditioned, rtol 1e-8.
+
+One step = acr_setup (coefficients already on the device) + acr_krylov_solve
++ acr_destroy.  `value` is seconds per solve for the whole job: with N
+replicas (one process per GPU, independent solves), value = step time / N.
+
+The JSON line also carries: the FP64 plain form (--fp64-steps, default 1),
+an end-to-end measurement through the public API with host buffers, the
+roofline of the dominant setup kernel (from one extra profiled step), the
+apply's HBM roofline, and the CPU oracle timed on a bounded sample.
+
+--impl reference times the CPU oracle instead (the only reference this
+method has), each step one bounded sample of the same workload.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ACR setup+Krylov s to rel-res 1e-8 at n=128; mixed vs FP64 plain, same GB300"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+
+
+def load_peaks():
+    if os.path.exists(PEAKS_FILE):
+        with open(PEAKS_FILE) as fh:
+            return json.load(fh), "measured"
+    return {"hbm_gbs": FALLBACK_HBM_GBS, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# FP32 CUDA-core peak of the part: 152 SMs x 128 FP32 lanes x 2 flop/FMA
+def fp32_alu_peak_tflops(mhz):
+    return 152 * 128 * 2 * mhz * 1e6 / 1e12
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason sampling while the timed region runs."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu):
+        self.gpu = gpu
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- oracle arm
+def oracle_sample(n_sample=32):
+    """Oracle ACR setup + GMRES(30) on the n_sample instance of the workload.
+
+    Returns (seconds, iterations)."""
+    import numpy as np
+    from inputs import workload
+    from oracle.assembly import stencil_codi, stencil_matrix, plane_blocks
+    from oracle.cr import cr_setup, cr_apply
+    from oracle.hstructure import Structure
+    from oracle.krylov import gmres
+    spec, beta, f = workload("codi_n128", n=n_sample)
+    t0 = time.perf_counter()
+    st = stencil_codi(beta, n_sample)
+    A = stencil_matrix(st, n_sample)
+    D, Ld, Ud = plane_blocks(st, n_sample)
+    F = cr_setup(D, Ld, Ud, Structure(n_sample, 2.0, spec["leaf"]), spec["eps"])
+    u, it, hist = gmres(lambda v: A @ v, f, lambda v: cr_apply(F, v), rtol=spec["rtol"],
+                        restart=spec["restart"])
+    dt = time.perf_counter() - t0
+    assert hist[-1] <= spec["rtol"] * 1.0001
+    return dt, it
+
+
+def oracle_scale():
+    """Scale an n=32 oracle time to the n=128 workload.  The oracle keeps
+    every plane block as a dense n^2 x n^2 array, so its setup costs
+    O(n planes x (n^2)^3) = O(n^7); the factor (128/32)^7 is applied."""
+    return (128.0 / 32.0) ** 7
+
+
+def cpu_cores():
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        if os.environ.get(v):
+            return int(os.environ[v])
+    return os.cpu_count()
+
+
+SAMPLE_DESC = ("full oracle ACR setup + GMRES(30) to 1e-8 on the n=32 instance of the same "
+               "recipe (beta field, eps 1e-2, eta 2, leaf 64, seed 20), scaled to n=128 by "
+               "the oracle's O(n^7) dense-plane cost, (128/32)^7")
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    times = []
+    for i in range(args.warmup + args.steps):
+        dt, it = oracle_sample()
+        if i >= args.warmup:
+            times.append(dt)
+    t = sum(times) / len(times)
+    value = t * oracle_scale()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": t * 1000.0, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "codi_n128_acr_gmres30", "n": 128, "eps": 1e-2, "eta": 2.0,
+                       "leaf": 64, "sample": "n=32 oracle solve per step",
+                       "l2": "inputs larger than L2"},
+            "cpu_baseline": {"value": value, "unit": "s", "cores": cpu_cores(), "kind": "oracle",
+                             "sample": SAMPLE_DESC, "sample_seconds": t},
+            "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- GPU arm
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="acr", choices=["acr", "reference"])
+    ap.add_argument("--n", type=int, default=128)
+    ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--rank-cap", type=int, default=24)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+    import paper_1712_08872_gb300 as acr
+    from inputs import workload
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    acr.load_library()
+
+    n = args.n
+    spec, beta, f = workload("codi_n128", n=n)
+    eps, eta, leaf = spec["eps"], 2.0, spec["leaf"]
+    rtol, restart = spec["rtol"], spec["restart"]
+    N = n ** 3
+    beta_d = torch.tensor(beta.ravel(), dtype=torch.float64, device=dev)
+    f_d = torch.tensor(f, dtype=torch.float64, device=dev)
+    coef = torch.empty(7 * N, dtype=torch.float64, device=dev)
+    acr.acr_stencil_codi(n, beta_d, coef)
+    u = torch.zeros(N, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(prec, flags=0):
+        h = acr.acr_setup(n, coef, eps, eta, leaf, prec, args.rank_cap, stream, flags)
+        u.zero_()
+        info, st = acr.acr_krylov_solve(h, coef, acr.ACR_GMRES, restart, rtol, 1000, f_d, u,
+                                        stream, check=False)
+        sinfo = acr.acr_get_setup_info(h)
+        prof = acr.acr_get_profile(h) if flags else None
+        acr.acr_destroy(h)
+        if st != 0:
+            raise RuntimeError("solve failed: " + acr.acr_status_string(st))
+        return info, sinfo, prof
+
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def timed(prec, steps):
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        l0 = acr.acr_launch_count()
+        e0.record(stream)
+        infos = [step(prec) for _ in range(steps)]
+        e1.record(stream)
+        barrier()
+        ms = e0.elapsed_time(e1) / steps
+        launches = (acr.acr_launch_count() - l0) // steps
+        if dist:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, infos, launches
+
+    # warm-up (mixed form)
+    for _ in range(args.warmup):
+        step(acr.ACR_FP32)
+    with ClockSampler(local) as clk:
+        ms, infos, launches = timed(acr.ACR_FP32, args.steps)
+    clocks = clk.summary()
+    solve_info, setup_info, _ = infos[-1]
+
+    # FP64 plain form on the same GPU
+    fp64 = None
+    if args.fp64_steps > 0:
+        ms64, inf64, _ = timed(acr.ACR_FP64, args.fp64_steps)
+        fp64 = {"s": ms64 / 1000.0, "iterations": inf64[-1][0].iterations,
+                "setup_ms": inf64[-1][1].setup_ms, "max_rank": inf64[-1][1].max_rank,
+                "factor_gb": inf64[-1][1].factor_bytes / 1e9}
+
+    # end to end through the public API: pinned host inputs -> device,
+    # assembly, setup, solve, solution -> host
+    e2e = None
+    if args.e2e_steps > 0:
+        beta_h = torch.tensor(beta.ravel(), dtype=torch.float64).pin_memory()
+        f_h = torch.tensor(f, dtype=torch.float64).pin_memory()
+        u_h = torch.empty(N, dtype=torch.float64).pin_memory()
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.e2e_steps):
+            bd = beta_h.to(dev, non_blocking=True)
+            fd = f_h.to(dev, non_blocking=True)
+            cf = torch.empty(7 * N, dtype=torch.float64, device=dev)
+            acr.acr_stencil_codi(n, bd, cf)
+            h = acr.acr_setup(n, cf, eps, eta, leaf, acr.ACR_FP32, args.rank_cap, stream)
+            uu = torch.zeros(N, dtype=torch.float64, device=dev)
+            acr.acr_krylov_solve(h, cf, acr.ACR_GMRES, restart, rtol, 1000, fd, uu, stream)
+            acr.acr_destroy(h)
+            u_h.copy_(uu, non_blocking=True)
+        e1.record(stream)
+        barrier()
+        e2e_s = e0.elapsed_time(e1) / args.e2e_steps / 1000.0
+        e2e = {"value": e2e_s / world, "unit": "s", "h2d_bytes_per_step": 4 * N * 8,
+               "d2h_bytes_per_step": N * 8}
+
+    # roofline: one extra profiled step (CUDA events around every setup launch)
+    _, _, prof = step(acr.ACR_FP32, acr.ACR_FLAG_PROFILE)
+    peaks, peak_src = load_peaks()
+    stats = {k: getattr(prof, k) for k in ("gemm", "orth", "eig", "leaf_inv", "other")}
+    dom = max(stats, key=lambda k: stats[k].ms)
+    mhz = clocks["sm_mhz"] or peaks.get("sm_max_mhz", 2070.0)
+    ds = stats[dom]
+    if dom == "gemm":
+        achieved = ds.flops / (ds.ms / 1000.0) / 1e12
+        peak = fp32_alu_peak_tflops(peaks.get("sm_max_mhz", 2070.0))
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None, "kernel": "k_ggemm<float>",
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock",
+                "launches": ds.launches, "ms_total": ds.ms}
+    else:
+        achieved = ds.flops / (ds.ms / 1000.0) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": None, "unit": "TFLOP/s",
+                "frac": None, "traffic": None, "kernel": dom, "launches": ds.launches,
+                "ms_total": ds.ms}
+    roof["setup_breakdown_ms"] = {k: round(v.ms, 1) for k, v in stats.items()}
+
+    # apply (hot loop of the solve): HBM roofline
+    h = acr.acr_setup(n, coef, eps, eta, leaf, acr.ACR_FP32, args.rank_cap, stream)
+    z = torch.empty_like(f_d)
+    for _ in range(3):
+        acr.acr_apply(h, f_d, z, 1, stream)
+    torch.cuda.synchronize()
+    ea = torch.cuda.Event(enable_timing=True)
+    eb = torch.cuda.Event(enable_timing=True)
+    ea.record(stream)
+    for _ in range(10):
+        acr.acr_apply(h, f_d, z, 1, stream)
+    eb.record(stream)
+    torch.cuda.synchronize()
+    apply_ms = ea.elapsed_time(eb) / 10
+    ainfo = acr.acr_get_setup_info(h)
+    acr.acr_destroy(h)
+    apply_gbs = ainfo.apply_bytes / (apply_ms / 1000.0) / 1e9
+    apply_roof = {"bound": "hbm", "achieved": apply_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                  "frac": apply_gbs / peaks["hbm_gbs"], "ms": apply_ms,
+                  "bytes_per_apply": ainfo.apply_bytes, "peak_source": peak_src}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        dt, it = oracle_sample()
+        cpu = {"value": dt * oracle_scale(), "unit": "s", "cores": cpu_cores(), "kind": "oracle",
+               "sample": SAMPLE_DESC, "sample_seconds": dt}
+
+    value = ms / 1000.0 / world
+    line = {"metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "codi_n128_acr_gmres30", "n": n, "unknowns": N, "eps": eps,
+                       "eta": eta, "leaf": leaf, "rank_cap": args.rank_cap,
+                       "form": "FP32 factors; FP64 leaf inverses, cores and GMRES",
+                       "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "inputs larger than L2 (factors tens of GB)"},
+            "iterations": solve_info.iterations, "rel_residual": solve_info.rel_residual,
+            "setup_s": setup_info.setup_ms / 1000.0, "solve_s": solve_info.solve_ms / 1000.0,
+            "max_rank": setup_info.max_rank, "factor_gb": setup_info.factor_bytes / 1e9,
+            "fp64_plain": fp64,
+            "speedup_vs_fp64": (fp64["s"] / (ms / 1000.0)) if fp64 else None,
+            "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks,
+            "roofline": roof, "apply_roofline": apply_roof, "cpu_baseline": cpu}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -74,9 +74,14 @@ typedef struct {
   double eta;            /* admissibility parameter, > 0 */
   int32_t leaf;          /* n_min: clusters with at most this many points are leaves */
   int32_t precision;     /* acr_precision */
-  int32_t rank_cap;      /* 1..64; 0 selects the default (32) */
-  int32_t reserved;
+  int32_t rank_cap;      /* 1..48; 0 selects the default (32) */
+  int32_t flags;         /* ACR_FLAG_* bits */
 } acr_options;
+
+/* acr_options.flags: record per-kernel-class device time (CUDA events
+ * around every setup launch) and counted arithmetic of the setup, readable
+ * with acr_get_profile.  Adds a small per-launch host cost. */
+#define ACR_FLAG_PROFILE 1
 
 typedef struct {
   int32_t levels;            /* CR levels, ceil(log2 nz) */
@@ -87,8 +92,29 @@ typedef struct {
   int32_t n_dense_leaves;    /* per plane H-matrix */
   int32_t n_lowrank_leaves;  /* per plane H-matrix */
   double setup_ms;           /* device time of the last setup (CUDA events) */
-  double structure_ms;       /* host time spent building the block structure and plans */
+  double structure_ms;       /* host time spent building the block structure */
+  int64_t apply_bytes;       /* bytes one acr_apply must move: every stored factor entry it
+                                reads (dense leaves, U and V up to their ranks, couplings) plus
+                                its FP64 vector traffic */
+  int64_t apply_flops;       /* multiply-adds x 2 of one acr_apply */
 } acr_setup_info;
+
+/* Per-kernel-class setup statistics (ACR_FLAG_PROFILE).  flops counts the
+ * arithmetic the kernels were asked to do with the ranks they met
+ * (2 m n k per GEMM item, cores counted by their loop bounds). */
+typedef struct {
+  int64_t launches;
+  double ms;                 /* summed CUDA-event time of the launches */
+  double flops;
+} acr_kernel_stat;
+
+typedef struct {
+  acr_kernel_stat gemm;      /* grouped small GEMMs (k_ggemm) */
+  acr_kernel_stat orth;      /* pivoted-Cholesky cores (k_pchol), FP64 */
+  acr_kernel_stat eig;       /* Jacobi recompression cores (k_eig), FP64 */
+  acr_kernel_stat leaf_inv;  /* dense leaf inverses (k_leaf_inv), FP64 */
+  acr_kernel_stat other;     /* conversion, scaling */
+} acr_profile;
 
 typedef struct {
   int32_t iterations;        /* Krylov iterations performed */
@@ -163,6 +189,10 @@ acr_status acr_krylov_solve_plain(const acr_grid* grid, const double* coef, int3
 /* Setup statistics of a handle (host struct). */
 acr_status acr_get_setup_info(const acr_handle* h, acr_setup_info* info);
 
+/* Per-kernel-class profile of the last setup; INVALID_ARG unless the
+ * handle was set up with ACR_FLAG_PROFILE. */
+acr_status acr_get_profile(const acr_handle* h, acr_profile* prof);
+
 /* Host-only introspection of the plane block structure used for (n, eta,
  * leaf) (Sec. 3.1): counts[0..5] = {clusters, dense leaves, low-rank
  * leaves, sum of low-rank rows, sum of low-rank cols, tree depth}.  If
@@ -172,6 +202,10 @@ acr_status acr_get_setup_info(const acr_handle* h, acr_setup_info* info);
  * permutation.  Makes no CUDA call. */
 acr_status acr_structure_query(int32_t n, double eta, int32_t leaf, int64_t* counts,
                                int32_t* leaves_host, int32_t* perm_host);
+
+/* Number of CUDA kernels this library has launched in the process so far
+ * (all handles, all threads); for accounting in benchmarks. */
+int64_t acr_launch_count(void);
 
 /* Release a handle and all its device memory (NULL is a no-op). */
 void acr_destroy(acr_handle* h);

@@ -33,7 +33,10 @@ class Grid(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [("eps", ctypes.c_double), ("eta", ctypes.c_double), ("leaf", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("rank_cap", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("flags", ctypes.c_int32)]
+
+
+ACR_FLAG_PROFILE = 1
 
 
 class SetupInfo(ctypes.Structure):
@@ -41,7 +44,17 @@ class SetupInfo(ctypes.Structure):
                 ("avg_rank", ctypes.c_double), ("factor_bytes", ctypes.c_int64),
                 ("factor_capacity_bytes", ctypes.c_int64), ("n_dense_leaves", ctypes.c_int32),
                 ("n_lowrank_leaves", ctypes.c_int32), ("setup_ms", ctypes.c_double),
-                ("structure_ms", ctypes.c_double)]
+                ("structure_ms", ctypes.c_double), ("apply_bytes", ctypes.c_int64),
+                ("apply_flops", ctypes.c_int64)]
+
+
+class KernelStat(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64), ("ms", ctypes.c_double), ("flops", ctypes.c_double)]
+
+
+class Profile(ctypes.Structure):
+    _fields_ = [("gemm", KernelStat), ("orth", KernelStat), ("eig", KernelStat),
+                ("leaf_inv", KernelStat), ("other", KernelStat)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -75,12 +88,15 @@ def load_library(path=LIB_PATH):
         "acr_krylov_solve_plain": [ctypes.POINTER(Grid), _P, I32, I32, F64, I32, _P, _P,
                                    ctypes.POINTER(SolveInfo), _P],
         "acr_get_setup_info": [_P, ctypes.POINTER(SetupInfo)],
+        "acr_get_profile": [_P, ctypes.POINTER(Profile)],
         "acr_structure_query": [I32, F64, I32, I64p, _P, _P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
         fn.argtypes = args
         fn.restype = ctypes.c_int
+    lib.acr_launch_count.argtypes = []
+    lib.acr_launch_count.restype = ctypes.c_int64
     lib.acr_destroy.argtypes = [_P]
     lib.acr_destroy.restype = None
     lib.acr_status_string.argtypes = [ctypes.c_int]
@@ -136,10 +152,10 @@ def acr_spmv(n, coef, x, y, nrhs=1, stream=None):
                                     _stream(stream)), "acr_spmv")
 
 
-def acr_setup(n, coef, eps, eta, leaf, precision=ACR_FP64, rank_cap=0, stream=None):
+def acr_setup(n, coef, eps, eta, leaf, precision=ACR_FP64, rank_cap=0, stream=None, flags=0):
     """Returns an opaque handle (int); release it with acr_destroy."""
     N = n ** 3
-    opt = Options(eps, eta, leaf, precision, rank_cap, 0)
+    opt = Options(eps, eta, leaf, precision, rank_cap, flags)
     h = _P()
     _check(load_library().acr_setup(ctypes.byref(_grid(n)), _dev(coef, 7 * N, "coef"),
                                      ctypes.byref(opt), _stream(stream), ctypes.byref(h)),
@@ -185,6 +201,12 @@ def acr_get_setup_info(handle):
     return info
 
 
+def acr_get_profile(handle):
+    prof = Profile()
+    _check(load_library().acr_get_profile(_P(handle), ctypes.byref(prof)), "acr_get_profile")
+    return prof
+
+
 def acr_structure_query(n, eta, leaf, with_leaves=False):
     """Host-only: (counts[6], leaves (k, 5) int32 or None, perm or None)."""
     import numpy as np
@@ -201,6 +223,10 @@ def acr_structure_query(n, eta, leaf, with_leaves=False):
     return c, leaves, perm
 
 
+def acr_launch_count():
+    return int(load_library().acr_launch_count())
+
+
 def acr_destroy(handle):
     if handle:
         load_library().acr_destroy(_P(handle))
@@ -213,9 +239,11 @@ def acr_status_string(status):
 class Handle:
     """Owning wrapper of an acr_setup handle."""
 
-    def __init__(self, n, coef, eps, eta, leaf, precision=ACR_FP64, rank_cap=0, stream=None):
+    def __init__(self, n, coef, eps, eta, leaf, precision=ACR_FP64, rank_cap=0, stream=None,
+                 flags=0):
         self.n = n
-        self.h = acr_setup(n, coef, eps, eta, leaf, precision, rank_cap, stream)
+        self.h = None
+        self.h = acr_setup(n, coef, eps, eta, leaf, precision, rank_cap, stream, flags)
 
     def apply(self, r, z, stream=None):
         acr_apply(self.h, r, z, 1, stream)
@@ -225,6 +253,9 @@ class Handle:
 
     def info(self):
         return acr_get_setup_info(self.h)
+
+    def profile(self):
+        return acr_get_profile(self.h)
 
     def close(self):
         if self.h:

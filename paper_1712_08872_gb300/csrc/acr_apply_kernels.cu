@@ -152,7 +152,7 @@ void launch_hmatvec(const MatvecDev& mv, T* const* dense, T* const* U, T* const*
   if (mv.nl > 0) k_lr_proj<T><<<dim3(mv.nl, P), 128, 0, st>>>(mv, U, V, rank, x, tv, trans);
   k_hmv_rows<T><<<dim3(mv.nchunks, P), 256, 0, st>>>(mv, dense, U, V, rank, x, y, alpha, beta, tv,
                                                      trans);
-  ACR_CUDA(cudaGetLastError());
+  ACR_LAUNCHED(mv.nl > 0 ? 2 : 1);
 }
 
 void launch_permute(const double* in, double* out, const int* perm, int n2, int nplanes,
@@ -160,7 +160,7 @@ void launch_permute(const double* in, double* out, const int* perm, int n2, int 
   int64_t total = (int64_t)n2 * nplanes;
   int blocks = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
   k_permute<<<blocks, 256, 0, st>>>(in, out, perm, n2, total, to_cluster);
-  ACR_CUDA(cudaGetLastError());
+  ACR_LAUNCHED(1);
 }
 
 void launch_diag_update(double* const* y, const double* const* a, const double* const* x,
@@ -169,7 +169,7 @@ void launch_diag_update(double* const* y, const double* const* a, const double* 
   if (P <= 0) return;
   dim3 grid((n2 + 255) / 256 < 64 ? (n2 + 255) / 256 : 64, P);
   k_diag_update<<<grid, 256, 0, st>>>(y, a, x, b, z, n2, sgn);
-  ACR_CUDA(cudaGetLastError());
+  ACR_LAUNCHED(1);
 }
 
 void launch_copy_planes(double* const* dst, const double* const* src, int n2, int P,
@@ -177,7 +177,7 @@ void launch_copy_planes(double* const* dst, const double* const* src, int n2, in
   if (P <= 0) return;
   dim3 grid((n2 + 255) / 256 < 64 ? (n2 + 255) / 256 : 64, P);
   k_copy_planes<<<grid, 256, 0, st>>>(dst, src, n2);
-  ACR_CUDA(cudaGetLastError());
+  ACR_LAUNCHED(1);
 }
 
 template void launch_hmatvec<double>(const MatvecDev&, double* const*, double* const*,

@@ -11,6 +11,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -24,6 +25,9 @@
 #include "acr_internal.h"
 
 namespace acr {
+
+static std::atomic<int64_t> g_launches{0};
+void count_launches(int64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
 namespace {
 
@@ -101,6 +105,8 @@ class EngineBase {
   virtual void setup(const double* coef, cudaStream_t st) = 0;
   virtual void apply(const double* r, double* z, bool trans, cudaStream_t st) = 0;
   acr_setup_info info{};
+  acr_profile prof{};
+  bool profiling = false;
   int n = 0;
   int64_t N = 0;
 };
@@ -108,8 +114,9 @@ class EngineBase {
 template <typename T>
 class Engine : public EngineBase {
  public:
-  Engine(int n_, double eps_, double eta_, int leaf_, int kc_) : eps(eps_), eta(eta_),
+  Engine(int n_, double eps_, double eta_, int leaf_, int kc_, int flags_) : eps(eps_), eta(eta_),
       leaf(leaf_), kc(kc_) {
+    profiling = (flags_ & ACR_FLAG_PROFILE) != 0;
     n = n_;
     n2 = n * n;
     N = (int64_t)n2 * n;
@@ -160,6 +167,49 @@ class Engine : public EngineBase {
   };
   std::vector<ApplyStep> fwd_steps, bwd_steps, fwdT_steps, bwdT_steps;
   int maxP = 1;
+  std::map<const void*, int64_t> hm_used;   // stored entries an apply reads per H-matrix
+
+  // ---- optional per-kernel-class profile (CUDA events around launches)
+  cudaStream_t cur_st = 0;
+  double* d_fl = nullptr;                   // 5 counted-flop accumulators
+  struct Pend { int cls; cudaEvent_t a, b; };
+  std::vector<Pend> pend;
+  std::vector<cudaEvent_t> evfree;
+  cudaEvent_t ev() {
+    if (evfree.empty()) {
+      cudaEvent_t e;
+      ACR_CUDA(cudaEventCreate(&e));
+      return e;
+    }
+    cudaEvent_t e = evfree.back();
+    evfree.pop_back();
+    return e;
+  }
+  double* fl(int cls) { return profiling ? d_fl + cls : nullptr; }
+  template <class F>
+  void timed(int cls, F&& f) {
+    if (!profiling) { f(); return; }
+    Pend pd{cls, ev(), ev()};
+    ACR_CUDA(cudaEventRecord(pd.a, cur_st));
+    f();
+    ACR_CUDA(cudaEventRecord(pd.b, cur_st));
+    pend.push_back(pd);
+    if (pend.size() >= 4096) flush_prof();
+  }
+  void flush_prof() {
+    if (!profiling) return;
+    ACR_CUDA(cudaStreamSynchronize(cur_st));
+    acr_kernel_stat* ks[5] = {&prof.gemm, &prof.orth, &prof.eig, &prof.leaf_inv, &prof.other};
+    for (Pend& pd : pend) {
+      float ms = 0;
+      ACR_CUDA(cudaEventElapsedTime(&ms, pd.a, pd.b));
+      ks[pd.cls]->ms += ms;
+      ks[pd.cls]->launches += 1;
+      evfree.push_back(pd.a);
+      evfree.push_back(pd.b);
+    }
+    pend.clear();
+  }
 
   HM alloc_hm() {
     HM h;
@@ -192,6 +242,9 @@ class Engine : public EngineBase {
     if (scratch_ranks) cudaFree(scratch_ranks);
     scratch = nullptr; scratch_ranks = nullptr;
     ring.release();
+    for (Pend& pd : pend) { cudaEventDestroy(pd.a); cudaEventDestroy(pd.b); }
+    for (cudaEvent_t e : evfree) cudaEventDestroy(e);
+    pend.clear(); evfree.clear();
   }
 
   // ------------------------------------------------------------ plans
@@ -207,18 +260,6 @@ class Engine : public EngineBase {
     if (it != plans.end()) return *it->second;
     auto pl = std::make_unique<Plan>();
     build_plan(S, op, pp, *pl);
-    pl->d_groups = dmalloc(std::max<size_t>(pl->groups.size(), 1) * sizeof(GGroup));
-    pl->d_items = dmalloc(std::max<size_t>(pl->items.size(), 1) * sizeof(GItem));
-    pl->d_targets = dmalloc(std::max<size_t>(pl->targets.size(), 1) * sizeof(TInfo));
-    if (!pl->groups.empty())
-      ACR_CUDA(cudaMemcpy(pl->d_groups, pl->groups.data(), pl->groups.size() * sizeof(GGroup),
-                          cudaMemcpyHostToDevice));
-    if (!pl->items.empty())
-      ACR_CUDA(cudaMemcpy(pl->d_items, pl->items.data(), pl->items.size() * sizeof(GItem),
-                          cudaMemcpyHostToDevice));
-    if (!pl->targets.empty())
-      ACR_CUDA(cudaMemcpy(pl->d_targets, pl->targets.data(), pl->targets.size() * sizeof(TInfo),
-                          cudaMemcpyHostToDevice));
     Plan& ref = *pl;
     plans[key] = std::move(pl);
     return ref;
@@ -241,11 +282,65 @@ class Engine : public EngineBase {
     }
   }
 
+  void upload_plan(Plan& pl) {
+    if (pl.d_groups) return;
+    pl.d_groups = dmalloc(std::max<size_t>(pl.groups.size(), 1) * sizeof(GGroup));
+    pl.d_items = dmalloc(std::max<size_t>(pl.items.size(), 1) * sizeof(GItem));
+    pl.d_targets = dmalloc(std::max<size_t>(pl.targets.size(), 1) * sizeof(TInfo));
+    if (!pl.groups.empty())
+      ACR_CUDA(cudaMemcpy(pl.d_groups, pl.groups.data(), pl.groups.size() * sizeof(GGroup),
+                          cudaMemcpyHostToDevice));
+    if (!pl.items.empty())
+      ACR_CUDA(cudaMemcpy(pl.d_items, pl.items.data(), pl.items.size() * sizeof(GItem),
+                          cudaMemcpyHostToDevice));
+    if (!pl.targets.empty())
+      ACR_CUDA(cudaMemcpy(pl.d_targets, pl.targets.data(), pl.targets.size() * sizeof(TInfo),
+                          cudaMemcpyHostToDevice));
+  }
+
+  // Run a formatted operation, splitting it into the four child target
+  // blocks (products re-rooted at the child cluster pairs) while its
+  // per-plane scratch would not let a useful number of planes share the
+  // scratch arena.  Splitting changes no arithmetic: every term and every
+  // target leaf is the same, only grouped into smaller launches.
+  void run_split(const OpDesc& op, const std::vector<std::vector<HM>>& roles, int P,
+                 cudaStream_t st) {
+    if (P <= 0) return;
+    const BNode& c = S.bn[op.c_node];
+    bool can = c.kind == BK_INNER;
+    for (const auto& pr : op.prods)
+      can = can && S.bn[pr.a_node].kind == BK_INNER && S.bn[pr.b_node].kind == BK_INNER;
+    if (can) {
+      Plan& pl = get_plan(op);
+      const size_t want = (size_t)pl.scratch * sizeof(T) * (size_t)std::min(P, 8);
+      if (want <= scratch_budget) can = false;
+    }
+    if (!can) {
+      run_op(op, roles, P, st);
+      return;
+    }
+    for (int k = 0; k < 4; ++k) {
+      const int i = k / 2, j = k % 2;
+      OpDesc sub = op;
+      sub.c_node = c.child[k];
+      sub.prods.clear();
+      for (const auto& pr : op.prods) {
+        const BNode& A = S.bn[pr.a_node];
+        const BNode& B = S.bn[pr.b_node];
+        for (int m = 0; m < 2; ++m)
+          sub.prods.push_back(OpDesc::Prod{A.child[i * 2 + m], B.child[m * 2 + j], pr.a_role,
+                                           pr.b_role, pr.coef});
+      }
+      run_split(sub, roles, P, st);
+    }
+  }
+
   // roles[r][p]: H-matrix of role r for plane p of the batch
   void run_op(const OpDesc& op, const std::vector<std::vector<HM>>& roles, int P,
               cudaStream_t st) {
     if (P <= 0) return;
     Plan& pl = get_plan(op);
+    upload_plan(pl);
     const int nr = op.nroles;
     size_t per_plane = std::max<size_t>((size_t)pl.scratch * sizeof(T), 256);
     int Pc = (int)std::max<size_t>(1, std::min<size_t>(P, scratch_budget / per_plane));
@@ -270,11 +365,14 @@ class Engine : public EngineBase {
       int* const* d_rtab = (int* const*)ring.push(rtab.data(), sizeof(void*) * (nr + 1) * pc, st);
       for (const Stage& sg : pl.stages) {
         if (sg.kind == ST_GEMM)
-          launch_ggemm<T>(pl, sg.beg, sg.end, d_tab, (const int* const*)d_rtab, pc, d_coefs, st);
+          timed(0, [&] { launch_ggemm<T>(pl, sg.beg, sg.end, d_tab, (const int* const*)d_rtab, pc,
+                                         d_coefs, st, fl(0)); });
         else if (sg.kind == ST_PCHOL || sg.kind == ST_PCHOL + 16)
-          launch_pchol<T>(pl, sg.beg, sg.end, sg.kind == ST_PCHOL, tau_orth(), d_tab, d_rtab, pc, st);
+          timed(1, [&] { launch_pchol<T>(pl, sg.beg, sg.end, sg.kind == ST_PCHOL, tau_orth(), d_tab,
+                                         d_rtab, pc, st, fl(1)); });
         else if (sg.kind == ST_EIG)
-          launch_eig<T>(pl, sg.beg, sg.end, eps, kc, op.c_role, d_tab, d_rtab, pc, d_err, st);
+          timed(2, [&] { launch_eig<T>(pl, sg.beg, sg.end, eps, kc, op.c_role, d_tab, d_rtab, pc,
+                                       d_err, st, fl(2)); });
       }
     }
   }
@@ -292,7 +390,8 @@ class Engine : public EngineBase {
     const Cluster& c = S.cl[t];
     if (c.child[0] < 0) {
       int nd = S.node(t, t);
-      launch_leaf_inv<T>((T* const*)d_xdense, S.dense_off(S.bn[nd].leaf), S.lsz, P, d_err, st);
+      timed(3, [&] { launch_leaf_inv<T>((T* const*)d_xdense, S.dense_off(S.bn[nd].leaf), S.lsz, P,
+                                        d_err, st, fl(3)); });
       return;
     }
     const int t1 = c.child[0], t2 = c.child[1];
@@ -305,13 +404,13 @@ class Engine : public EngineBase {
       return op;
     };
     hinv(t1, roles, d_xdense, P, st);
-    run_op(mk(n12, 1, -1, n11, 0, n12, 0, 0), roles, P, st);   // T12 = X11 A12
-    run_op(mk(n21, 1, -1, n21, 0, n11, 0, 0), roles, P, st);   // T21 = A21 X11
-    run_op(mk(n22, 0, 0, n21, 0, n12, 1, 1), roles, P, st);    // S = A22 - A21 T12
+    run_split(mk(n12, 1, -1, n11, 0, n12, 0, 0), roles, P, st);   // T12 = X11 A12
+    run_split(mk(n21, 1, -1, n21, 0, n11, 0, 0), roles, P, st);   // T21 = A21 X11
+    run_split(mk(n22, 0, 0, n21, 0, n12, 1, 1), roles, P, st);    // S = A22 - A21 T12
     hinv(t2, roles, d_xdense, P, st);
-    run_op(mk(n12, 0, -1, n12, 1, n22, 0, 1), roles, P, st);   // X12 = -T12 X22
-    run_op(mk(n21, 0, -1, n22, 0, n21, 1, 1), roles, P, st);   // X21 = -X22 T21
-    run_op(mk(n11, 0, 0, n12, 0, n21, 1, 1), roles, P, st);    // X11 = X11 - X12 T21
+    run_split(mk(n12, 0, -1, n12, 1, n22, 0, 1), roles, P, st);   // X12 = -T12 X22
+    run_split(mk(n21, 0, -1, n22, 0, n21, 1, 1), roles, P, st);   // X21 = -X22 T21
+    run_split(mk(n11, 0, 0, n12, 0, n21, 1, 1), roles, P, st);    // X11 = X11 - X12 T21
   }
 
   void hinv_batch(const std::vector<int>& planes, cudaStream_t st) {
@@ -357,6 +456,7 @@ class Engine : public EngineBase {
 template <typename T>
 void Engine<T>::setup(const double* coef, cudaStream_t st) {
   auto h0 = std::chrono::steady_clock::now();
+  cur_st = st;
   S.build(n, eta, leaf);
   if (!S.balanced || S.lsz > 64 || S.lsz < 1)
     throw AcrError{S_UNSUPPORTED, "cluster tree is not balanced with leaves of at most 64 points"};
@@ -434,6 +534,11 @@ void Engine<T>::setup(const double* coef, cudaStream_t st) {
   d_err = (int*)dmalloc(sizeof(int));
   owned.push_back(d_err);
   ACR_CUDA(cudaMemset(d_err, 0, sizeof(int)));
+  if (profiling) {
+    d_fl = (double*)dmalloc(5 * sizeof(double));
+    owned.push_back(d_fl);
+    ACR_CUDA(cudaMemset(d_fl, 0, 5 * sizeof(double)));
+  }
   std::vector<int> allp(n);
   for (int k = 0; k < n; ++k) allp[k] = k;
   d_planes_all = (int*)upload(allp, owned);
@@ -452,8 +557,8 @@ void Engine<T>::setup(const double* coef, cudaStream_t st) {
     for (int k = 0; k < n; ++k) { td[k] = D[k].dense; tu[k] = D[k].U; tv[k] = D[k].V; tr[k] = D[k].rank; }
     void** a = put_tables(td); void** b = put_tables(tu); void** c = put_tables(tv);
     void** d = put_tables(tr);
-    launch_plane_to_h<T>(sd, coef, n, d_planes_all, n, (T* const*)a, (T* const*)b, (T* const*)c,
-                         (int* const*)d, kc, st);
+    timed(4, [&] { launch_plane_to_h<T>(sd, coef, n, d_planes_all, n, (T* const*)a, (T* const*)b,
+                                        (T* const*)c, (int* const*)d, kc, st); });
     if (has_cpl) {
       OpDesc op;
       op.c_node = 0; op.c_role = 0; op.alpha = 0; op.nroles = 1;
@@ -512,10 +617,12 @@ void Engine<T>::setup(const double* coef, cudaStream_t st) {
         void** t[10] = {put_tables(od), put_tables(ou), put_tables(ov), put_tables(orr),
                         put_tables(xd), put_tables(xu), put_tables(xv), put_tables(xr),
                         put_tables(rr), put_tables(cc)};
-        launch_hscale<T>(sd, (T* const*)t[0], (T* const*)t[1], (T* const*)t[2], (int* const*)t[3],
-                         (T* const*)t[4], (T* const*)t[5], (T* const*)t[6],
-                         (const int* const*)t[7], (const double* const*)t[8],
-                         (const double* const*)t[9], sgn, kc, PB, st);
+        timed(4, [&] {
+          launch_hscale<T>(sd, (T* const*)t[0], (T* const*)t[1], (T* const*)t[2], (int* const*)t[3],
+                           (T* const*)t[4], (T* const*)t[5], (T* const*)t[6],
+                           (const int* const*)t[7], (const double* const*)t[8],
+                           (const double* const*)t[9], sgn, kc, PB, st);
+        });
       };
       scale(Ta, Xa, rowA, colA, 1.0);
       scale(Tb, Xb, rowB, colB, 1.0);
@@ -554,18 +661,18 @@ void Engine<T>::setup(const double* coef, cudaStream_t st) {
       OpDesc opT;
       opT.c_node = 0; opT.c_role = 0; opT.alpha = -1; opT.nroles = 3;
       opT.prods.push_back(OpDesc::Prod{0, 0, 1, 2, 0});
-      run_op(opT, {Ta, Lj, Xa}, PB, st);              // Ta = L_j X_a
-      run_op(opT, {Tb, Uj, Xb}, PB, st);              // Tb = U_j X_b
+      run_split(opT, {Ta, Lj, Xa}, PB, st);           // Ta = L_j X_a
+      run_split(opT, {Tb, Uj, Xb}, PB, st);           // Tb = U_j X_b
       OpDesc opD;
       opD.c_node = 0; opD.c_role = 0; opD.alpha = 0; opD.nroles = 5;
       opD.prods.push_back(OpDesc::Prod{0, 0, 1, 2, 1});
       opD.prods.push_back(OpDesc::Prod{0, 0, 3, 4, 1});
-      run_op(opD, {Dj, Ta, Ua, Tb, Lb}, PB, st);      // D_j -= Ta U_a + Tb L_b
+      run_split(opD, {Dj, Ta, Ua, Tb, Lb}, PB, st);   // D_j -= Ta U_a + Tb L_b
       OpDesc opN;
       opN.c_node = 0; opN.c_role = 0; opN.alpha = -1; opN.nroles = 3;
       opN.prods.push_back(OpDesc::Prod{0, 0, 1, 2, 1});
-      run_op(opN, {nL, Ta, La}, PB, st);              // L_j' = -Ta L_a
-      run_op(opN, {nU, Tb, Ub}, PB, st);              // U_j' = -Tb U_b
+      run_split(opN, {nL, Ta, La}, PB, st);           // L_j' = -Ta L_a
+      run_split(opN, {nU, Tb, Ub}, PB, st);           // U_j' = -Tb U_b
       ACR_CUDA(cudaStreamSynchronize(st));
       for (int q = 0; q < PB; ++q) {
         if (Ta[q].dense) free_hm(Ta[q]);
@@ -587,6 +694,13 @@ void Engine<T>::setup(const double* coef, cudaStream_t st) {
   ACR_CUDA(cudaEventSynchronize(e1));
   float ms = 0;
   ACR_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+  if (profiling) {
+    flush_prof();
+    double h[5];
+    ACR_CUDA(cudaMemcpy(h, d_fl, sizeof(h), cudaMemcpyDeviceToHost));
+    prof.gemm.flops = h[0]; prof.orth.flops = h[1]; prof.eig.flops = h[2];
+    prof.leaf_inv.flops = h[3]; prof.other.flops = h[4];
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   info.setup_ms = ms;
@@ -608,21 +722,26 @@ void Engine<T>::collect_info() {
   int64_t sumr = 0, cnt = 0;
   int mx = 0;
   int64_t bytes = 0;
+  std::vector<const void*> seen;
   auto account = [&](const HM& h) {
     if (!h.dense) return;
+    if (std::find(seen.begin(), seen.end(), h.dense) != seen.end()) return;
+    seen.push_back(h.dense);
     if (!rk.empty())
       ACR_CUDA(cudaMemcpy(rk.data(), h.rank, rk.size() * sizeof(int), cudaMemcpyDeviceToHost));
-    bytes += (int64_t)S.dleaf.size() * S.lsz * S.lsz * sizeof(T);
+    int64_t used = (int64_t)S.dleaf.size() * S.lsz * S.lsz;
     for (size_t l = 0; l < rk.size(); ++l) {
       mx = std::max(mx, rk[l]);
       sumr += rk[l];
       ++cnt;
-      bytes += (int64_t)rk[l] * (mvp.lr_m[l] + mvp.lr_n[l]) * sizeof(T);
+      used += (int64_t)rk[l] * (mvp.lr_m[l] + mvp.lr_n[l]);
     }
+    hm_used[h.dense] = used;
+    bytes += used * (int64_t)sizeof(T);
   };
   for (const Level& lev : levels) {
     for (int i : lev.red) account(D[i]);
-    for (int k = 0; k < n; ++k) { account(lev.L[k]); account(lev.U[k]); }
+    for (int k = 0; k < n; k += lev.s) { account(lev.L[k]); account(lev.U[k]); }
   }
   account(D[0]);
   info.max_rank = mx;
@@ -644,9 +763,21 @@ void Engine<T>::build_apply_program() {
   owned.push_back(tvscr);
   auto vec = [&](double* base, int k) -> double* { return (k >= 0 && k < n) ? base + (int64_t)k * n2 : nullptr; };
   // hmatvec tables: dense, U, V, rank, x, y (6 * P pointers)
+  int64_t abytes = 0, aflops = 0;
+  bool count = true;   // count the plain (non-transposed) program only
   auto mv_step = [&](const std::vector<HM>& H, const std::vector<double*>& x,
                      const std::vector<double*>& y, double alpha, double beta, bool trans) {
     const int P = (int)H.size();
+    if (count)
+      for (int p = 0; p < P; ++p) {
+        if (!y[p]) continue;
+        abytes += (int64_t)n2 * 8 * (beta != 0.0 ? 2 : 1);
+        if (H[p].dense && x[p]) {
+          const int64_t u = hm_used.count(H[p].dense) ? hm_used[H[p].dense] : 0;
+          abytes += u * (int64_t)sizeof(T) + (int64_t)n2 * 8;
+          aflops += 2 * u;
+        }
+      }
     std::vector<void*> t(6 * P);
     for (int p = 0; p < P; ++p) {
       t[p] = H[p].dense; t[P + p] = H[p].U; t[2 * P + p] = H[p].V; t[3 * P + p] = H[p].rank;
@@ -658,6 +789,13 @@ void Engine<T>::build_apply_program() {
                        const std::vector<double*>& x, const std::vector<const double*>& b,
                        const std::vector<double*>& z, double sgn) {
     const int P = (int)y.size();
+    if (count)
+      for (int p = 0; p < P; ++p) {
+        if (!y[p]) continue;
+        abytes += (int64_t)n2 * 8 * 2;
+        if (a[p] && x[p]) { abytes += (int64_t)n2 * 16; aflops += 2 * n2; }
+        if (b[p] && z[p]) { abytes += (int64_t)n2 * 16; aflops += 2 * n2; }
+      }
     std::vector<const void*> t(5 * P);
     for (int p = 0; p < P; ++p) {
       t[p] = y[p]; t[P + p] = a[p]; t[2 * P + p] = x[p]; t[3 * P + p] = b[p]; t[4 * P + p] = z[p];
@@ -666,12 +804,15 @@ void Engine<T>::build_apply_program() {
   };
   auto copy_step = [&](const std::vector<double*>& dst, const std::vector<double*>& src) {
     const int P = (int)dst.size();
+    if (count)
+      for (int p = 0; p < P; ++p) abytes += (int64_t)n2 * 8 * (src[p] ? 2 : 1);
     std::vector<void*> t(2 * P);
     for (int p = 0; p < P; ++p) { t[p] = dst[p]; t[P + p] = src[p]; }
     return ApplyStep{2, P, false, 0.0, 0.0, 0.0, put_tables(t)};
   };
   for (int pass = 0; pass < 2; ++pass) {
     const bool tr = pass == 1;
+    count = !tr;
     auto& fw = tr ? fwdT_steps : fwd_steps;
     auto& bw = tr ? bwdT_steps : bwd_steps;
     for (size_t r = 0; r < levels.size(); ++r) {
@@ -770,6 +911,9 @@ void Engine<T>::build_apply_program() {
       bw.push_back(mv_step(X, tmp, us, -1.0, 1.0, tr));  // u_i -= X_i tmp
     }
   }
+  // the two permutations between natural and cluster order
+  info.apply_bytes = abytes + 4 * N * 8;
+  info.apply_flops = aflops;
 }
 
 template <typename T>
@@ -1101,9 +1245,9 @@ acr_status acr_setup(const acr_grid* grid, const double* coef, const acr_options
   h->precision = opt->precision;
   acr_status s = guarded([&] {
     if (opt->precision == ACR_FP64)
-      h->e = new acr::Engine<double>(grid->nx, opt->eps, opt->eta, opt->leaf, kc);
+      h->e = new acr::Engine<double>(grid->nx, opt->eps, opt->eta, opt->leaf, kc, opt->flags);
     else
-      h->e = new acr::Engine<float>(grid->nx, opt->eps, opt->eta, opt->leaf, kc);
+      h->e = new acr::Engine<float>(grid->nx, opt->eps, opt->eta, opt->leaf, kc, opt->flags);
     h->e->setup(coef, stream);
     return 0;
   });
@@ -1188,6 +1332,12 @@ acr_status acr_get_setup_info(const acr_handle* h, acr_setup_info* info) {
   return ACR_OK;
 }
 
+acr_status acr_get_profile(const acr_handle* h, acr_profile* prof) {
+  if (!h || !h->e || !prof || !h->e->profiling) return ACR_ERR_INVALID_ARG;
+  *prof = h->e->prof;
+  return ACR_OK;
+}
+
 acr_status acr_structure_query(int32_t n, double eta, int32_t leaf, int64_t* counts,
                                int32_t* leaves_host, int32_t* perm_host) {
   if (n < 1 || n > 1024 || !(eta > 0.0) || leaf < 1 || !counts) return ACR_ERR_INVALID_ARG;
@@ -1219,6 +1369,8 @@ acr_status acr_structure_query(int32_t n, double eta, int32_t leaf, int64_t* cou
   }
   return ACR_OK;
 }
+
+int64_t acr_launch_count(void) { return acr::g_launches.load(); }
 
 void acr_destroy(acr_handle* h) {
   if (!h) return;

@@ -15,6 +15,9 @@ enum Status {
   S_RANK_CAP = 5, S_NOT_CONVERGED = 6, S_TIMEOUT = 7, S_UNSUPPORTED = 8
 };
 
+// Process-wide count of kernel launches made by the library.
+void count_launches(int64_t k);
+
 // Device-side error word bits (written by kernels, read by the host).
 enum : int { ERR_PIVOT = 1, ERR_RANKCAP = 2 };
 
@@ -29,27 +32,37 @@ struct CudaError {
     if (e_ != cudaSuccess) throw ::acr::CudaError{e_, #x};  \
   } while (0)
 
+// after every kernel launch: account it and surface launch errors
+#define ACR_LAUNCHED(k)                    \
+  do {                                     \
+    ::acr::count_launches(k);              \
+    ACR_CUDA(cudaGetLastError());          \
+  } while (0)
+
 // ------------------------------------------------------------ setup kernels
 // Grouped small GEMMs of a plan stage: one CTA per (group, plane).
 template <typename T>
 void launch_ggemm(const Plan& pl, int gbeg, int gend, T* const* d_tab, const int* const* d_rtab,
-                  int P, const double* d_coefs, cudaStream_t st);
+                  int P, const double* d_coefs, cudaStream_t st, double* d_flops = nullptr);
 
 // Pivoted-Cholesky orthonormalisation cores (FP64) of plan targets.
 template <typename T>
 void launch_pchol(const Plan& pl, int tbeg, int tend, bool truncate, double tau,
-                  T* const* d_tab, int* const* d_rtab, int P, cudaStream_t st);
+                  T* const* d_tab, int* const* d_rtab, int P, cudaStream_t st,
+                  double* d_flops = nullptr);
 
 // Jacobi eigen cores (FP64) of plan targets; writes the kept ranks into
 // the rank buffer of role c_role and raises ERR_RANKCAP above kc.
 template <typename T>
 void launch_eig(const Plan& pl, int tbeg, int tend, double eps, int kc, int c_role,
-                T* const* d_tab, int* const* d_rtab, int P, int* d_err, cudaStream_t st);
+                T* const* d_tab, int* const* d_rtab, int P, int* d_err, cudaStream_t st,
+                double* d_flops = nullptr);
 
 // In-place FP64 Gauss-Jordan inverse (partial pivoting) of one dense
 // lsz x lsz leaf in each of P H-matrices (base pointers in d_dense[p]).
 template <typename T>
-void launch_leaf_inv(T* const* d_dense, int64_t off, int lsz, int P, int* d_err, cudaStream_t st);
+void launch_leaf_inv(T* const* d_dense, int64_t off, int lsz, int P, int* d_err, cudaStream_t st,
+                     double* d_flops = nullptr);
 
 // Device copies of the plane structure arrays.
 struct StructDev {

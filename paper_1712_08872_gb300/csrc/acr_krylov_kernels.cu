@@ -145,17 +145,17 @@ inline int grid_for(int64_t N) {
 
 void launch_stencil_poisson(const double* kappa, double* coef, int n, cudaStream_t st) {
   k_stencil_poisson<<<grid_for((int64_t)n * n * n), 256, 0, st>>>(kappa, coef, n);
-  ACR_CUDA(cudaGetLastError());
+  ACR_LAUNCHED(1);
 }
 
 void launch_stencil_codi(const double* beta, double* coef, int n, cudaStream_t st) {
   k_stencil_codi<<<grid_for((int64_t)n * n * n), 256, 0, st>>>(beta, coef, n);
-  ACR_CUDA(cudaGetLastError());
+  ACR_LAUNCHED(1);
 }
 
 void launch_spmv(const double* coef, const double* x, double* y, int n, cudaStream_t st) {
   k_spmv<<<grid_for((int64_t)n * n * n), 256, 0, st>>>(coef, x, y, n);
-  ACR_CUDA(cudaGetLastError());
+  ACR_LAUNCHED(1);
 }
 
 void launch_multidot(const double* V, int64_t ldv, int nv, const double* w, int64_t N,
@@ -165,25 +165,25 @@ void launch_multidot(const double* V, int64_t ldv, int nv, const double* w, int6
   if (nb < 1) nb = 1;
   k_multidot_partial<<<dim3(nb, nv), RB, 0, st>>>(V, ldv, w, N, partial);
   k_multidot_final<<<nv, RB, 0, st>>>(partial, nb, out);
-  ACR_CUDA(cudaGetLastError());
+  ACR_LAUNCHED(2);
 }
 
 void launch_multiaxpy(double* w, const double* V, int64_t ldv, int nv, const double* coef,
                       double scale, int64_t N, cudaStream_t st) {
   if (nv <= 0) return;
   k_multiaxpy<<<grid_for(N), 256, 0, st>>>(w, V, ldv, nv, coef, scale, N);
-  ACR_CUDA(cudaGetLastError());
+  ACR_LAUNCHED(1);
 }
 
 void launch_axpby(double* y, const double* x, double a, double b, int64_t N, cudaStream_t st) {
   k_axpby<<<grid_for(N), 256, 0, st>>>(y, x, a, b, N);
-  ACR_CUDA(cudaGetLastError());
+  ACR_LAUNCHED(1);
 }
 
 void launch_axpby_dev(double* y, const double* x, const double* a, double asgn, double b,
                       int64_t N, cudaStream_t st) {
   k_axpby_dev<<<grid_for(N), 256, 0, st>>>(y, x, a, asgn, b, N);
-  ACR_CUDA(cudaGetLastError());
+  ACR_LAUNCHED(1);
 }
 
 }  // namespace acr

@@ -45,9 +45,11 @@ __global__ void __launch_bounds__(NT) k_ggemm(const GGroup* __restrict__ groups,
                                               const GItem* __restrict__ items,
                                               T* const* __restrict__ tab,
                                               const int* const* __restrict__ rtab, int P,
-                                              int gbase, const double* __restrict__ coefs) {
+                                              int gbase, const double* __restrict__ coefs,
+                                              double* __restrict__ flops) {
   const int p = blockIdx.y;
   const GGroup G = groups[gbase + blockIdx.x];
+  double fl = 0.0;
   T* C = tab[G.cbuf * P + p];
   if (!C) return;
   const int m = dimv(G.m_st, G.m_rb, G.m_ri, rtab, P, p);
@@ -84,6 +86,7 @@ __global__ void __launch_bounds__(NT) k_ggemm(const GGroup* __restrict__ groups,
     if (k <= 0 || rows <= 0) continue;
     const Acc cf = (Acc)coefs[I.coef];
     const int r0 = I.row_off;
+    fl += (I.aflags & FL_IDENT) || (I.bflags & FL_IDENT) ? (double)rows * n : 2.0 * rows * n * k;
     if (I.aflags & FL_IDENT) {   // C(r0+i, j) += cf * B(i, j)
 #pragma unroll
       for (int a = 0; a < 4; ++a) {
@@ -167,6 +170,7 @@ __global__ void __launch_bounds__(NT) k_ggemm(const GGroup* __restrict__ groups,
       *c = (T)v;
     }
   }
+  if (flops && threadIdx.x == 0 && fl > 0.0) atomicAdd(flops, fl);
 }
 
 // ---------------------------------------------------------------- cores
@@ -199,7 +203,7 @@ template <typename T>
 __global__ void __launch_bounds__(NT) k_pchol(const TInfo* __restrict__ tis, int tbase, bool truncate,
                                               double tau, T* const* __restrict__ tab,
                                               int* const* __restrict__ rtab, int P, int scr_buf,
-                                              int scr_rbuf) {
+                                              int scr_rbuf, double* __restrict__ flops) {
   const int p = blockIdx.y;
   const TInfo ti = tis[tbase + blockIdx.x];
   T* scr = tab[scr_buf * P + p];
@@ -297,7 +301,10 @@ __global__ void __launch_bounds__(NT) k_pchol(const TInfo* __restrict__ tis, int
     int j = e % r, c = e / r;
     Tm[piv[j] + (int64_t)c * ld] = (T)(j <= c ? L[c][j] : 0.0);
   }
-  if (threadIdx.x == 0) rs[ti.r_ri] = r;
+  if (threadIdx.x == 0) {
+    rs[ti.r_ri] = r;
+    if (flops) atomicAdd(flops, (double)pd * r * r - 2.0 * r * r * r / 3.0 + (double)r * r * r / 3.0);
+  }
 }
 
 // Cyclic Jacobi (round-robin parallel order) on the r x r symmetric core H.
@@ -305,7 +312,7 @@ template <typename T>
 __global__ void __launch_bounds__(NT) k_eig(const TInfo* __restrict__ tis, int tbase, double eps,
                                             int kc, int c_rbuf, T* const* __restrict__ tab,
                                             int* const* __restrict__ rtab, int P, int scr_buf,
-                                            int scr_rbuf, int* err) {
+                                            int scr_rbuf, int* err, double* __restrict__ flops) {
   const int p = blockIdx.y;
   const TInfo ti = tis[tbase + blockIdx.x];
   T* scr = tab[scr_buf * P + p];
@@ -337,6 +344,7 @@ __global__ void __launch_bounds__(NT) k_eig(const TInfo* __restrict__ tis, int t
   __syncthreads();
   const int nn = (r + 1) & ~1;   // even number of players (r may get a dummy)
   const int npair = nn / 2;
+  int sweeps_done = 0;
   for (int sweep = 0; sweep < 40; ++sweep) {
     // off-diagonal and total norms
     double off = 0, tot = 0;
@@ -363,6 +371,7 @@ __global__ void __launch_bounds__(NT) k_eig(const TInfo* __restrict__ tis, int t
     double tots = red[0];
     __syncthreads();
     if (offs <= 1e-30 * tots || r == 1) break;
+    ++sweeps_done;
     for (int round = 0; round < nn - 1; ++round) {
       // circle method: player 0 fixed, others rotate
       for (int k = threadIdx.x; k < npair; k += NT) {
@@ -438,6 +447,7 @@ __global__ void __launch_bounds__(NT) k_eig(const TInfo* __restrict__ tis, int t
     }
     kkeep = k;
     crank[ti.c_leaf] = k;
+    if (flops) atomicAdd(flops, 9.0 * r * r * r * sweeps_done);
   }
   __syncthreads();
   const int k = kkeep;
@@ -450,7 +460,7 @@ __global__ void __launch_bounds__(NT) k_eig(const TInfo* __restrict__ tis, int t
 // In-place Gauss-Jordan inverse with partial pivoting, FP64, n <= 64.
 template <typename T>
 __global__ void __launch_bounds__(NT) k_leaf_inv(T* const* __restrict__ dense, int64_t off, int n,
-                                                 int* err) {
+                                                 int* err, double* __restrict__ flops) {
   const int p = blockIdx.x;
   T* Ap = dense[p];
   if (!Ap) return;
@@ -509,6 +519,7 @@ __global__ void __launch_bounds__(NT) k_leaf_inv(T* const* __restrict__ dense, i
     __syncthreads();
   }
   for (int e = threadIdx.x; e < n * n; e += NT) Ap[e] = (T)A[e % n][e / n];
+  if (flops && threadIdx.x == 0) atomicAdd(flops, 2.0 * n * n * n);
 }
 
 // out = sgn * diag(r) X diag(c): dense part
@@ -620,7 +631,7 @@ __global__ void k_plane_lr(const double* __restrict__ coef, int n, const int* __
 
 template <typename T>
 void launch_ggemm(const Plan& pl, int gbeg, int gend, T* const* d_tab, const int* const* d_rtab,
-                  int P, const double* d_coefs, cudaStream_t st) {
+                  int P, const double* d_coefs, cudaStream_t st, double* d_fl) {
   int ng = gend - gbeg;
   if (ng <= 0 || P <= 0) return;
   using Acc = T;
@@ -628,14 +639,14 @@ void launch_ggemm(const Plan& pl, int gbeg, int gend, T* const* d_tab, const int
   for (int g0 = 0; g0 < ng; g0 += maxg) {
     dim3 grid(std::min(maxg, ng - g0), P);
     k_ggemm<T, Acc><<<grid, NT, 0, st>>>((const GGroup*)pl.d_groups, (const GItem*)pl.d_items,
-                                         d_tab, d_rtab, P, gbeg + g0, d_coefs);
+                                         d_tab, d_rtab, P, gbeg + g0, d_coefs, d_fl);
+    ACR_LAUNCHED(1);
   }
-  ACR_CUDA(cudaGetLastError());
 }
 
 template <typename T>
 void launch_pchol(const Plan& pl, int tbeg, int tend, bool truncate, double tau, T* const* d_tab,
-                  int* const* d_rtab, int P, cudaStream_t st) {
+                  int* const* d_rtab, int P, cudaStream_t st, double* d_fl) {
   int nt = tend - tbeg;
   if (nt <= 0 || P <= 0) return;
   const size_t smem = 2 * CMAX * (CMAX + 1) * sizeof(double);
@@ -643,14 +654,15 @@ void launch_pchol(const Plan& pl, int tbeg, int tend, bool truncate, double tau,
   for (int t0 = 0; t0 < nt; t0 += 65535) {
     dim3 grid(std::min(65535, nt - t0), P);
     k_pchol<T><<<grid, NT, smem, st>>>((const TInfo*)pl.d_targets, tbeg + t0, truncate, tau, d_tab,
-                                    d_rtab, P, 3 * pl.nroles, pl.nroles);
+                                    d_rtab, P, 3 * pl.nroles, pl.nroles, d_fl);
+    ACR_LAUNCHED(1);
   }
-  ACR_CUDA(cudaGetLastError());
 }
 
 template <typename T>
 void launch_eig(const Plan& pl, int tbeg, int tend, double eps, int kc, int c_role,
-                T* const* d_tab, int* const* d_rtab, int P, int* d_err, cudaStream_t st) {
+                T* const* d_tab, int* const* d_rtab, int P, int* d_err, cudaStream_t st,
+                double* d_fl) {
   int nt = tend - tbeg;
   if (nt <= 0 || P <= 0) return;
   const size_t smem = 2 * CMAX * (CMAX + 1) * sizeof(double);
@@ -658,16 +670,17 @@ void launch_eig(const Plan& pl, int tbeg, int tend, double eps, int kc, int c_ro
   for (int t0 = 0; t0 < nt; t0 += 65535) {
     dim3 grid(std::min(65535, nt - t0), P);
     k_eig<T><<<grid, NT, smem, st>>>((const TInfo*)pl.d_targets, tbeg + t0, eps, kc, c_role, d_tab,
-                                  d_rtab, P, 3 * pl.nroles, pl.nroles, d_err);
+                                  d_rtab, P, 3 * pl.nroles, pl.nroles, d_err, d_fl);
+    ACR_LAUNCHED(1);
   }
-  ACR_CUDA(cudaGetLastError());
 }
 
 template <typename T>
-void launch_leaf_inv(T* const* d_dense, int64_t off, int lsz, int P, int* d_err, cudaStream_t st) {
+void launch_leaf_inv(T* const* d_dense, int64_t off, int lsz, int P, int* d_err, cudaStream_t st,
+                     double* d_fl) {
   if (P <= 0) return;
-  k_leaf_inv<T><<<P, NT, 0, st>>>(d_dense, off, lsz, d_err);
-  ACR_CUDA(cudaGetLastError());
+  k_leaf_inv<T><<<P, NT, 0, st>>>(d_dense, off, lsz, d_err, d_fl);
+  ACR_LAUNCHED(1);
 }
 
 template <typename T>
@@ -683,7 +696,7 @@ void launch_hscale(const StructDev& sd, T* const* out_dense, T* const* out_U, T*
     k_hscale_lr<T><<<dim3(sd.nl, P), 256, 0, st>>>(out_U, out_V, out_rank, x_U, x_V, x_rank,
                                                    rowscale, colscale, sd.linfo, sd.row0,
                                                    sd.col0, kc, sgn);
-  ACR_CUDA(cudaGetLastError());
+  ACR_LAUNCHED((sd.nd > 0) + (sd.nl > 0));
 }
 
 template <typename T>
@@ -697,17 +710,17 @@ void launch_plane_to_h(const StructDev& sd, const double* coef, int n, const int
   if (sd.nl > 0)
     k_plane_lr<T><<<dim3(sd.nl, P), 256, 0, st>>>(coef, n, d_planes, U, V, rank, sd.perm, sd.cpl,
                                                   sd.cptr, sd.linfo, sd.row0, sd.col0, kc);
-  ACR_CUDA(cudaGetLastError());
+  ACR_LAUNCHED((sd.nd > 0) + (sd.nl > 0));
 }
 
 #define ACR_INST(T)                                                                              \
   template void launch_ggemm<T>(const Plan&, int, int, T* const*, const int* const*, int,        \
-                                const double*, cudaStream_t);                                    \
+                                const double*, cudaStream_t, double*);                           \
   template void launch_pchol<T>(const Plan&, int, int, bool, double, T* const*, int* const*, int, \
-                                cudaStream_t);                                                   \
+                                cudaStream_t, double*);                                          \
   template void launch_eig<T>(const Plan&, int, int, double, int, int, T* const*, int* const*,   \
-                              int, int*, cudaStream_t);                                          \
-  template void launch_leaf_inv<T>(T* const*, int64_t, int, int, int*, cudaStream_t);            \
+                              int, int*, cudaStream_t, double*);                                 \
+  template void launch_leaf_inv<T>(T* const*, int64_t, int, int, int*, cudaStream_t, double*);   \
   template void launch_hscale<T>(const StructDev&, T* const*, T* const*, T* const*, int* const*, \
                                  T* const*, T* const*, T* const*, const int* const*,             \
                                  const double* const*, const double* const*, double, int, int,   \

@@ -1,0 +1,288 @@
+"""GPU parity tests: the CUDA path (through the C ABI) against the CPU oracle.
+
+Tolerances:
+* assembly, SpMV: FP64 with a different rounding order -> 1e-14 relative;
+* ACR apply, FP64 form: the GPU formats every block exactly like the
+  oracle (exact result, then truncation at eps) except that its range finder
+  discards directions below tau = max(1e-3 eps, 1e-7) of the sketch before
+  the final truncation; allowed difference 10 tau relative;
+* ACR apply, FP32 form: 1e-5 relative (factors in float, FP64 vectors);
+* Krylov solutions: the oracle's own SpMV must confirm ||f - A u|| <= rtol
+  ||f||, and ||u - u_ref|| <= 10 cond(A) rtol ||u_ref|| for the exact u_ref.
+"""
+import functools
+
+import numpy as np
+import pytest
+import scipy.sparse.linalg as sla
+
+from inputs import workload, codi_beta, uniform_rhs, gaussian_field_kappa
+from oracle.assembly import (stencil_poisson, stencil_codi, stencil_apply, stencil_matrix,
+                             plane_blocks, NAMES)
+from oracle.cr import cr_setup, cr_apply
+from oracle.hstructure import Structure
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def acr():
+    from paper_1712_08872_gb300 import _build
+    _build.build()
+    import paper_1712_08872_gb300 as pkg
+    pkg.load_library()
+    return pkg
+
+
+def T(x):
+    return torch.tensor(np.ascontiguousarray(x), dtype=torch.float64, device="cuda:0")
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def operator(acr, kind, n, seed=0):
+    if kind == "poisson":
+        kap = gaussian_field_kappa(n, seed)
+        st = stencil_poisson(kap, n)
+        coef = torch.empty(7 * n ** 3, dtype=torch.float64, device="cuda:0")
+        acr.acr_stencil_poisson(n, T(kap), coef)
+    else:
+        beta = codi_beta(n)
+        st = stencil_codi(beta, n)
+        coef = torch.empty(7 * n ** 3, dtype=torch.float64, device="cuda:0")
+        acr.acr_stencil_codi(n, T(beta), coef)
+    return st, coef
+
+
+@pytest.mark.parametrize("kind,n", [("poisson", 7), ("poisson", 16), ("codi", 9), ("codi", 32)])
+def test_assembly_and_spmv(acr, kind, n):
+    st, coef = operator(acr, kind, n)
+    ref = np.concatenate([st[k] for k in NAMES])
+    assert rel(coef.cpu().numpy(), ref) <= 1e-14
+    x = np.random.default_rng(1).standard_normal(n ** 3)
+    y = torch.empty(n ** 3, dtype=torch.float64, device="cuda:0")
+    acr.acr_spmv(n, coef, T(x), y)
+    assert rel(y.cpu().numpy(), stencil_apply(st, n, x)) <= 1e-14
+
+
+@pytest.mark.parametrize("kind,method", [("poisson", 0), ("codi", 1)])
+def test_plain_krylov(acr, kind, method):
+    n = 10
+    st, coef = operator(acr, kind, n)
+    f = uniform_rhs(n, 3)
+    u = torch.zeros(n ** 3, dtype=torch.float64, device="cuda:0")
+    info, status = acr.acr_krylov_solve_plain(n, coef, method, 20, 1e-10, 3000, T(f), u)
+    assert status == 0 and info.converged
+    uh = u.cpu().numpy()
+    assert rel(stencil_apply(st, n, uh), f) <= 1e-10 * 1.0001
+    A = stencil_matrix(st, n)
+    ue = sla.spsolve(A.tocsc(), f)
+    cond = np.linalg.cond(A.toarray())
+    assert rel(uh, ue) <= 10 * cond * 1e-10
+
+
+def cond_estimate(A, its=40):
+    """2-norm condition number estimate: power iteration on A^T A for
+    sigma_max, inverse power iteration with a sparse LU for sigma_min."""
+    lu = sla.splu(A.tocsc())
+    luT = sla.splu(A.T.tocsc())
+    x = np.random.default_rng(0).standard_normal(A.shape[0])
+    y = x.copy()
+    smax = smin_inv = 0.0
+    for _ in range(its):
+        x = A.T @ (A @ x)
+        smax = np.sqrt(np.linalg.norm(x))
+        x /= np.linalg.norm(x)
+        y = lu.solve(luT.solve(y))
+        smin_inv = np.sqrt(np.linalg.norm(y))
+        y /= np.linalg.norm(y)
+    return smax * smin_inv
+
+
+def tau(eps):
+    return max(1e-3 * eps, 1e-7)
+
+
+APPLY_CASES = [("poisson", 8, 1.0, 16, 1e-10), ("codi", 8, 2.0, 8, 1e-3),
+               ("poisson", 16, 1.0, 32, 1e-6), ("codi", 16, 2.0, 32, 1e-2),
+               ("poisson", 16, 2.0, 16, 1e-2)]
+# eta = 16 puts plane couplings inside admissible blocks (exact ranks up to
+# the interface length) and deepens the H-arithmetic; FP64 parity holds,
+# the FP32 form is checked by its FP64 Krylov outcome below.
+APPLY_CASES_FP64 = APPLY_CASES + [("codi", 16, 16.0, 32, 1e-2)]
+
+
+@pytest.mark.parametrize("kind,n,eta,leaf,eps,prec",
+                         [c + (0,) for c in APPLY_CASES_FP64] + [c + (1,) for c in APPLY_CASES])
+def test_acr_apply_matches_oracle(acr, kind, n, eta, leaf, eps, prec):
+    st, coef = operator(acr, kind, n, seed=2)
+    f = uniform_rhs(n, 4)
+    D, Ld, Ud = plane_blocks(st, n)
+    zo = cr_apply(cr_setup(D, Ld, Ud, Structure(n, eta, leaf), eps), f)
+    h = acr.Handle(n, coef, eps, eta, leaf, prec, 32)
+    z = torch.empty(n ** 3, dtype=torch.float64, device="cuda:0")
+    h.apply(T(f), z)
+    torch.cuda.synchronize()
+    err = rel(z.cpu().numpy(), zo)
+    tol = 10 * tau(eps) if prec == 0 else 1e-5
+    h.close()
+    assert err <= tol, err
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_acr_apply_transpose_matches_oracle(acr, prec):
+    n, eta, leaf, eps = 8, 2.0, 8, 1e-3
+    st, coef = operator(acr, "codi", n)
+    D, Ld, Ud = plane_blocks(st, n)
+    F = cr_setup(D, Ld, Ud, Structure(n, eta, leaf), eps)
+    N = n ** 3
+    Minv = np.stack([cr_apply(F, e) for e in np.eye(N)], axis=1)   # columns M^-1 e_j
+    r = uniform_rhs(n, 5)
+    want = Minv.T @ r
+    h = acr.Handle(n, coef, eps, eta, leaf, prec, 32)
+    z = torch.empty(N, dtype=torch.float64, device="cuda:0")
+    h.apply_transpose(T(r), z)
+    torch.cuda.synchronize()
+    err = rel(z.cpu().numpy(), want)
+    h.close()
+    assert err <= (10 * tau(eps) if prec == 0 else 1e-5), err
+
+
+def test_fp32_form_eta16_solves_to_fp64_accuracy(acr):
+    n = 16
+    st, coef = operator(acr, "codi", n)
+    f = uniform_rhs(n, 8)
+    h = acr.Handle(n, coef, 1e-2, 16.0, 32, 1, 32)
+    u = torch.zeros(n ** 3, dtype=torch.float64, device="cuda:0")
+    info, status = acr.acr_krylov_solve(h.h, coef, acr.ACR_GMRES, 30, 1e-8, 100, T(f), u)
+    torch.cuda.synchronize()
+    h.close()
+    assert status == 0 and info.iterations <= 6
+    assert rel(stencil_apply(st, n, u.cpu().numpy()), f) <= 1e-8 * 1.0001
+
+
+def test_exact_limit_equals_direct_solve(acr):
+    n = 16
+    st, coef = operator(acr, "codi", n)
+    f = uniform_rhs(n, 6)
+    ue = sla.spsolve(stencil_matrix(st, n).tocsc(), f)
+    h = acr.Handle(n, coef, 1e-10, 2.0, 16, 0, 48)
+    z = torch.empty(n ** 3, dtype=torch.float64, device="cuda:0")
+    h.apply(T(f), z)
+    torch.cuda.synchronize()
+    h.close()
+    assert rel(z.cpu().numpy(), ue) <= 1e-8
+
+
+def _solve_case(acr, name, n, prec, eta=2.0):
+    spec, cin, f = workload(name, n=n)
+    if spec["pde"] == "codi":
+        st = stencil_codi(cin, n)
+        coef = torch.empty(7 * n ** 3, dtype=torch.float64, device="cuda:0")
+        acr.acr_stencil_codi(n, T(cin), coef)
+    else:
+        st = stencil_poisson(cin, n)
+        coef = torch.empty(7 * n ** 3, dtype=torch.float64, device="cuda:0")
+        acr.acr_stencil_poisson(n, T(cin), coef)
+    h = acr.Handle(n, coef, spec["eps"], eta, spec["leaf"], prec, 32)
+    u = torch.zeros(n ** 3, dtype=torch.float64, device="cuda:0")
+    method = acr.ACR_GMRES if spec["krylov"] == "gmres" else acr.ACR_PCG
+    info, status = acr.acr_krylov_solve(h.h, coef, method, spec.get("restart", 30), spec["rtol"],
+                                        1000, T(f), u)
+    torch.cuda.synchronize()
+    h.close()
+    return spec, st, f, u.cpu().numpy(), info
+
+
+def test_config_poisson_grf_n16_dense_lu(acr):
+    """kappa = exp(GRF), n = 16, leaf 32, eta 1, eps 1e-6, PCG to 1e-10,
+    checked against a dense LU solve."""
+    spec, st, f, u, info = _solve_case(acr, "poisson_grf_n16", 16, 0, eta=1.0)
+    A = stencil_matrix(st, 16).toarray()
+    ue = np.linalg.solve(A, f)
+    assert rel(A @ u, f) <= spec["rtol"] * 1.0001
+    assert rel(u, ue) <= 10 * np.linalg.cond(A) * spec["rtol"]
+    assert info.iterations <= 5
+
+
+@pytest.mark.parametrize("name,n,prec", [("poisson_boxes_n64", 32, 0), ("poisson_boxes_n64", 32, 1),
+                                         ("codi_n128", 32, 0), ("codi_n128", 32, 1)])
+def test_config_recipes_small_grid(acr, name, n, prec):
+    spec, st, f, u, info = _solve_case(acr, name, n, prec)
+    A = stencil_matrix(st, n)
+    assert rel(A @ u, f) <= spec["rtol"] * 1.0001
+    ue, cond = _direct_and_cond(name, n)
+    assert rel(u, ue) <= 10 * cond * spec["rtol"]
+
+
+@functools.lru_cache(maxsize=None)
+def _direct_and_cond(name, n):
+    spec, cin, f = workload(name, n=n)
+    st = stencil_codi(cin, n) if spec["pde"] == "codi" else stencil_poisson(cin, n)
+    A = stencil_matrix(st, n)
+    return sla.splu(A.tocsc()).solve(f), cond_estimate(A, its=25)
+
+
+def test_full_size_codi_n128_fp32(acr):
+    """The benchmark workload at full size (n = 128, FP32 factors, GMRES(30)):
+    the oracle's own SpMV confirms the relative residual."""
+    spec, st, f, u, info = _solve_case(acr, "codi_n128", 128, 1)
+    assert info.converged
+    assert rel(stencil_apply(st, 128, u), f) <= spec["rtol"] * 1.0001
+
+
+def test_edge_cases(acr):
+    # n = 1 (one plane, one point) and n = 2
+    for n in (1, 2, 4):
+        st, coef = operator(acr, "poisson", n)
+        f = uniform_rhs(n, 7) if n > 1 else np.array([0.5])
+        h = acr.Handle(n, coef, 1e-8, 2.0, 4, 0, 8)
+        z = torch.empty(n ** 3, dtype=torch.float64, device="cuda:0")
+        h.apply(T(f), z)
+        torch.cuda.synchronize()
+        A = stencil_matrix(st, n).toarray()
+        assert rel(z.cpu().numpy(), np.linalg.solve(A, f)) <= 1e-10
+        # zero right-hand side
+        u = torch.ones(n ** 3, dtype=torch.float64, device="cuda:0")
+        info, status = acr.acr_krylov_solve(h.h, coef, 0, 0, 1e-8, 10,
+                                            torch.zeros_like(u), u)
+        assert status == 0 and float(u.abs().max()) == 0.0
+        h.close()
+
+
+def test_error_statuses(acr):
+    import ctypes
+    n = 16
+    st, coef = operator(acr, "codi", n)
+    with pytest.raises(acr.AcrError) as e:
+        acr.Handle(n, coef, 0.0, 2.0, 16)
+    assert e.value.status == 1
+    with pytest.raises(acr.AcrError) as e:
+        acr.Handle(n, coef, 1e-2, 2.0, 16, 0, 49)
+    assert e.value.status == 1
+    with pytest.raises(acr.AcrError) as e:          # leaves above 64 points
+        acr.Handle(n, coef, 1e-2, 2.0, 128)
+    assert e.value.status == 8
+    with pytest.raises(acr.AcrError) as e:          # rank cap 1 at eps 1e-10
+        acr.Handle(n, coef, 1e-10, 2.0, 16, 0, 1)
+    assert e.value.status == 5
+    lib = acr.load_library()
+    assert lib.acr_apply(None, None, None, 1, None) == 1
+    # the library stays usable after the errors
+    h = acr.Handle(n, coef, 1e-2, 2.0, 16)
+    h.close()
+
+
+def test_profile_counts(acr):
+    n = 16
+    st, coef = operator(acr, "codi", n)
+    h = acr.Handle(n, coef, 1e-2, 2.0, 16, 1, 16, flags=acr.ACR_FLAG_PROFILE)
+    p = h.profile()
+    info = h.info()
+    assert p.gemm.launches > 0 and p.gemm.flops > 0 and p.gemm.ms > 0
+    assert p.leaf_inv.launches > 0 and p.eig.launches > 0
+    assert info.apply_bytes > info.factor_bytes
+    h.close()
