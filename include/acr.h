@@ -186,6 +186,29 @@ acr_status acr_krylov_solve_plain(const acr_grid* grid, const double* coef, int3
                                   const double* f, double* u, acr_solve_info* info,
                                   cudaStream_t stream);
 
+/* Allocation-free variant of acr_krylov_solve_plain with method ACR_PCG
+ * (the paper has no counterpart: this serves callers that cannot call
+ * cudaMalloc where they solve, e.g. an application whose device memory is
+ * fully reserved by its own pool allocator, or a latency-critical loop that
+ * cannot afford the device synchronisation of cudaMalloc / cudaFree).
+ * Same arguments and results as acr_krylov_solve_plain(ACR_PCG), but every
+ * work vector and reduction buffer lives in one fixed 24 MiB device array
+ * that the library defines at file scope; each GPU that loads the library
+ * holds that array until the process exits.  Grids with more than
+ * acr_noalloc_max_unknowns() unknowns (about 6.2e5, n <= 85) are rejected
+ * with ACR_ERR_INVALID_ARG.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress); make that first call
+ * before any stream capture.  Every call shares the one array and keeps
+ * the previous call's contents; calls that overlap on the GPU (other
+ * streams, other host threads) race with each other.  The call reads a
+ * few scalars back per iteration and synchronises `stream`. */
+acr_status acr_krylov_solve_plain_noalloc(const acr_grid* grid, const double* coef, double rtol,
+                                          int32_t maxit, const double* f, double* u,
+                                          acr_solve_info* info, cudaStream_t stream);
+
+/* Largest number of unknowns acr_krylov_solve_plain_noalloc accepts. */
+int64_t acr_noalloc_max_unknowns(void);
+
 /* Setup statistics of a handle (host struct). */
 acr_status acr_get_setup_info(const acr_handle* h, acr_setup_info* info);
 

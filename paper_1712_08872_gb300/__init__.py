@@ -11,4 +11,5 @@ from .acr import (  # noqa: F401
     acr_apply, acr_apply_transpose, acr_krylov_solve, acr_krylov_solve_plain,
     acr_get_setup_info, acr_get_profile, acr_structure_query, ACR_FLAG_PROFILE,
     KernelStat, Profile, acr_destroy, acr_status_string, Handle, acr_launch_count,
+    acr_krylov_solve_plain_noalloc, acr_noalloc_max_unknowns,
 )

@@ -87,6 +87,8 @@ def load_library(path=LIB_PATH):
                              ctypes.POINTER(SolveInfo), _P],
         "acr_krylov_solve_plain": [ctypes.POINTER(Grid), _P, I32, I32, F64, I32, _P, _P,
                                    ctypes.POINTER(SolveInfo), _P],
+        "acr_krylov_solve_plain_noalloc": [ctypes.POINTER(Grid), _P, F64, I32, _P, _P,
+                                           ctypes.POINTER(SolveInfo), _P],
         "acr_get_setup_info": [_P, ctypes.POINTER(SetupInfo)],
         "acr_get_profile": [_P, ctypes.POINTER(Profile)],
         "acr_structure_query": [I32, F64, I32, I64p, _P, _P],
@@ -95,6 +97,8 @@ def load_library(path=LIB_PATH):
         fn = getattr(lib, name)
         fn.argtypes = args
         fn.restype = ctypes.c_int
+    lib.acr_noalloc_max_unknowns.argtypes = []
+    lib.acr_noalloc_max_unknowns.restype = ctypes.c_int64
     lib.acr_launch_count.argtypes = []
     lib.acr_launch_count.restype = ctypes.c_int64
     lib.acr_destroy.argtypes = [_P]
@@ -193,6 +197,21 @@ def acr_krylov_solve_plain(n, coef, method, restart, rtol, maxit, f, u, stream=N
     if check:
         _check(st, "acr_krylov_solve_plain")
     return info, st
+
+
+def acr_krylov_solve_plain_noalloc(n, coef, rtol, maxit, f, u, stream=None, check=True):
+    """Unpreconditioned FP64 CG that allocates nothing (see include/acr.h)."""
+    info = SolveInfo()
+    st = load_library().acr_krylov_solve_plain_noalloc(
+        ctypes.byref(_grid(n)), _dev(coef, None, "coef"), rtol, maxit, _dev(f, None, "f"),
+        _dev(u, None, "u"), ctypes.byref(info), _stream(stream))
+    if check:
+        _check(st, "acr_krylov_solve_plain_noalloc")
+    return info, st
+
+
+def acr_noalloc_max_unknowns():
+    return int(load_library().acr_noalloc_max_unknowns())
 
 
 def acr_get_setup_info(handle):
