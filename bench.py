@@ -316,6 +316,9 @@ def main():
                 "frac": None, "traffic": None, "kernel": dom, "launches": ds.launches,
                 "ms_total": ds.ms}
     roof["setup_breakdown_ms"] = {k: round(v.ms, 1) for k, v in stats.items()}
+    roof["gemm_stage_ms"] = {nm: round(prof.stage_ms[i], 1) for i, nm in enumerate(prof.STAGES)}
+    roof["gemm_stage_tflops"] = {nm: round(prof.stage_flops[i] / max(prof.stage_ms[i], 1e-9) / 1e9, 3)
+                                 for i, nm in enumerate(prof.STAGES)}
 
     # apply (hot loop of the solve): HBM roofline
     h = acr.acr_setup(n, coef, eps, eta, leaf, acr.ACR_FP32, args.rank_cap, stream)

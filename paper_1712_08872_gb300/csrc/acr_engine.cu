@@ -171,8 +171,8 @@ class Engine : public EngineBase {
 
   // ---- optional per-kernel-class profile (CUDA events around launches)
   cudaStream_t cur_st = 0;
-  double* d_fl = nullptr;                   // 5 counted-flop accumulators
-  struct Pend { int cls; cudaEvent_t a, b; };
+  double* d_fl = nullptr;                   // counted-flop accumulators: 5 classes, 12 stages
+  struct Pend { int cls; cudaEvent_t a, b; int tag; };
   std::vector<Pend> pend;
   std::vector<cudaEvent_t> evfree;
   cudaEvent_t ev() {
@@ -187,9 +187,9 @@ class Engine : public EngineBase {
   }
   double* fl(int cls) { return profiling ? d_fl + cls : nullptr; }
   template <class F>
-  void timed(int cls, F&& f) {
+  void timed(int cls, F&& f, int tag = -1) {
     if (!profiling) { f(); return; }
-    Pend pd{cls, ev(), ev()};
+    Pend pd{cls, ev(), ev(), tag};
     ACR_CUDA(cudaEventRecord(pd.a, cur_st));
     f();
     ACR_CUDA(cudaEventRecord(pd.b, cur_st));
@@ -205,6 +205,7 @@ class Engine : public EngineBase {
       ACR_CUDA(cudaEventElapsedTime(&ms, pd.a, pd.b));
       ks[pd.cls]->ms += ms;
       ks[pd.cls]->launches += 1;
+      if (pd.tag >= 0 && pd.tag < 12) prof.stage_ms[pd.tag] += ms;
       evfree.push_back(pd.a);
       evfree.push_back(pd.b);
     }
@@ -366,7 +367,8 @@ class Engine : public EngineBase {
       for (const Stage& sg : pl.stages) {
         if (sg.kind == ST_GEMM)
           timed(0, [&] { launch_ggemm<T>(pl, sg.beg, sg.end, d_tab, (const int* const*)d_rtab, pc,
-                                         d_coefs, st, fl(0)); });
+                                         d_coefs, st, sg.tag >= 0 ? fl(5 + sg.tag) : fl(0)); },
+                sg.tag);
         else if (sg.kind == ST_PCHOL || sg.kind == ST_PCHOL + 16)
           timed(1, [&] { launch_pchol<T>(pl, sg.beg, sg.end, sg.kind == ST_PCHOL, tau_orth(), d_tab,
                                          d_rtab, pc, st, fl(1)); });
@@ -535,9 +537,9 @@ void Engine<T>::setup(const double* coef, cudaStream_t st) {
   owned.push_back(d_err);
   ACR_CUDA(cudaMemset(d_err, 0, sizeof(int)));
   if (profiling) {
-    d_fl = (double*)dmalloc(5 * sizeof(double));
+    d_fl = (double*)dmalloc(17 * sizeof(double));
     owned.push_back(d_fl);
-    ACR_CUDA(cudaMemset(d_fl, 0, 5 * sizeof(double)));
+    ACR_CUDA(cudaMemset(d_fl, 0, 17 * sizeof(double)));
   }
   std::vector<int> allp(n);
   for (int k = 0; k < n; ++k) allp[k] = k;
@@ -582,8 +584,11 @@ void Engine<T>::setup(const double* coef, cudaStream_t st) {
     lev.L = curL;
     lev.U = curU;
     // a4: H-inverse of the red planes, in place
+    auto lvl_t0 = std::chrono::steady_clock::now();
     hinv_batch(lev.red, st);
     check_err(st);
+    auto lvl_t1 = std::chrono::steady_clock::now();
+    if (profiling && r < 16) prof.inv_ms[r] = std::chrono::duration<double, std::milli>(lvl_t1 - lvl_t0).count();
     // a5-a7: Schur updates of the black planes
     const int PB = (int)lev.black.size();
     std::vector<HM> newL(n), newU(n);
@@ -682,24 +687,35 @@ void Engine<T>::setup(const double* coef, cudaStream_t st) {
       }
     }
     check_err(st);
+    if (profiling && r < 16)
+      prof.upd_ms[r] = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - lvl_t1).count();
     for (int j : lev.black) { curL[j] = newL[j]; curU[j] = newU[j]; }
     levels.push_back(std::move(lev));
     s *= 2;
     ++r;
   }
   // a8: the last plane
-  hinv_batch({0}, st);
-  check_err(st);
+  {
+    auto t0 = std::chrono::steady_clock::now();
+    hinv_batch({0}, st);
+    check_err(st);
+    if (profiling && r < 16)
+      prof.inv_ms[r] = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  }
   ACR_CUDA(cudaEventRecord(e1, st));
   ACR_CUDA(cudaEventSynchronize(e1));
   float ms = 0;
   ACR_CUDA(cudaEventElapsedTime(&ms, e0, e1));
   if (profiling) {
     flush_prof();
-    double h[5];
+    double h[17];
     ACR_CUDA(cudaMemcpy(h, d_fl, sizeof(h), cudaMemcpyDeviceToHost));
     prof.gemm.flops = h[0]; prof.orth.flops = h[1]; prof.eig.flops = h[2];
     prof.leaf_inv.flops = h[3]; prof.other.flops = h[4];
+    for (int t = 0; t < 12; ++t) {
+      prof.stage_flops[t] = h[5 + t];
+      prof.gemm.flops += h[5 + t];
+    }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

@@ -74,8 +74,8 @@ struct Builder {
     P.items.push_back(it);
     P.groups.back().ie = (int)P.items.size();
   }
-  void stage(int kind, int beg, int end) {
-    if (end > beg) P.stages.push_back(Stage{kind, beg, end});
+  void stage(int kind, int beg, int end, int tag = -1) {
+    if (end > beg) P.stages.push_back(Stage{kind, beg, end, tag});
   }
 
   // ---------------------------------------------------------------- terms
@@ -152,7 +152,7 @@ struct Builder {
         }
       }
     }
-    stage(ST_GEMM, g0, (int)P.groups.size());
+    stage(ST_GEMM, g0, (int)P.groups.size(), TAG_M);
     // index M by (term, leaf node)
     std::unordered_map<int64_t, int64_t> moff_of;
     for (const MRef& m : mrefs) moff_of[(int64_t)m.term * (int64_t)S.bn.size() + m.leaf_node] = m.off;
@@ -227,7 +227,7 @@ struct Builder {
         P.flops_static += 2LL * lsz * lsz * lsz;
       }
     }
-    stage(ST_GEMM, g0, (int)P.groups.size());
+    stage(ST_GEMM, g0, (int)P.groups.size(), TAG_FACT);
   }
 
   // ---------------------------------------------------------------- phase 2
@@ -414,7 +414,7 @@ struct Builder {
                  (int)(1000003u * (uint32_t)(lt.node + 1)), li.col_off);
       }
     }
-    stage(ST_GEMM, gdense0, (int)P.groups.size());
+    stage(ST_GEMM, gdense0, (int)P.groups.size(), TAG_DENSE_S);
 
     // Y = sum_i coef_i X_i S_i   (dense items: X_i Omega[col rows])
     int g0 = (int)P.groups.size();
@@ -436,7 +436,7 @@ struct Builder {
         }
       }
     }
-    stage(ST_GEMM, g0, (int)P.groups.size());
+    stage(ST_GEMM, g0, (int)P.groups.size(), TAG_Y);
 
     // orthonormal basis of range(Y): G = Y^T Y, pivoted Cholesky, Q = Y T
     auto orth_pass = [&](bool from_y) {
@@ -449,7 +449,7 @@ struct Builder {
         begin_group(bscr(), ti.g_off, lt.p, pc, pc, -1);
         add_item(bscr(), src, ti.m, FL_T, bscr(), src, ti.m, 0, dconst(ti.m), pc, 0, 0);
       }
-      stage(ST_GEMM, gg, (int)P.groups.size());
+      stage(ST_GEMM, gg, (int)P.groups.size(), from_y ? TAG_G : TAG_G2);
       P.stages.push_back(Stage{ST_PCHOL, 0, (int)lts.size()});
       // record whether this pass truncates (first) or only re-orthogonalises
       if (!from_y) P.stages.back().kind = ST_PCHOL + 16;
@@ -466,7 +466,7 @@ struct Builder {
           add_item(bscr(), src + r0, ti.m, 0, bscr(), ti.t_off, lt.p, 0, pin, dconst(tr), 0, 0);
         }
       }
-      stage(ST_GEMM, gg, (int)P.groups.size());
+      stage(ST_GEMM, gg, (int)P.groups.size(), from_y ? TAG_Q : TAG_Q2);
     };
     orth_pass(true);
     if (pp.cholqr2) {
@@ -486,7 +486,7 @@ struct Builder {
                  dconst(li.xrows), kd, 0, 0);
       }
     }
-    stage(ST_GEMM, g0, (int)P.groups.size());
+    stage(ST_GEMM, g0, (int)P.groups.size(), TAG_P);
 
     // B^T = sum_i coef_i Z_i P_i   (n x r)
     g0 = (int)P.groups.size();
@@ -508,7 +508,7 @@ struct Builder {
         }
       }
     }
-    stage(ST_GEMM, g0, (int)P.groups.size());
+    stage(ST_GEMM, g0, (int)P.groups.size(), TAG_BT);
 
     // H = (B^T)^T B^T   (r x r), core eigen-decomposition
     g0 = (int)P.groups.size();
@@ -518,7 +518,7 @@ struct Builder {
       begin_group(bscr(), ti.h_off, lts[i].p, rr, rr, -1);
       add_item(bscr(), lts[i].bt, ti.n, FL_T, bscr(), lts[i].bt, ti.n, 0, dconst(ti.n), rr, 0, 0);
     }
-    stage(ST_GEMM, g0, (int)P.groups.size());
+    stage(ST_GEMM, g0, (int)P.groups.size(), TAG_H);
     P.stages.push_back(Stage{ST_EIG, 0, (int)lts.size()});
 
     // U = Q W_k, V = B^T W_k into C
@@ -538,7 +538,7 @@ struct Builder {
         add_item(bscr(), lts[i].bt + r0, ti.n, 0, bscr(), ti.w_off, lts[i].p, 0, rr, dconst(tr), 0, 0);
       }
     }
-    stage(ST_GEMM, g0, (int)P.groups.size());
+    stage(ST_GEMM, g0, (int)P.groups.size(), TAG_UV);
     (void)capsum_max;
   }
 };

@@ -73,7 +73,23 @@ struct TInfo {
 };
 
 enum StageKind { ST_GEMM = 0, ST_PCHOL = 1, ST_EIG = 2 };
-struct Stage { int kind; int beg, end; };
+// what a GEMM stage computes (for profiling)
+enum StageTag {
+  TAG_M = 0,       // phase 1: small inner products U^T V
+  TAG_FACT = 1,    // phase 1: term factors B^T V, A U, dense products
+  TAG_DENSE_S = 2, // dense target sums and sketches Z^T Omega
+  TAG_Y = 3,       // sketch Y
+  TAG_G = 4,       // Gram of the sketch
+  TAG_Q = 5,       // basis Q = Y T
+  TAG_G2 = 6,      // second Gram
+  TAG_Q2 = 7,      // re-orthogonalised basis
+  TAG_P = 8,       // X^T Q
+  TAG_BT = 9,      // B^T = S^T Q
+  TAG_H = 10,      // core Gram
+  TAG_UV = 11,     // recomposition
+  NTAGS = 12
+};
+struct Stage { int kind; int beg, end; int tag = -1; };
 
 // Operand roles: role r owns buffers 3r (dense), 3r+1 (U), 3r+2 (V) and
 // rank buffer r.  The scratch real buffer is 3*nroles, the scratch rank

@@ -21,7 +21,6 @@ namespace acr {
 namespace {
 
 constexpr int TILE = 64;
-constexpr int KT = 16;
 constexpr int NT = 256;
 
 __device__ __forceinline__ int dimv(int st, int rb, int ri, const int* const* rtab, int P, int p) {
@@ -40,6 +39,24 @@ __device__ __forceinline__ double omega(uint32_t seed, uint32_t row, uint32_t co
   return (double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0;
 }
 
+constexpr int STAGE_BYTES = 36864;   // shared staging of one K-chunk (A and B panels)
+
+// One CTA computes the (m x n) output tile of one group for one plane:
+//   C = beta C + sum_items coef * op(A)[rows] op(B)
+// Large tiles (m, n > 32) use 4x4 register blocking over 64x64; every other
+// tile spreads its m*n outputs over the threads and, when there are fewer
+// outputs than threads, splits each K-chunk across the spare threads and
+// reduces the partial sums in shared memory.  K-chunks are exact (no zero
+// padding) and sized to the staging buffer, so thin long products stream
+// their operands in a few large coalesced chunks.
+// One CTA computes the (m x n) output tile of one group for one plane:
+//   C = beta C + sum_items coef * op(A)[rows] op(B)
+// Items are concatenated along K in a shared staging buffer (each item's
+// coefficient folded into its A panel, rows outside the item zero), so a
+// group of many thin items costs one barrier pair per full chunk.  Large
+// tiles (m, n > 32) use 4x4 register blocking over 64x64; smaller tiles
+// spread their outputs over the threads and split each chunk's K across the
+// spare threads, reducing the partial sums in shared memory at the end.
 template <typename T, typename Acc>
 __global__ void __launch_bounds__(NT) k_ggemm(const GGroup* __restrict__ groups,
                                               const GItem* __restrict__ items,
@@ -56,118 +73,196 @@ __global__ void __launch_bounds__(NT) k_ggemm(const GGroup* __restrict__ groups,
   const int n = dimv(G.n_st, G.n_rb, G.n_ri, rtab, P, p);
   if (m <= 0 || n <= 0) return;
   C += G.coff;
-  __shared__ Acc As[KT][TILE + 1];
-  __shared__ Acc Bs[KT][TILE + 1];
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  Acc acc[4][4];
-#pragma unroll
-  for (int a = 0; a < 4; ++a)
-#pragma unroll
-    for (int b = 0; b < 4; ++b) acc[a][b] = Acc(0);
+  constexpr int SE = STAGE_BYTES / sizeof(Acc);
+  __shared__ __align__(16) unsigned char stage_raw[STAGE_BYTES];
+  __shared__ Acc red[NT];
+  Acc* sm = reinterpret_cast<Acc*>(stage_raw);
+  const Acc beta = G.beta >= 0 ? (Acc)coefs[G.beta] : Acc(0);
+  const bool blocked = (m > 32 && n > 32);
+  const int lda_s = blocked ? TILE + 1 : m + 1;
+  const int ldb_s = blocked ? TILE + 1 : n + 1;
+  const int KC = SE / (lda_s + ldb_s);
+  Acc* As = sm;                 // As[kk * lda_s + i]
+  Acc* Bs = sm + KC * lda_s;    // Bs[kk * ldb_s + j]
 
+  // thread roles
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;   // blocked
+  const int nout = m * n;
+  int OL = 1;
+  while (OL < nout && OL < NT) OL <<= 1;
+  const int S = blocked ? 1 : NT / OL;
+  const int lane = threadIdx.x % OL, slice = threadIdx.x / OL;
+  const int Q = (nout + OL - 1) / OL;
+  Acc acc[16];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) acc[q] = Acc(0);
+
+  auto compute = [&](int kfill) {
+    __syncthreads();
+    if (blocked) {
+      for (int kk = 0; kk < kfill; ++kk) {
+        Acc av[4], bv[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) av[a] = As[kk * lda_s + ty + 16 * a];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) bv[b] = Bs[kk * ldb_s + tx + 16 * b];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) acc[a * 4 + b] += av[a] * bv[b];
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        if (q >= Q) break;
+        const int o = lane + q * OL;
+        if (o >= nout) break;
+        const Acc* ap = As + (o % m);
+        const Acc* bp = Bs + (o / m);
+        Acc s0 = Acc(0), s1 = Acc(0), s2 = Acc(0), s3 = Acc(0);
+        int kk = slice;
+        for (; kk + 3 * S < kfill; kk += 4 * S) {
+          s0 += ap[kk * lda_s] * bp[kk * ldb_s];
+          s1 += ap[(kk + S) * lda_s] * bp[(kk + S) * ldb_s];
+          s2 += ap[(kk + 2 * S) * lda_s] * bp[(kk + 2 * S) * ldb_s];
+          s3 += ap[(kk + 3 * S) * lda_s] * bp[(kk + 3 * S) * ldb_s];
+        }
+        for (; kk < kfill; kk += S) s0 += ap[kk * lda_s] * bp[kk * ldb_s];
+        acc[q] += (s0 + s1) + (s2 + s3);
+      }
+    }
+    __syncthreads();
+  };
+
+  int kfill = 0;
   for (int it = G.ib; it < G.ie; ++it) {
     const GItem I = items[it];
     if (I.guard0 >= 0 && !tab[I.guard0 * P + p]) continue;
     if (I.guard1 >= 0 && !tab[I.guard1 * P + p]) continue;
     const T* A = nullptr;
     const T* B = nullptr;
-    if (I.abuf >= 0) {
-      A = tab[I.abuf * P + p];
-      if (!A) continue;
-      A += I.aoff;
-    }
-    if (I.bbuf >= 0) {
-      B = tab[I.bbuf * P + p];
-      if (!B) continue;
-      B += I.boff;
-    }
+    if (I.abuf >= 0) { A = tab[I.abuf * P + p]; if (!A) continue; A += I.aoff; }
+    if (I.bbuf >= 0) { B = tab[I.bbuf * P + p]; if (!B) continue; B += I.boff; }
     const int k = dimv(I.k_st, I.k_rb, I.k_ri, rtab, P, p);
     const int rows = dimv(I.r_st, I.r_rb, I.r_ri, rtab, P, p);
     if (k <= 0 || rows <= 0) continue;
     const Acc cf = (Acc)coefs[I.coef];
     const int r0 = I.row_off;
-    fl += (I.aflags & FL_IDENT) || (I.bflags & FL_IDENT) ? (double)rows * n : 2.0 * rows * n * k;
-    if (I.aflags & FL_IDENT) {   // C(r0+i, j) += cf * B(i, j)
+    if ((I.aflags & FL_IDENT) || (I.bflags & FL_IDENT)) {
+      // C(r0+i, j) += cf * B(i, j)  or  cf * A(i, j): straight into the accumulators
+      fl += (double)rows * n;
+      const bool ai = I.aflags & FL_IDENT;
+      if (blocked) {
 #pragma unroll
-      for (int a = 0; a < 4; ++a) {
-        const int i = ty + 16 * a - r0;
-        if (i < 0 || i >= rows) continue;
+        for (int a = 0; a < 4; ++a) {
+          const int i = ty + 16 * a - r0;
+          if (i < 0 || i >= rows) continue;
 #pragma unroll
-        for (int b = 0; b < 4; ++b) {
-          const int j = tx + 16 * b;
-          if (j < n) acc[a][b] += cf * (Acc)B[i + (int64_t)j * I.ldb];
+          for (int b = 0; b < 4; ++b) {
+            const int j = tx + 16 * b;
+            if (j < n)
+              acc[a * 4 + b] += cf * (ai ? (Acc)B[i + (int64_t)j * I.ldb] : (Acc)A[i + (int64_t)j * I.lda]);
+          }
+        }
+      } else if (slice == 0) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          if (q >= Q) break;
+          const int o = lane + q * OL;
+          if (o >= nout) break;
+          const int i = o % m - r0, j = o / m;
+          if (i < 0 || i >= rows) continue;
+          acc[q] += cf * (ai ? (Acc)B[i + (int64_t)j * I.ldb] : (Acc)A[i + (int64_t)j * I.lda]);
         }
       }
       continue;
     }
-    if (I.bflags & FL_IDENT) {   // C(r0+i, j) += cf * A(i, j)
-#pragma unroll
-      for (int a = 0; a < 4; ++a) {
-        const int i = ty + 16 * a - r0;
-        if (i < 0 || i >= rows) continue;
-#pragma unroll
-        for (int b = 0; b < 4; ++b) {
-          const int j = tx + 16 * b;
-          if (j < n) acc[a][b] += cf * (Acc)A[i + (int64_t)j * I.lda];
+    fl += 2.0 * rows * n * k;
+    const bool at = I.aflags & FL_T, bt = I.bflags & FL_T, bo = I.bflags & FL_OMEGA;
+    const bool full = (r0 == 0 && rows >= m);
+    for (int k0 = 0; k0 < k;) {
+      const int t = min(k - k0, KC - kfill);
+      // A panel -> As[(kfill + kk) * lda_s + r0 + i], zero elsewhere in those columns
+      if (!full)
+        for (int e = threadIdx.x; e < t * m; e += NT) {
+          const int kk = e / m, i = e - kk * m;
+          if (i < r0 || i >= r0 + rows) As[(kfill + kk) * lda_s + i] = Acc(0);
+        }
+      if (at) {
+        for (int e = threadIdx.x; e < rows * t; e += NT) {
+          const int i = e / t, kk = e - i * t;
+          As[(kfill + kk) * lda_s + r0 + i] = cf * (Acc)A[(k0 + kk) + (int64_t)i * I.lda];
+        }
+      } else {
+        for (int e = threadIdx.x; e < rows * t; e += NT) {
+          const int kk = e / rows, i = e - kk * rows;
+          As[(kfill + kk) * lda_s + r0 + i] = cf * (Acc)A[i + (int64_t)(k0 + kk) * I.lda];
         }
       }
-      continue;
-    }
-    const bool at = I.aflags & FL_T;
-    const bool bt = I.bflags & FL_T;
-    const bool bo = I.bflags & FL_OMEGA;
-    for (int k0 = 0; k0 < k; k0 += KT) {
-      // A tile: As[kk][i] = cf * op(A)(i - r0, k0 + kk)
-      for (int e = threadIdx.x; e < KT * TILE; e += NT) {
-        int i, kk;
-        if (at) { kk = e % KT; i = e / KT; } else { i = e % TILE; kk = e / TILE; }
-        const int ia = i - r0, ka = k0 + kk;
-        Acc v = Acc(0);
-        if (ia >= 0 && ia < rows && ka < k)
-          v = at ? (Acc)A[ka + (int64_t)ia * I.lda] : (Acc)A[ia + (int64_t)ka * I.lda];
-        As[kk][i] = cf * v;
-      }
-      // B tile: Bs[kk][j] = op(B)(k0 + kk, j)
-      for (int e = threadIdx.x; e < KT * TILE; e += NT) {
-        int j, kk;
-        if (bt) { j = e % TILE; kk = e / TILE; } else { kk = e % KT; j = e / KT; }
-        const int kb = k0 + kk;
-        Acc v = Acc(0);
-        if (kb < k && j < n) {
-          if (bo) v = (Acc)omega((uint32_t)I.seed, (uint32_t)(I.omega_row0 + kb), (uint32_t)j);
-          else v = bt ? (Acc)B[j + (int64_t)kb * I.ldb] : (Acc)B[kb + (int64_t)j * I.ldb];
+      // B panel -> Bs[(kfill + kk) * ldb_s + j]
+      if (bo) {
+        for (int e = threadIdx.x; e < t * n; e += NT) {
+          const int kk = e / n, j = e - kk * n;
+          Bs[(kfill + kk) * ldb_s + j] =
+              (Acc)omega((uint32_t)I.seed, (uint32_t)(I.omega_row0 + k0 + kk), (uint32_t)j);
         }
-        Bs[kk][j] = v;
+      } else if (bt) {
+        for (int e = threadIdx.x; e < t * n; e += NT) {
+          const int kk = e / n, j = e - kk * n;
+          Bs[(kfill + kk) * ldb_s + j] = (Acc)B[j + (int64_t)(k0 + kk) * I.ldb];
+        }
+      } else {
+        for (int e = threadIdx.x; e < t * n; e += NT) {
+          const int j = e / t, kk = e - j * t;
+          Bs[(kfill + kk) * ldb_s + j] = (Acc)B[(k0 + kk) + (int64_t)j * I.ldb];
+        }
       }
-      __syncthreads();
-#pragma unroll
-      for (int kk = 0; kk < KT; ++kk) {
-        Acc av[4], bv[4];
-#pragma unroll
-        for (int a = 0; a < 4; ++a) av[a] = As[kk][ty + 16 * a];
-#pragma unroll
-        for (int b = 0; b < 4; ++b) bv[b] = Bs[kk][tx + 16 * b];
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-          for (int b = 0; b < 4; ++b) acc[a][b] += av[a] * bv[b];
+      kfill += t;
+      k0 += t;
+      if (kfill == KC) {
+        compute(kfill);
+        kfill = 0;
       }
-      __syncthreads();
     }
   }
-  const Acc beta = G.beta >= 0 ? (Acc)coefs[G.beta] : Acc(0);
+  if (kfill > 0) compute(kfill);
+
+  if (blocked) {
 #pragma unroll
-  for (int a = 0; a < 4; ++a) {
-    const int i = ty + 16 * a;
-    if (i >= m) continue;
+    for (int a = 0; a < 4; ++a) {
+      const int i = ty + 16 * a;
+      if (i >= m) continue;
 #pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      const int j = tx + 16 * b;
-      if (j >= n) continue;
-      T* c = C + i + (int64_t)j * G.ldc;
-      Acc v = acc[a][b];
-      if (G.beta >= 0) v += beta * (Acc)(*c);
-      *c = (T)v;
+      for (int b = 0; b < 4; ++b) {
+        const int j = tx + 16 * b;
+        if (j >= n) continue;
+        T* c = C + i + (int64_t)j * G.ldc;
+        Acc v = acc[a * 4 + b];
+        if (G.beta >= 0) v += beta * (Acc)(*c);
+        *c = (T)v;
+      }
+    }
+  } else {
+    if (S > 1) {   // Q == 1: one output per lane, reduce the K slices
+      red[threadIdx.x] = acc[0];
+      __syncthreads();
+      if (slice == 0) {
+        Acc s2 = Acc(0);
+        for (int t2 = 0; t2 < S; ++t2) s2 += red[lane + t2 * OL];
+        acc[0] = s2;
+      }
+    }
+    if (slice == 0) {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        if (q >= Q) break;
+        const int o = lane + q * OL;
+        if (o >= nout) break;
+        T* c = C + (o % m) + (int64_t)(o / m) * G.ldc;
+        Acc v = acc[q];
+        if (G.beta >= 0) v += beta * (Acc)(*c);
+        *c = (T)v;
+      }
     }
   }
   if (flops && threadIdx.x == 0 && fl > 0.0) atomicAdd(flops, fl);
