@@ -114,13 +114,13 @@ typedef struct {
   acr_kernel_stat eig;       /* Jacobi recompression cores (k_eig), FP64 */
   acr_kernel_stat leaf_inv;  /* dense leaf inverses (k_leaf_inv), FP64 */
   acr_kernel_stat other;     /* conversion, scaling */
-  /* k_ggemm time and counted flops per plan stage: 0 inner products U^T V of
-   * phase 1, 1 term factors (H-matrix x block products, dense products),
-   * 2 dense-leaf sums and sketches Z^T Omega, 3 sketch Y, 4 first Gram,
-   * 5 first basis, 6 second Gram, 7 second basis, 8 X^T Q, 9 B^T, 10 core
-   * Gram, 11 recomposition U = Q W, V = B^T W */
-  double stage_ms[12];
-  double stage_flops[12];
+  /* grouped-GEMM time and counted flops per plan stage: 0 inner products
+   * U^T V of phase 1, 1 term factors (H-matrix x block products, dense
+   * products), 2 dense-leaf sums, 3 sketches Z^T Omega, 4 sketch Y, 5 first
+   * Gram, 6 first basis, 7 second Gram, 8 second basis, 9 X^T Q, 10 B^T,
+   * 11 core Gram, 12 recomposition U = Q W, V = B^T W; 13..15 unused */
+  double stage_ms[16];
+  double stage_flops[16];
   /* wall time (CUDA events) of each CR level's H-inversion batch and of its
    * Schur-update batch; index = level, the last plane's inversion is in
    * inv_ms[levels] */

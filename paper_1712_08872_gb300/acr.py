@@ -55,11 +55,11 @@ class KernelStat(ctypes.Structure):
 class Profile(ctypes.Structure):
     _fields_ = [("gemm", KernelStat), ("orth", KernelStat), ("eig", KernelStat),
                 ("leaf_inv", KernelStat), ("other", KernelStat),
-                ("stage_ms", ctypes.c_double * 12), ("stage_flops", ctypes.c_double * 12),
+                ("stage_ms", ctypes.c_double * 16), ("stage_flops", ctypes.c_double * 16),
                 ("inv_ms", ctypes.c_double * 16), ("upd_ms", ctypes.c_double * 16)]
 
-    STAGES = ("inner_UtV", "term_factors", "dense_and_sketch_S", "sketch_Y", "gram1", "basis1",
-              "gram2", "basis2", "XtQ", "Bt", "core_gram", "recompose")
+    STAGES = ("inner_UtV", "term_factors", "dense_sums", "sketch_S", "sketch_Y", "gram1",
+              "basis1", "gram2", "basis2", "XtQ", "Bt", "core_gram", "recompose")
 
 
 class SolveInfo(ctypes.Structure):

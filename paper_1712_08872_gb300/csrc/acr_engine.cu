@@ -21,6 +21,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "acr.h"
 #include "acr_internal.h"
 
@@ -205,7 +207,7 @@ class Engine : public EngineBase {
       ACR_CUDA(cudaEventElapsedTime(&ms, pd.a, pd.b));
       ks[pd.cls]->ms += ms;
       ks[pd.cls]->launches += 1;
-      if (pd.tag >= 0 && pd.tag < 12) prof.stage_ms[pd.tag] += ms;
+      if (pd.tag >= 0 && pd.tag < 16) prof.stage_ms[pd.tag] += ms;
       evfree.push_back(pd.a);
       evfree.push_back(pd.b);
     }
@@ -367,7 +369,8 @@ class Engine : public EngineBase {
       for (const Stage& sg : pl.stages) {
         if (sg.kind == ST_GEMM)
           timed(0, [&] { launch_ggemm<T>(pl, sg.beg, sg.end, d_tab, (const int* const*)d_rtab, pc,
-                                         d_coefs, st, sg.tag >= 0 ? fl(5 + sg.tag) : fl(0)); },
+                                         d_coefs, st, sg.tag >= 0 ? fl(5 + sg.tag) : fl(0),
+                                         sg.tag); },
                 sg.tag);
         else if (sg.kind == ST_PCHOL || sg.kind == ST_PCHOL + 16)
           timed(1, [&] { launch_pchol<T>(pl, sg.beg, sg.end, sg.kind == ST_PCHOL, tau_orth(), d_tab,
@@ -537,9 +540,9 @@ void Engine<T>::setup(const double* coef, cudaStream_t st) {
   owned.push_back(d_err);
   ACR_CUDA(cudaMemset(d_err, 0, sizeof(int)));
   if (profiling) {
-    d_fl = (double*)dmalloc(17 * sizeof(double));
+    d_fl = (double*)dmalloc(21 * sizeof(double));
     owned.push_back(d_fl);
-    ACR_CUDA(cudaMemset(d_fl, 0, 17 * sizeof(double)));
+    ACR_CUDA(cudaMemset(d_fl, 0, 21 * sizeof(double)));
   }
   std::vector<int> allp(n);
   for (int k = 0; k < n; ++k) allp[k] = k;
@@ -585,8 +588,14 @@ void Engine<T>::setup(const double* coef, cudaStream_t st) {
     lev.U = curU;
     // a4: H-inverse of the red planes, in place
     auto lvl_t0 = std::chrono::steady_clock::now();
+    char rname[16];
+    snprintf(rname, sizeof(rname), "inv%d", r);
+    nvtxRangePushA(rname);   // trace ranges: invN / updN per CR level
     hinv_batch(lev.red, st);
     check_err(st);
+    nvtxRangePop();
+    snprintf(rname, sizeof(rname), "upd%d", r);
+    nvtxRangePushA(rname);
     auto lvl_t1 = std::chrono::steady_clock::now();
     if (profiling && r < 16) prof.inv_ms[r] = std::chrono::duration<double, std::milli>(lvl_t1 - lvl_t0).count();
     // a5-a7: Schur updates of the black planes
@@ -687,6 +696,7 @@ void Engine<T>::setup(const double* coef, cudaStream_t st) {
       }
     }
     check_err(st);
+    nvtxRangePop();
     if (profiling && r < 16)
       prof.upd_ms[r] = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - lvl_t1).count();
     for (int j : lev.black) { curL[j] = newL[j]; curU[j] = newU[j]; }
@@ -708,11 +718,11 @@ void Engine<T>::setup(const double* coef, cudaStream_t st) {
   ACR_CUDA(cudaEventElapsedTime(&ms, e0, e1));
   if (profiling) {
     flush_prof();
-    double h[17];
+    double h[21];
     ACR_CUDA(cudaMemcpy(h, d_fl, sizeof(h), cudaMemcpyDeviceToHost));
     prof.gemm.flops = h[0]; prof.orth.flops = h[1]; prof.eig.flops = h[2];
     prof.leaf_inv.flops = h[3]; prof.other.flops = h[4];
-    for (int t = 0; t < 12; ++t) {
+    for (int t = 0; t < 16; ++t) {
       prof.stage_flops[t] = h[5 + t];
       prof.gemm.flops += h[5 + t];
     }

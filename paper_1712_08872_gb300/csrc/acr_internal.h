@@ -43,7 +43,8 @@ struct CudaError {
 // Grouped small GEMMs of a plan stage: one CTA per (group, plane).
 template <typename T>
 void launch_ggemm(const Plan& pl, int gbeg, int gend, T* const* d_tab, const int* const* d_rtab,
-                  int P, const double* d_coefs, cudaStream_t st, double* d_flops = nullptr);
+                  int P, const double* d_coefs, cudaStream_t st, double* d_flops = nullptr,
+                  int tag = -1);
 
 // Pivoted-Cholesky orthonormalisation cores (FP64) of plan targets.
 template <typename T>

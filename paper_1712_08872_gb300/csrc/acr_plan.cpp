@@ -405,7 +405,9 @@ struct Builder {
     }
     for (size_t i = 0; i < lts.size(); ++i) P.targets[i].seed = (int)(1000003u * (uint32_t)(lts[i].node + 1));
 
-    // S_i = Z_i^T Omega (k_i x p)     [same stage as the dense targets]
+    stage(ST_GEMM, gdense0, (int)P.groups.size(), TAG_DENSE);
+    // S_i = Z_i^T Omega (k_i x p)
+    const int gs0 = (int)P.groups.size();
     for (LT& lt : lts) {
       for (const LItem& li : lt.items) {
         if (li.dense) continue;
@@ -414,7 +416,7 @@ struct Builder {
                  (int)(1000003u * (uint32_t)(lt.node + 1)), li.col_off);
       }
     }
-    stage(ST_GEMM, gdense0, (int)P.groups.size(), TAG_DENSE_S);
+    stage(ST_GEMM, gs0, (int)P.groups.size(), TAG_S);
 
     // Y = sum_i coef_i X_i S_i   (dense items: X_i Omega[col rows])
     int g0 = (int)P.groups.size();

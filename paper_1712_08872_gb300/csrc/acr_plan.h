@@ -77,18 +77,25 @@ enum StageKind { ST_GEMM = 0, ST_PCHOL = 1, ST_EIG = 2 };
 enum StageTag {
   TAG_M = 0,       // phase 1: small inner products U^T V
   TAG_FACT = 1,    // phase 1: term factors B^T V, A U, dense products
-  TAG_DENSE_S = 2, // dense target sums and sketches Z^T Omega
-  TAG_Y = 3,       // sketch Y
-  TAG_G = 4,       // Gram of the sketch
-  TAG_Q = 5,       // basis Q = Y T
-  TAG_G2 = 6,      // second Gram
-  TAG_Q2 = 7,      // re-orthogonalised basis
-  TAG_P = 8,       // X^T Q
-  TAG_BT = 9,      // B^T = S^T Q
-  TAG_H = 10,      // core Gram
-  TAG_UV = 11,     // recomposition
-  NTAGS = 12
+  TAG_DENSE = 2,   // dense target sums
+  TAG_S = 3,       // sketches Z^T Omega
+  TAG_Y = 4,       // sketch Y
+  TAG_G = 5,       // Gram of the sketch
+  TAG_Q = 6,       // basis Q = Y T
+  TAG_G2 = 7,      // second Gram
+  TAG_Q2 = 8,      // re-orthogonalised basis
+  TAG_P = 9,       // X^T Q
+  TAG_BT = 10,     // B^T = S^T Q
+  TAG_H = 11,      // core Gram
+  TAG_UV = 12,     // recomposition
+  NTAGS = 13
 };
+// Stages whose items all read A transposed and B untransposed (or omega),
+// i.e. both operands contiguous along the contraction, rows == m, no offset.
+inline bool tag_is_dot(int t) {
+  return t == TAG_M || t == TAG_S || t == TAG_G || t == TAG_G2 || t == TAG_P || t == TAG_H;
+}
+
 struct Stage { int kind; int beg, end; int tag = -1; };
 
 // Operand roles: role r owns buffers 3r (dense), 3r+1 (U), 3r+2 (V) and

@@ -29,14 +29,28 @@ __device__ __forceinline__ int dimv(int st, int rb, int ri, const int* const* rt
   return r ? r[ri] : 0;
 }
 
-// counter-based hash -> uniform in [-1, 1) (SplitMix64 finaliser)
-__device__ __forceinline__ double omega(uint32_t seed, uint32_t row, uint32_t col) {
-  uint64_t z = ((uint64_t)seed << 40) ^ ((uint64_t)row << 16) ^ (uint64_t)col;
-  z += 0x9E3779B97F4A7C15ull;
-  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-  z ^= z >> 31;
-  return (double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0;
+// Sketch matrix Omega of the range finder: entries uniform in (-1, 1) on a
+// 2^-15 grid (never 0); entry (row, col) takes the low or high 16 bits of a
+// 32-bit counter-based hash of (seed, row, col / 2) (the "lowbias32"
+// integer finaliser), so one hash serves two columns.  Continuous-valued
+// entries keep small restrictions of Omega nonsingular, which the range
+// finder's exactness for low stacked ranks relies on.
+__device__ __forceinline__ uint32_t omega_bits(uint32_t seed, uint32_t row, uint32_t word) {
+  uint32_t x = seed ^ (row * 0x9E3779B9u) ^ (word * 0x85EBCA6Bu);
+  x ^= x >> 16;
+  x *= 0x7FEB352Du;
+  x ^= x >> 15;
+  x *= 0x846CA68Bu;
+  x ^= x >> 16;
+  return x;
+}
+// (float arithmetic is exact here: a 16-bit integer plus 1/2, times 2^-15)
+__device__ __forceinline__ float omega_half(uint32_t bits, uint32_t col) {
+  const uint32_t h = (col & 1u) ? (bits >> 16) : (bits & 0xFFFFu);
+  return ((float)h + 0.5f) * (1.0f / 32768.0f) - 1.0f;
+}
+__device__ __forceinline__ float omega(uint32_t seed, uint32_t row, uint32_t col) {
+  return omega_half(omega_bits(seed, row, col >> 1), col);
 }
 
 constexpr int STAGE_BYTES = 36864;   // shared staging of one K-chunk (A and B panels)
@@ -266,6 +280,138 @@ __global__ void __launch_bounds__(NT) k_ggemm(const GGroup* __restrict__ groups,
     }
   }
   if (flops && threadIdx.x == 0 && fl > 0.0) atomicAdd(flops, fl);
+}
+
+// Stages whose items read A transposed and B untransposed (or the sketch
+// hash), so both operands are contiguous along the contraction: U^T V,
+// Z^T Omega, X^T Q and the Grams.  Each warp owns a 4x4 output sub-tile and
+// a slice of K; lanes stride K with coalesced loads straight into registers;
+// the 16 sums are reduced with shuffles (and across K-slices through shared
+// memory in a fixed order).  No staging, no integer division per element.
+template <typename T, typename Acc>
+__global__ void __launch_bounds__(NT) k_gdot(const GGroup* __restrict__ groups,
+                                             const GItem* __restrict__ items,
+                                             T* const* __restrict__ tab,
+                                             const int* const* __restrict__ rtab, int P, int gbase,
+                                             const double* __restrict__ coefs,
+                                             double* __restrict__ flops) {
+  const int p = blockIdx.y;
+  const GGroup G = groups[gbase + blockIdx.x];
+  T* C = tab[G.cbuf * P + p];
+  if (!C) return;
+  const int m = dimv(G.m_st, G.m_rb, G.m_ri, rtab, P, p);
+  const int n = dimv(G.n_st, G.n_rb, G.n_ri, rtab, P, p);
+  if (m <= 0 || n <= 0) return;
+  C += G.coff;
+  const Acc beta = G.beta >= 0 ? (Acc)coefs[G.beta] : Acc(0);
+  const int TM = (m + 3) >> 2, TN = (n + 3) >> 2, ntile = TM * TN;
+  const int KS = ntile >= 8 ? 1 : 8 / ntile;
+  const int units = ntile * KS;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __shared__ Acc red[8 * 16];
+  if (flops && threadIdx.x == 0) {
+    double fl = 0.0;
+    for (int it = G.ib; it < G.ie; ++it) {
+      const GItem I = items[it];
+      if (I.abuf >= 0 && !tab[I.abuf * P + p]) continue;
+      if (I.bbuf >= 0 && !tab[I.bbuf * P + p]) continue;
+      const int k = dimv(I.k_st, I.k_rb, I.k_ri, rtab, P, p);
+      const int rows = dimv(I.r_st, I.r_rb, I.r_ri, rtab, P, p);
+      if (k > 0 && rows > 0) fl += 2.0 * rows * n * k;
+    }
+    if (fl > 0.0) atomicAdd(flops, fl);
+  }
+  for (int u = warp; u < units; u += 8) {
+    const int tile = u % ntile, ks = u / ntile;
+    const int i0 = (tile % TM) * 4, j0 = (tile / TM) * 4;
+    Acc acc[4][4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[r][c] = Acc(0);
+    for (int it = G.ib; it < G.ie; ++it) {
+      const GItem I = items[it];
+      if (I.guard0 >= 0 && !tab[I.guard0 * P + p]) continue;
+      if (I.guard1 >= 0 && !tab[I.guard1 * P + p]) continue;
+      const T* A = tab[I.abuf * P + p];
+      if (!A) continue;
+      A += I.aoff;
+      const T* B = nullptr;
+      const bool bo = I.bflags & FL_OMEGA;
+      if (!bo) {
+        B = tab[I.bbuf * P + p];
+        if (!B) continue;
+        B += I.boff;
+      }
+      const int k = dimv(I.k_st, I.k_rb, I.k_ri, rtab, P, p);
+      const int rows = dimv(I.r_st, I.r_rb, I.r_ri, rtab, P, p);
+      if (k <= 0 || rows <= 0) continue;
+      const Acc cf = (Acc)coefs[I.coef];
+      const T* ar[4];
+      const T* bc[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) ar[r] = (i0 + r < rows) ? A + (int64_t)(i0 + r) * I.lda : nullptr;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) bc[c] = (!bo && j0 + c < n) ? B + (int64_t)(j0 + c) * I.ldb : nullptr;
+      for (int l = ks * 32 + lane; l < k; l += 32 * KS) {
+        Acc av[4], bv[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) av[r] = ar[r] ? cf * (Acc)ar[r][l] : Acc(0);
+        if (bo) {   // j0 is a multiple of 4: two hash words serve its 4 columns
+          const uint32_t row = (uint32_t)(I.omega_row0 + l);
+          const uint32_t b0 = omega_bits((uint32_t)I.seed, row, (uint32_t)j0 >> 1);
+          const uint32_t b1 = omega_bits((uint32_t)I.seed, row, ((uint32_t)j0 >> 1) + 1);
+#pragma unroll
+          for (int c = 0; c < 4; ++c)
+            bv[c] = (j0 + c < n) ? (Acc)omega_half(c < 2 ? b0 : b1, (uint32_t)(j0 + c)) : Acc(0);
+        } else {
+#pragma unroll
+          for (int c = 0; c < 4; ++c) bv[c] = bc[c] ? (Acc)bc[c][l] : Acc(0);
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) acc[r][c] += av[r] * bv[c];
+      }
+    }
+    // all-lane butterfly reductions; lane e keeps element e
+    Acc mine = Acc(0);
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+      Acc v = acc[e & 3][e >> 2];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == e) mine = v;
+    }
+    if (KS == 1) {
+      if (lane < 16) {
+        const int i = i0 + (lane & 3), j = j0 + (lane >> 2);
+        if (i < m && j < n) {
+          T* c = C + i + (int64_t)j * G.ldc;
+          Acc v = mine;
+          if (G.beta >= 0) v += beta * (Acc)(*c);
+          *c = (T)v;
+        }
+      }
+    } else if (lane < 16) {
+      red[u * 16 + lane] = mine;
+    }
+  }
+  if (KS > 1) {
+    __syncthreads();
+    for (int t = threadIdx.x; t < ntile * 16; t += NT) {
+      const int tile = t >> 4, e = t & 15;
+      Acc v = Acc(0);
+      for (int ks = 0; ks < KS; ++ks) v += red[(tile + ks * ntile) * 16 + e];
+      const int i0 = (tile % TM) * 4, j0 = (tile / TM) * 4;
+      const int i = i0 + (e & 3), j = j0 + (e >> 2);
+      if (i < m && j < n) {
+        T* c = C + i + (int64_t)j * G.ldc;
+        if (G.beta >= 0) v += beta * (Acc)(*c);
+        *c = (T)v;
+      }
+    }
+  }
 }
 
 // ---------------------------------------------------------------- cores
@@ -726,15 +872,19 @@ __global__ void k_plane_lr(const double* __restrict__ coef, int n, const int* __
 
 template <typename T>
 void launch_ggemm(const Plan& pl, int gbeg, int gend, T* const* d_tab, const int* const* d_rtab,
-                  int P, const double* d_coefs, cudaStream_t st, double* d_fl) {
+                  int P, const double* d_coefs, cudaStream_t st, double* d_fl, int tag) {
   int ng = gend - gbeg;
   if (ng <= 0 || P <= 0) return;
   using Acc = T;
   const int maxg = 65535;
   for (int g0 = 0; g0 < ng; g0 += maxg) {
     dim3 grid(std::min(maxg, ng - g0), P);
-    k_ggemm<T, Acc><<<grid, NT, 0, st>>>((const GGroup*)pl.d_groups, (const GItem*)pl.d_items,
-                                         d_tab, d_rtab, P, gbeg + g0, d_coefs, d_fl);
+    const GGroup* gr = (const GGroup*)pl.d_groups;
+    const GItem* it = (const GItem*)pl.d_items;
+    if (tag_is_dot(tag))
+      k_gdot<T, Acc><<<grid, NT, 0, st>>>(gr, it, d_tab, d_rtab, P, gbeg + g0, d_coefs, d_fl);
+    else
+      k_ggemm<T, Acc><<<grid, NT, 0, st>>>(gr, it, d_tab, d_rtab, P, gbeg + g0, d_coefs, d_fl);
     ACR_LAUNCHED(1);
   }
 }
@@ -810,7 +960,7 @@ void launch_plane_to_h(const StructDev& sd, const double* coef, int n, const int
 
 #define ACR_INST(T)                                                                              \
   template void launch_ggemm<T>(const Plan&, int, int, T* const*, const int* const*, int,        \
-                                const double*, cudaStream_t, double*);                           \
+                                const double*, cudaStream_t, double*, int);                      \
   template void launch_pchol<T>(const Plan&, int, int, bool, double, T* const*, int* const*, int, \
                                 cudaStream_t, double*);                                          \
   template void launch_eig<T>(const Plan&, int, int, double, int, int, T* const*, int* const*,   \
