@@ -8,8 +8,13 @@
 //                sum of dense leaves of block row c times x
 //                + sum of U_l[rows of c] tv_l over low-rank leaves covering c)
 // Every stored dense entry and every U, V entry up to the block's rank is
-// read exactly once; the vectors are FP64, the accumulation is FP64.
+// read exactly once; the vectors are FP64.  FP64 factors accumulate in FP64;
+// FP32 factors multiply in FP32 and add short FP32 partial sums (at most 16
+// products) into FP64 accumulators, keeping the slow FP64 pipe off the
+// per-entry path.
 #include <cuda_runtime.h>
+
+#include <type_traits>
 
 #include "acr_internal.h"
 
@@ -36,7 +41,16 @@ __global__ void __launch_bounds__(128) k_lr_proj(MatvecDev mv, T* const* __restr
   for (int j = warp; j < k; j += 4) {
     const T* col = base + (int64_t)j * rows;
     double s = 0.0;
-    for (int i = lane; i < rows; i += 32) s += (double)col[i] * xp[start + i];
+    if (std::is_same<T, float>::value) {
+      for (int i0 = lane; i0 < rows; i0 += 32 * 16) {
+        float sf = 0.f;
+        const int iend = min(rows, i0 + 32 * 16);
+        for (int i = i0; i < iend; i += 32) sf += (float)col[i] * (float)xp[start + i];
+        s += (double)sf;
+      }
+    } else {
+      for (int i = lane; i < rows; i += 32) s += (double)col[i] * xp[start + i];
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) out[j] = s;
@@ -63,11 +77,18 @@ __global__ void __launch_bounds__(256) k_hmv_rows(MatvecDev mv, T* const* __rest
   const bool have = D[p] != nullptr && xp != nullptr;
   if (have && i < lsz) {
     const T* Dp = D[p];
+    constexpr bool f32 = std::is_same<T, float>::value;
     if (!trans) {
       for (int e = mv.d_ptr[c]; e < mv.d_ptr[c + 1]; ++e) {
         const T* blk = Dp + (int64_t)mv.d_leaf[e] * lsz * lsz;
         const double* xs = xp + mv.d_col[e];
-        for (int j = g; j < lsz; j += 4) acc += (double)blk[i + (int64_t)j * lsz] * xs[j];
+        if (f32) {
+          float sf = 0.f;
+          for (int j = g; j < lsz; j += 4) sf += (float)blk[i + (int64_t)j * lsz] * (float)xs[j];
+          acc += (double)sf;
+        } else {
+          for (int j = g; j < lsz; j += 4) acc += (double)blk[i + (int64_t)j * lsz] * xs[j];
+        }
       }
       const T* Up = U[p];
       for (int e = mv.l_ptr[c]; e < mv.l_ptr[c + 1]; ++e) {
@@ -76,7 +97,13 @@ __global__ void __launch_bounds__(256) k_hmv_rows(MatvecDev mv, T* const* __rest
         const int m = mv.lr_m[l];
         const T* ub = Up + mv.lr_row0[l] * mv.kc + mv.l_rowoff[e];
         const double* t = tv + ((int64_t)p * mv.nl + l) * mv.kc;
-        for (int j = g; j < k; j += 4) acc += (double)ub[i + (int64_t)j * m] * t[j];
+        if (f32) {
+          float sf = 0.f;
+          for (int j = g; j < k; j += 4) sf += (float)ub[i + (int64_t)j * m] * (float)t[j];
+          acc += (double)sf;
+        } else {
+          for (int j = g; j < k; j += 4) acc += (double)ub[i + (int64_t)j * m] * t[j];
+        }
       }
     } else {
       for (int e = mv.dt_ptr[c]; e < mv.dt_ptr[c + 1]; ++e) {

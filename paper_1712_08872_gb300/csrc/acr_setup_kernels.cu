@@ -80,7 +80,7 @@ __global__ void __launch_bounds__(NT) k_ggemm(const GGroup* __restrict__ groups,
                                               double* __restrict__ flops) {
   const int p = blockIdx.y;
   const GGroup G = groups[gbase + blockIdx.x];
-  double fl = 0.0;
+  long long fl = 0;   // counted flops (integer: FP64 is a slow pipe here)
   T* C = tab[G.cbuf * P + p];
   if (!C) return;
   const int m = dimv(G.m_st, G.m_rb, G.m_ri, rtab, P, p);
@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(NT) k_ggemm(const GGroup* __restrict__ groups,
     const int r0 = I.row_off;
     if ((I.aflags & FL_IDENT) || (I.bflags & FL_IDENT)) {
       // C(r0+i, j) += cf * B(i, j)  or  cf * A(i, j): straight into the accumulators
-      fl += (double)rows * n;
+      fl += (long long)rows * n;
       const bool ai = I.aflags & FL_IDENT;
       if (blocked) {
 #pragma unroll
@@ -191,7 +191,7 @@ __global__ void __launch_bounds__(NT) k_ggemm(const GGroup* __restrict__ groups,
       }
       continue;
     }
-    fl += 2.0 * rows * n * k;
+    fl += 2LL * rows * n * k;
     const bool at = I.aflags & FL_T, bt = I.bflags & FL_T, bo = I.bflags & FL_OMEGA;
     const bool full = (r0 == 0 && rows >= m);
     for (int k0 = 0; k0 < k;) {
@@ -279,7 +279,7 @@ __global__ void __launch_bounds__(NT) k_ggemm(const GGroup* __restrict__ groups,
       }
     }
   }
-  if (flops && threadIdx.x == 0 && fl > 0.0) atomicAdd(flops, fl);
+  if (flops && threadIdx.x == 0 && fl > 0) atomicAdd(flops, (double)fl);
 }
 
 // Stages whose items read A transposed and B untransposed (or the sketch
