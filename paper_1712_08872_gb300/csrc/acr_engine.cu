@@ -241,6 +241,10 @@ class Engine : public EngineBase {
       cudaFree(kv.second->d_groups); cudaFree(kv.second->d_items); cudaFree(kv.second->d_targets);
     }
     plans.clear();
+    for (auto& kv : merged_plans) {
+      cudaFree(kv.second->d_groups); cudaFree(kv.second->d_items); cudaFree(kv.second->d_targets);
+    }
+    merged_plans.clear();
     if (scratch) cudaFree(scratch);
     if (scratch_ranks) cudaFree(scratch_ranks);
     scratch = nullptr; scratch_ranks = nullptr;
@@ -338,13 +342,53 @@ class Engine : public EngineBase {
     }
   }
 
+  std::map<std::vector<int>, std::unique_ptr<Plan>> merged_plans;
+
+  // Independent operations on the same roles in one set of launches (their
+  // plans merged stage by stage); falls back to separate runs when the
+  // merged scratch would not let a useful number of planes share the arena.
+  void run_merged(const std::vector<OpDesc>& ops, const std::vector<std::vector<HM>>& roles,
+                  int P, cudaStream_t st) {
+    if (P <= 0) return;
+    std::vector<int> key;
+    std::vector<const Plan*> ps;
+    for (const OpDesc& op : ops) {
+      Plan& pl = get_plan(op);
+      ps.push_back(&pl);
+      key.push_back(op.c_node); key.push_back(op.c_role); key.push_back(op.alpha);
+      for (auto& pr : op.prods) {
+        key.push_back(pr.a_node); key.push_back(pr.b_node); key.push_back(pr.a_role);
+        key.push_back(pr.b_role); key.push_back(pr.coef);
+      }
+      key.push_back(-9);
+    }
+    size_t scr = 0;
+    for (const Plan* p : ps) scr += (size_t)p->scratch * sizeof(T);
+    if (scr * (size_t)std::min(P, 8) > scratch_budget) {
+      for (const OpDesc& op : ops) run_split(op, roles, P, st);
+      return;
+    }
+    auto it = merged_plans.find(key);
+    if (it == merged_plans.end()) {
+      auto mp = std::make_unique<Plan>();
+      merge_plans(ps, *mp);
+      it = merged_plans.emplace(key, std::move(mp)).first;
+    }
+    run_plan(*it->second, ops[0].c_role, roles, P, st);
+  }
+
   // roles[r][p]: H-matrix of role r for plane p of the batch
   void run_op(const OpDesc& op, const std::vector<std::vector<HM>>& roles, int P,
               cudaStream_t st) {
     if (P <= 0) return;
     Plan& pl = get_plan(op);
+    run_plan(pl, op.c_role, roles, P, st);
+  }
+
+  void run_plan(Plan& pl, int c_role, const std::vector<std::vector<HM>>& roles, int P,
+                cudaStream_t st) {
     upload_plan(pl);
-    const int nr = op.nroles;
+    const int nr = pl.nroles;
     size_t per_plane = std::max<size_t>((size_t)pl.scratch * sizeof(T), 256);
     int Pc = (int)std::max<size_t>(1, std::min<size_t>(P, scratch_budget / per_plane));
     ensure_scratch(per_plane * Pc, (size_t)std::max(pl.scratch_ranks, 1) * Pc, st);
@@ -376,7 +420,7 @@ class Engine : public EngineBase {
           timed(1, [&] { launch_pchol<T>(pl, sg.beg, sg.end, sg.kind == ST_PCHOL, tau_orth(), d_tab,
                                          d_rtab, pc, st, fl(1)); });
         else if (sg.kind == ST_EIG)
-          timed(2, [&] { launch_eig<T>(pl, sg.beg, sg.end, eps, kc, op.c_role, d_tab, d_rtab, pc,
+          timed(2, [&] { launch_eig<T>(pl, sg.beg, sg.end, eps, kc, c_role, d_tab, d_rtab, pc,
                                        d_err, st, fl(2)); });
       }
     }
@@ -409,12 +453,14 @@ class Engine : public EngineBase {
       return op;
     };
     hinv(t1, roles, d_xdense, P, st);
-    run_split(mk(n12, 1, -1, n11, 0, n12, 0, 0), roles, P, st);   // T12 = X11 A12
-    run_split(mk(n21, 1, -1, n21, 0, n11, 0, 0), roles, P, st);   // T21 = A21 X11
+    run_merged({mk(n12, 1, -1, n11, 0, n12, 0, 0),      // T12 = X11 A12
+                mk(n21, 1, -1, n21, 0, n11, 0, 0)},     // T21 = A21 X11
+               roles, P, st);
     run_split(mk(n22, 0, 0, n21, 0, n12, 1, 1), roles, P, st);    // S = A22 - A21 T12
     hinv(t2, roles, d_xdense, P, st);
-    run_split(mk(n12, 0, -1, n12, 1, n22, 0, 1), roles, P, st);   // X12 = -T12 X22
-    run_split(mk(n21, 0, -1, n22, 0, n21, 1, 1), roles, P, st);   // X21 = -X22 T21
+    run_merged({mk(n12, 0, -1, n12, 1, n22, 0, 1),      // X12 = -T12 X22
+                mk(n21, 0, -1, n22, 0, n21, 1, 1)},     // X21 = -X22 T21
+               roles, P, st);
     run_split(mk(n11, 0, 0, n12, 0, n21, 1, 1), roles, P, st);    // X11 = X11 - X12 T21
   }
 

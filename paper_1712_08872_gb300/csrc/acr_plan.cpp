@@ -565,6 +565,84 @@ void build_plan(const Structure& S, const OpDesc& op, const PlanParams& pp, Plan
   b.phase2();
 }
 
+namespace {
+// canonical position of a stage in every plan
+int stage_slot(const Stage& sg) {
+  if (sg.kind == ST_GEMM) {
+    static const int slot_of_tag[NTAGS] = {0, 1, 2, 3, 4, 5, 7, 8, 10, 11, 12, 13, 15};
+    return slot_of_tag[sg.tag];
+  }
+  if (sg.kind == ST_PCHOL) return 6;
+  if (sg.kind == ST_PCHOL + 16) return 9;
+  return 14;   // ST_EIG
+}
+}  // namespace
+
+void merge_plans(const std::vector<const Plan*>& ps, Plan& out) {
+  out = Plan();
+  const int nr = ps[0]->nroles;
+  out.nroles = nr;
+  const int sb = 3 * nr, rb = nr;
+  std::vector<int64_t> soff(ps.size());
+  std::vector<int> roff(ps.size()), toff(ps.size());
+  for (size_t i = 0; i < ps.size(); ++i) {
+    soff[i] = out.scratch;
+    roff[i] = out.scratch_ranks;
+    toff[i] = (int)out.targets.size();
+    out.scratch += ps[i]->scratch;
+    out.scratch_ranks += ps[i]->scratch_ranks;
+    for (TInfo ti : ps[i]->targets) {
+      ti.g_off += soff[i]; ti.t_off += soff[i]; ti.h_off += soff[i]; ti.w_off += soff[i];
+      ti.r_ri += roff[i];
+      out.targets.push_back(ti);
+    }
+    out.n_lr_targets += ps[i]->n_lr_targets;
+    out.n_dense_targets += ps[i]->n_dense_targets;
+    out.n_terms += ps[i]->n_terms;
+    out.flops_static += ps[i]->flops_static;
+  }
+  for (int slot = 0; slot < 16; ++slot) {
+    int kind = -1, tag = -1, g0 = (int)out.groups.size(), tb = -1, te = -1;
+    for (size_t i = 0; i < ps.size(); ++i) {
+      for (const Stage& sg : ps[i]->stages) {
+        if (stage_slot(sg) != slot) continue;
+        kind = sg.kind;
+        tag = sg.tag;
+        if (sg.kind == ST_GEMM) {
+          for (int g = sg.beg; g < sg.end; ++g) {
+            GGroup G = ps[i]->groups[g];
+            const int ib = (int)out.items.size();
+            for (int it = G.ib; it < G.ie; ++it) {
+              GItem I = ps[i]->items[it];
+              if (I.abuf == sb) I.aoff += soff[i];
+              if (I.bbuf == sb) I.boff += soff[i];
+              if (I.k_rb == rb) I.k_ri += roff[i];
+              if (I.r_rb == rb) I.r_ri += roff[i];
+              out.items.push_back(I);
+            }
+            G.ib = ib;
+            G.ie = (int)out.items.size();
+            if (G.cbuf == sb) G.coff += soff[i];
+            if (G.m_rb == rb) G.m_ri += roff[i];
+            if (G.n_rb == rb) G.n_ri += roff[i];
+            out.groups.push_back(G);
+          }
+        } else {
+          const int b = sg.beg + toff[i], e = sg.end + toff[i];
+          tb = tb < 0 ? b : std::min(tb, b);
+          te = std::max(te, e);
+        }
+      }
+    }
+    if (kind < 0) continue;
+    if (kind == ST_GEMM) {
+      if ((int)out.groups.size() > g0) out.stages.push_back(Stage{kind, g0, (int)out.groups.size(), tag});
+    } else if (te > tb) {
+      out.stages.push_back(Stage{kind, tb, te, -1});
+    }
+  }
+}
+
 void MatvecPlan::build(const Structure& S) {
   const int nc = S.nleafcl, lsz = S.lsz;
   std::vector<std::vector<int>> dr(nc), dc(nc), lr(nc), lc(nc);

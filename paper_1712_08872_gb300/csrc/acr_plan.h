@@ -135,6 +135,11 @@ struct PlanParams {
 // Build the plan of one formatted operation.
 void build_plan(const Structure& S, const OpDesc& op, const PlanParams& pp, Plan& plan);
 
+// Merge plans of independent operations (same roles, same target role):
+// stage k of every plan runs in one launch; scratch, scratch rank slots and
+// targets are laid out one plan after another.
+void merge_plans(const std::vector<const Plan*>& ps, Plan& out);
+
 // H-matrix-vector product lists (apply).  Per leaf row-chunk c (leaf
 // clusters in cluster order): dense leaves of block row c and low-rank
 // leaves whose row cluster contains c.  The transposed lists use block
