@@ -194,9 +194,33 @@ __global__ void __launch_bounds__(NT) k_ggemm(const GGroup* __restrict__ groups,
     fl += 2LL * rows * n * k;
     const bool at = I.aflags & FL_T, bt = I.bflags & FL_T, bo = I.bflags & FL_OMEGA;
     const bool full = (r0 == 0 && rows >= m);
+    // a whole 64 x 64 dense leaf (contiguous, 16-byte aligned): staged with
+    // vector loads and shift indexing once it fits the chunk entirely
+    const bool blockA = (rows == 64 && r0 == 0 && k == 64 && I.lda == 64 && KC >= 64 &&
+                         (reinterpret_cast<uintptr_t>(A) & 15) == 0);
+    const bool blockB = (!bo && !bt && n == 64 && k == 64 && I.ldb == 64 && KC >= 64 &&
+                         (reinterpret_cast<uintptr_t>(B) & 15) == 0);
+    if ((blockA || blockB) && kfill + 64 > KC) {
+      compute(kfill);
+      kfill = 0;
+    }
     for (int k0 = 0; k0 < k;) {
       const int t = min(k - k0, KC - kfill);
       // A panel -> As[(kfill + kk) * lda_s + r0 + i], zero elsewhere in those columns
+      if (blockA && t == 64) {
+        constexpr int V = 16 / sizeof(T);
+        for (int e0 = threadIdx.x * V; e0 < 4096; e0 += NT * V) {
+          T v[V];
+          *reinterpret_cast<uint4*>(v) = *reinterpret_cast<const uint4*>(A + e0);
+#pragma unroll
+          for (int q = 0; q < V; ++q) {
+            const int e = e0 + q;
+            // column-major block: e = i + 64 l  (A)  or  e = l + 64 i  (A^T)
+            const int i = at ? (e >> 6) : (e & 63), kk = at ? (e & 63) : (e >> 6);
+            As[(kfill + kk) * lda_s + i] = cf * (Acc)v[q];
+          }
+        }
+      } else {
       if (!full)
         for (int e = threadIdx.x; e < t * m; e += NT) {
           const int kk = e / m, i = e - kk * m;
@@ -213,8 +237,20 @@ __global__ void __launch_bounds__(NT) k_ggemm(const GGroup* __restrict__ groups,
           As[(kfill + kk) * lda_s + r0 + i] = cf * (Acc)A[i + (int64_t)(k0 + kk) * I.lda];
         }
       }
+      }
       // B panel -> Bs[(kfill + kk) * ldb_s + j]
-      if (bo) {
+      if (blockB && t == 64) {
+        constexpr int V = 16 / sizeof(T);
+        for (int e0 = threadIdx.x * V; e0 < 4096; e0 += NT * V) {
+          T v[V];
+          *reinterpret_cast<uint4*>(v) = *reinterpret_cast<const uint4*>(B + e0);
+#pragma unroll
+          for (int q = 0; q < V; ++q) {
+            const int e = e0 + q;   // e = l + 64 j
+            Bs[(kfill + (e & 63)) * ldb_s + (e >> 6)] = (Acc)v[q];
+          }
+        }
+      } else if (bo) {
         for (int e = threadIdx.x; e < t * n; e += NT) {
           const int kk = e / n, j = e - kk * n;
           Bs[(kfill + kk) * ldb_s + j] =
@@ -412,6 +448,103 @@ __global__ void __launch_bounds__(NT) k_gdot(const GGroup* __restrict__ groups,
       }
     }
   }
+}
+
+// Warp-per-group form of the dot kernel for stages made of very many tiny
+// groups (U^T V, Z^T Omega, X^T Q): eight groups per CTA, each warp walks
+// its group's output in 4 x 8 tiles with lanes striding the contraction;
+// no shared memory, no barriers.
+template <typename T, typename Acc>
+__global__ void __launch_bounds__(NT) k_gdot_warp(const GGroup* __restrict__ groups,
+                                                  const GItem* __restrict__ items,
+                                                  T* const* __restrict__ tab,
+                                                  const int* const* __restrict__ rtab, int P,
+                                                  int gbase, int gend,
+                                                  const double* __restrict__ coefs,
+                                                  double* __restrict__ flops) {
+  const int p = blockIdx.y;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int gi = gbase + blockIdx.x * (NT / 32) + warp;
+  if (gi >= gend) return;
+  const GGroup G = groups[gi];
+  T* C = tab[G.cbuf * P + p];
+  if (!C) return;
+  const int m = dimv(G.m_st, G.m_rb, G.m_ri, rtab, P, p);
+  const int n = dimv(G.n_st, G.n_rb, G.n_ri, rtab, P, p);
+  if (m <= 0 || n <= 0) return;
+  C += G.coff;
+  const Acc beta = G.beta >= 0 ? (Acc)coefs[G.beta] : Acc(0);
+  long long fl = 0;
+  for (int i0 = 0; i0 < m; i0 += 4) {
+    for (int j0 = 0; j0 < n; j0 += 8) {
+      Acc acc[4][8];
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 8; ++c) acc[r][c] = Acc(0);
+      for (int it = G.ib; it < G.ie; ++it) {
+        const GItem I = items[it];
+        if (I.guard0 >= 0 && !tab[I.guard0 * P + p]) continue;
+        if (I.guard1 >= 0 && !tab[I.guard1 * P + p]) continue;
+        const T* A = tab[I.abuf * P + p];
+        if (!A) continue;
+        A += I.aoff;
+        const bool bo = I.bflags & FL_OMEGA;
+        const T* B = nullptr;
+        if (!bo) {
+          B = tab[I.bbuf * P + p];
+          if (!B) continue;
+          B += I.boff;
+        }
+        const int k = dimv(I.k_st, I.k_rb, I.k_ri, rtab, P, p);
+        const int rows = dimv(I.r_st, I.r_rb, I.r_ri, rtab, P, p);
+        if (k <= 0 || rows <= 0) continue;
+        if (i0 == 0 && j0 == 0) fl += 2LL * rows * n * k;
+        const Acc cf = (Acc)coefs[I.coef];
+        const T* ar[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) ar[r] = (i0 + r < rows) ? A + (int64_t)(i0 + r) * I.lda : nullptr;
+        for (int l = lane; l < k; l += 32) {
+          Acc av[4], bv[8];
+#pragma unroll
+          for (int r = 0; r < 4; ++r) av[r] = ar[r] ? cf * (Acc)ar[r][l] : Acc(0);
+          if (bo) {
+            const uint32_t row = (uint32_t)(I.omega_row0 + l);
+#pragma unroll
+            for (int w = 0; w < 4; ++w) {
+              const uint32_t bits = omega_bits((uint32_t)I.seed, row, ((uint32_t)j0 >> 1) + w);
+              bv[2 * w] = (j0 + 2 * w < n) ? (Acc)omega_half(bits, 0u) : Acc(0);
+              bv[2 * w + 1] = (j0 + 2 * w + 1 < n) ? (Acc)omega_half(bits, 1u) : Acc(0);
+            }
+          } else {
+#pragma unroll
+            for (int c = 0; c < 8; ++c)
+              bv[c] = (j0 + c < n) ? (Acc)B[l + (int64_t)(j0 + c) * I.ldb] : Acc(0);
+          }
+#pragma unroll
+          for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int c = 0; c < 8; ++c) acc[r][c] += av[r] * bv[c];
+        }
+      }
+      Acc mine = Acc(0);
+#pragma unroll
+      for (int e = 0; e < 32; ++e) {
+        Acc v = acc[e & 3][e >> 2];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == e) mine = v;
+      }
+      const int i = i0 + (lane & 3), j = j0 + (lane >> 2);
+      if (i < m && j < n) {
+        T* c = C + i + (int64_t)j * G.ldc;
+        Acc v = mine;
+        if (G.beta >= 0) v += beta * (Acc)(*c);
+        *c = (T)v;
+      }
+    }
+  }
+  if (flops && lane == 0 && fl > 0) atomicAdd(flops, (double)fl);
 }
 
 // ---------------------------------------------------------------- cores
@@ -881,7 +1014,12 @@ void launch_ggemm(const Plan& pl, int gbeg, int gend, T* const* d_tab, const int
     dim3 grid(std::min(maxg, ng - g0), P);
     const GGroup* gr = (const GGroup*)pl.d_groups;
     const GItem* it = (const GItem*)pl.d_items;
-    if (tag_is_dot(tag))
+    if (tag == TAG_M) {
+      const int cnt = std::min(maxg, ng - g0);
+      dim3 gw((cnt + NT / 32 - 1) / (NT / 32), P);
+      k_gdot_warp<T, Acc><<<gw, NT, 0, st>>>(gr, it, d_tab, d_rtab, P, gbeg + g0, gbeg + g0 + cnt,
+                                             d_coefs, d_fl);
+    } else if (tag_is_dot(tag))
       k_gdot<T, Acc><<<grid, NT, 0, st>>>(gr, it, d_tab, d_rtab, P, gbeg + g0, d_coefs, d_fl);
     else
       k_ggemm<T, Acc><<<grid, NT, 0, st>>>(gr, it, d_tab, d_rtab, P, gbeg + g0, d_coefs, d_fl);
