@@ -550,26 +550,6 @@ __global__ void __launch_bounds__(NT) k_gdot_warp(const GGroup* __restrict__ gro
 // ---------------------------------------------------------------- cores
 constexpr int CMAX = 64;   // largest sketch / core dimension
 
-__device__ __forceinline__ int block_argmax(double v, int idx, double* sv, int* si) {
-  // index of the largest v over the block (idx < 0: no candidate; ties -> smaller index)
-  const int t = threadIdx.x;
-  sv[t] = v; si[t] = idx;
-  __syncthreads();
-  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-    if (t < s) {
-      const double o = sv[t + s];
-      const int oi = si[t + s];
-      if (oi >= 0 && (si[t] < 0 || o > sv[t] || (o == sv[t] && oi < si[t]))) {
-        sv[t] = o; si[t] = oi;
-      }
-    }
-    __syncthreads();
-  }
-  const int r = si[0];
-  __syncthreads();
-  return r;
-}
-
 // Pivoted Cholesky of G (pd x pd): G = P L L^T P^T, stop when the largest
 // remaining diagonal <= tau^2 * max diag(G) (truncating pass).  Writes
 // T (p x r, ld p) with Q = Y T orthonormal, and r.
@@ -589,9 +569,9 @@ __global__ void __launch_bounds__(NT) k_pchol(const TInfo* __restrict__ tis, int
   double (*L)[CMAX + 1] = reinterpret_cast<double (*)[CMAX + 1]>(dsm);
   double (*F)[CMAX + 1] = reinterpret_cast<double (*)[CMAX + 1]>(dsm + CMAX * (CMAX + 1));
   __shared__ double d[CMAX];
+  __shared__ double colbuf[CMAX];
   __shared__ int piv[CMAX];
   __shared__ double sv[NT];
-  __shared__ int si[NT];
   const T* G = scr + ti.g_off;
   T* Tm = scr + ti.t_off;
   for (int e = threadIdx.x; e < pd * pd; e += NT) {
@@ -617,39 +597,60 @@ __global__ void __launch_bounds__(NT) k_pchol(const TInfo* __restrict__ tis, int
   // F: lower factor in pivoted order
   for (int e = threadIdx.x; e < CMAX * (CMAX + 1); e += NT) (&F[0][0])[e] = 0.0;
   __syncthreads();
+  __shared__ int s_q, s_stop;
+  __shared__ double s_ljj;
   for (int j = 0; j < pd; ++j) {
-    double best = -1.0;
-    int bi = -1;
-    for (int i = j + threadIdx.x; i < pd; i += NT) {
-      const double v = d[piv[i]];
-      if (v > best) { best = v; bi = i; }
+    if (threadIdx.x < 32) {
+      // largest remaining diagonal among pivoted positions j..pd-1
+      double best = -1.0;
+      int bi = -1;
+      for (int i = j + (threadIdx.x & 31); i < pd; i += 32) {
+        const double v = d[piv[i]];
+        if (v > best) { best = v; bi = i; }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (oi >= 0 && (bi < 0 || ov > best || (ov == best && oi < bi))) { best = ov; bi = oi; }
+      }
+      if (threadIdx.x == 0) {
+        const bool stop = bi < 0 || !(best > tol) || !(best > 0.0);
+        s_stop = stop ? 1 : 0;
+        if (!stop) {
+          const int t = piv[j]; piv[j] = piv[bi]; piv[bi] = t;
+          s_q = bi;
+          s_ljj = sqrt(best);
+        }
+      }
     }
-    const int q = block_argmax(best, bi, sv, si);
-    const double dq = (q >= 0) ? d[piv[q]] : 0.0;
-    if (q < 0 || dq <= tol || dq <= 0.0) {
+    __syncthreads();
+    if (s_stop) {
       // truncating pass: the rest of range(Y) is below tau; re-orthogonalising
       // pass: keep the dimension, the remaining directions get zero columns
       if (!truncate) r = pd;
       break;
     }
-    if (threadIdx.x == 0) {
-      const int tmp = piv[j]; piv[j] = piv[q]; piv[q] = tmp;
+    const int q = s_q;
+    const double ljj = s_ljj;
+    // the rows of the partial factor follow the pivot interchange; then column j
+    for (int i = j + threadIdx.x; i < pd; i += NT) {
+      // row i of the pivoted factor (before this step's swap, row q held what is now row j)
+      const int src = (i == j) ? q : (i == q ? j : i);
+      double sum = L[piv[i]][piv[j]];
+      for (int l = 0; l < j; ++l) sum -= F[src][l] * F[q][l];
+      colbuf[i] = (i == j) ? ljj : sum / ljj;
     }
-    // the rows of the partial factor follow the pivot interchange
+    __syncthreads();
+    // the row swap touches columns < j only; column j is written alongside
     if (q != j)
       for (int l = threadIdx.x; l < j; l += NT) {
         const double t = F[j][l]; F[j][l] = F[q][l]; F[q][l] = t;
       }
-    __syncthreads();
-    const double ljj = sqrt(d[piv[j]]);
     for (int i = j + threadIdx.x; i < pd; i += NT) {
-      double sum = L[piv[i]][piv[j]];
-      for (int l = 0; l < j; ++l) sum -= F[i][l] * F[j][l];
-      F[i][j] = (i == j) ? ljj : sum / ljj;
+      F[i][j] = colbuf[i];
+      if (i > j) d[piv[i]] -= colbuf[i] * colbuf[i];
     }
-    __syncthreads();
-    for (int i = j + 1 + threadIdx.x; i < pd; i += NT) d[piv[i]] -= F[i][j] * F[i][j];
-    __syncthreads();
     if (threadIdx.x == 0) d[piv[j]] = 0.0;
     __syncthreads();
     r = j + 1;
@@ -720,29 +721,29 @@ __global__ void __launch_bounds__(NT) k_eig(const TInfo* __restrict__ tis, int t
   const int npair = nn / 2;
   int sweeps_done = 0;
   for (int sweep = 0; sweep < 40; ++sweep) {
-    // off-diagonal and total norms
+    // off-diagonal and total norms: warp shuffles, then one pass over the warps
     double off = 0, tot = 0;
-    for (int e = threadIdx.x; e < r * r; e += NT) {
-      int i = e % r, j = e / r;
-      double v = A[i][j] * A[i][j];
-      tot += v;
-      if (i != j) off += v;
+    {
+      const int i = threadIdx.x & 63;
+      if (i < r)
+        for (int j = threadIdx.x >> 6; j < r; j += 4) {
+          const double v = A[i][j] * A[i][j];
+          tot += v;
+          if (i != j) off += v;
+        }
     }
-    red[threadIdx.x] = off;
-    __syncthreads();
-    for (int s = NT / 2; s > 0; s >>= 1) {
-      if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
-      __syncthreads();
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      off += __shfl_xor_sync(0xffffffffu, off, o);
+      tot += __shfl_xor_sync(0xffffffffu, tot, o);
     }
-    double offs = red[0];
-    __syncthreads();
-    red[threadIdx.x] = tot;
-    __syncthreads();
-    for (int s = NT / 2; s > 0; s >>= 1) {
-      if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
-      __syncthreads();
+    if ((threadIdx.x & 31) == 0) {
+      red[threadIdx.x >> 5] = off;
+      red[(NT >> 5) + (threadIdx.x >> 5)] = tot;
     }
-    double tots = red[0];
+    __syncthreads();
+    double offs = 0, tots = 0;
+    for (int w = 0; w < NT / 32; ++w) { offs += red[w]; tots += red[NT / 32 + w]; }
     __syncthreads();
     if (offs <= 1e-30 * tots || r == 1) break;
     ++sweeps_done;
@@ -760,36 +761,47 @@ __global__ void __launch_bounds__(NT) k_eig(const TInfo* __restrict__ tis, int t
           if (apq != 0.0) {
             double tau_ = (A[hi][hi] - A[lo][lo]) / (2.0 * apq);
             double t = (tau_ >= 0 ? 1.0 : -1.0) / (fabs(tau_) + sqrt(1.0 + tau_ * tau_));
-            c = 1.0 / sqrt(1.0 + t * t);
+            c = rsqrt(1.0 + t * t);
             s = t * c;
           }
         }
         cs[k] = c; sn[k] = s;
       }
       __syncthreads();
-      // column rotations of A and V
-      for (int e = threadIdx.x; e < npair * r; e += NT) {
-        int k = e / r, i = e % r;
-        int a = pp[k], b = qq[k];
-        if (b >= r) continue;
-        double c = cs[k], s = sn[k];
-        double x = A[i][a], y = A[i][b];
-        A[i][a] = c * x - s * y;
-        A[i][b] = s * x + c * y;
-        double vx = V[i][a], vy = V[i][b];
-        V[i][a] = c * vx - s * vy;
-        V[i][b] = s * vx + c * vy;
-      }
-      __syncthreads();
-      // row rotations of A
-      for (int e = threadIdx.x; e < npair * r; e += NT) {
-        int k = e / r, j = e % r;
-        int a = pp[k], b = qq[k];
-        if (b >= r) continue;
-        double c = cs[k], s = sn[k];
-        double x = A[a][j], y = A[b][j];
-        A[a][j] = c * x - s * y;
-        A[b][j] = s * x + c * y;
+      // A <- J^T A J in one pass: the pairs are disjoint, so each 2 x 2 block
+      // (rows of pair k1, columns of pair k2) is rotated on its own -- columns
+      // first, then rows; V <- V J alongside.  A pair holding the odd
+      // dimension's dummy index is the identity and has no second row/column.
+      // The blocks and the npair * r (row, pair) items of V share one flat
+      // index space, so that every lane has work.
+      const int nblk = npair * npair;
+      for (int e = threadIdx.x; e < nblk + npair * r; e += NT) {
+        if (e < nblk) {
+          const int k1 = e / npair, k2 = e - k1 * npair;
+          const int a1 = pp[k1], b1 = qq[k1], a2 = pp[k2], b2 = qq[k2];
+          const bool h1 = b1 < r, h2 = b2 < r;
+          const double c1 = cs[k1], s1 = sn[k1], c2 = cs[k2], s2 = sn[k2];
+          const double x00 = A[a1][a2];
+          const double x01 = h2 ? A[a1][b2] : 0.0;
+          const double x10 = h1 ? A[b1][a2] : 0.0;
+          const double x11 = (h1 && h2) ? A[b1][b2] : 0.0;
+          const double y00 = c2 * x00 - s2 * x01, y01 = s2 * x00 + c2 * x01;
+          const double y10 = c2 * x10 - s2 * x11, y11 = s2 * x10 + c2 * x11;
+          A[a1][a2] = c1 * y00 - s1 * y10;
+          if (h2) A[a1][b2] = c1 * y01 - s1 * y11;
+          if (h1) A[b1][a2] = s1 * y00 + c1 * y10;
+          if (h1 && h2) A[b1][b2] = s1 * y01 + c1 * y11;
+        } else {
+          const int f = e - nblk;
+          const int k = f / r, iv = f - k * r;
+          const int a = pp[k], b = qq[k];
+          if (b < r) {
+            const double c = cs[k], s = sn[k];
+            const double vx = V[iv][a], vy = V[iv][b];
+            V[iv][a] = c * vx - s * vy;
+            V[iv][b] = s * vx + c * vy;
+          }
+        }
       }
       __syncthreads();
     }
@@ -832,67 +844,94 @@ __global__ void __launch_bounds__(NT) k_eig(const TInfo* __restrict__ tis, int t
 }
 
 // In-place Gauss-Jordan inverse with partial pivoting, FP64, n <= 64.
+// Per elimination step warp 0 finds the pivot with shuffles, takes the one
+// reciprocal of the step and publishes the scaled pivot row, the displaced
+// row and the multipliers; then every entry is updated with the row
+// interchange folded in -- two barriers per step.  Thread t owns row t % 64
+// and columns t / 64 + 4 m.  The interchanges become one column permutation
+// of the result, applied when it is stored.
 template <typename T>
 __global__ void __launch_bounds__(NT) k_leaf_inv(T* const* __restrict__ dense, int64_t off, int n,
                                                  int* err, double* __restrict__ flops) {
+  static_assert(NT == 256 && CMAX == 64, "thread mapping assumes 256 threads and 64 x 64 leaves");
   const int p = blockIdx.x;
   T* Ap = dense[p];
   if (!Ap) return;
   Ap += off;
   __shared__ double A[CMAX][CMAX + 1];
+  __shared__ double rowk[CMAX], colk[CMAX], krow[CMAX];
   __shared__ int piv[CMAX];
-  __shared__ double sv[NT];
-  __shared__ int si[NT];
-  __shared__ double rowk[CMAX];
-  __shared__ double colk[CMAX];
-  for (int e = threadIdx.x; e < n * n; e += NT) A[e % n][e / n] = (double)Ap[e];
+  __shared__ int cmap[CMAX];
+  __shared__ int s_q, s_bad;
+  __shared__ double s_pinv;
+  const int ti = threadIdx.x & 63, tj = threadIdx.x >> 6;
+  for (int j = tj; j < n; j += 4)
+    if (ti < n) A[ti][j] = (double)Ap[ti + (int64_t)j * n];
+  if (threadIdx.x == 0) s_bad = 0;
   __syncthreads();
-  bool bad = false;
   for (int k = 0; k < n; ++k) {
-    double best = -1.0;
-    int bi = -1;
-    for (int i = k + threadIdx.x; i < n; i += NT) {
-      double v = fabs(A[i][k]);
-      if (v > best) { best = v; bi = i; }
-    }
-    int q = block_argmax(best, bi, sv, si);
-    if (threadIdx.x == 0) piv[k] = q;
-    if (q < 0 || A[q][k] == 0.0) { bad = true; break; }
-    // swap rows k and q
-    for (int j = threadIdx.x; j < n; j += NT) {
-      double t = A[k][j]; A[k][j] = A[q][j]; A[q][j] = t;
+    if (threadIdx.x < 32) {
+      const int lane = threadIdx.x;
+      double best = -1.0;
+      int q = -1;
+      for (int i = k + lane; i < n; i += 32) {
+        const double v = fabs(A[i][k]);
+        if (v > best) { best = v; q = i; }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, q, o);
+        if (oi >= 0 && (q < 0 || ov > best || (ov == best && oi < q))) { best = ov; q = oi; }
+      }
+      // every lane holds the same winner
+      if (q < 0 || !(best > 0.0)) {
+        if (lane == 0) s_bad = 1;
+      } else {
+        const double pinv = 1.0 / A[q][k];
+        for (int j = lane; j < n; j += 32) {
+          rowk[j] = (j == k) ? pinv : A[q][j] * pinv;   // new row k
+          krow[j] = A[k][j];                             // old row k (moves to row q)
+          colk[j] = (j == k) ? 0.0 : (j == q ? A[k][k] : A[j][k]);   // multipliers after the swap
+        }
+        if (lane == 0) { s_q = q; s_pinv = pinv; piv[k] = q; }
+      }
     }
     __syncthreads();
-    const double pinv = 1.0 / A[k][k];
-    for (int j = threadIdx.x; j < n; j += NT) {
-      rowk[j] = (j == k) ? pinv : A[k][j] * pinv;
-      colk[j] = A[j][k];
+    if (s_bad) break;
+    const int q = s_q;
+    const double pinv = s_pinv;
+    if (ti < n) {
+      const double f = colk[ti];
+      for (int j = tj; j < n; j += 4) {
+        if (ti == k) {
+          A[ti][j] = rowk[j];
+        } else {
+          const double old = (ti == q) ? krow[j] : A[ti][j];
+          A[ti][j] = (j == k) ? -f * pinv : old - f * rowk[j];
+        }
+      }
     }
-    __syncthreads();
-    for (int e = threadIdx.x; e < n * n; e += NT) {
-      int i = e % n, j = e / n;
-      if (i == k) continue;
-      const double f = colk[i];
-      A[i][j] = (j == k) ? -f * pinv : A[i][j] - f * rowk[j];
-    }
-    __syncthreads();
-    for (int j = threadIdx.x; j < n; j += NT) A[k][j] = rowk[j];
     __syncthreads();
   }
-  if (bad) {
+  if (s_bad) {
     if (threadIdx.x == 0) atomicOr(err, ERR_PIVOT);
     return;
   }
-  // undo the row interchanges as column swaps, last first
-  for (int k = n - 1; k >= 0; --k) {
-    int q = piv[k];
-    if (q != k)
-      for (int i = threadIdx.x; i < n; i += NT) {
-        double t = A[i][k]; A[i][k] = A[i][q]; A[i][q] = t;
-      }
-    __syncthreads();
+  if (threadIdx.x == 0) {
+    // the interchanges, undone last first as column swaps, compose into one
+    // permutation: stored column c comes from working column pi(c)
+    int pi_[CMAX];
+    for (int c = 0; c < n; ++c) pi_[c] = c;
+    for (int k = n - 1; k >= 0; --k) {
+      const int q = piv[k];
+      const int t = pi_[k]; pi_[k] = pi_[q]; pi_[q] = t;
+    }
+    for (int c = 0; c < n; ++c) cmap[pi_[c]] = c;
   }
-  for (int e = threadIdx.x; e < n * n; e += NT) Ap[e] = (T)A[e % n][e / n];
+  __syncthreads();
+  for (int j = tj; j < n; j += 4)
+    if (ti < n) Ap[ti + (int64_t)cmap[j] * n] = (T)A[ti][j];
   if (flops && threadIdx.x == 0) atomicAdd(flops, 2.0 * n * n * n);
 }
 
