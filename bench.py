@@ -136,6 +136,33 @@ def oracle_scale():
     return (128.0 / 32.0) ** 7
 
 
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "grouped_gemm_dram_codi_n64.md")
+GEMM_SOURCE = os.path.join(ROOT, "paper_1712_08872_gb300", "csrc", "acr_setup_kernels.cu")
+
+
+def gemm_traffic_per_flop():
+    """DRAM bytes per algorithmic flop of the grouped-GEMM kernels, from the
+    committed ncu summary, or None when the kernel source has changed since
+    those counters were taken."""
+    import hashlib
+    try:
+        txt = open(TRAFFIC_FILE).read()
+        with open(GEMM_SOURCE, "rb") as fh:
+            sha = hashlib.sha256(fh.read()).hexdigest()
+    except OSError:
+        return None, "no capture"
+    bpf = rec = None
+    for ln in txt.splitlines():
+        ln = ln.strip()
+        if ln.startswith("bytes_per_flop:"):
+            bpf = float(ln.split(":")[1])
+        elif ln.startswith("source_sha256:"):
+            rec = ln.split(":")[1].strip()
+    if bpf is None or rec != sha:
+        return None, "kernel changed since the capture"
+    return bpf, "profiles/grouped_gemm_dram_codi_n64.md, scaled by flops per launch"
+
+
 def cpu_cores():
     for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         if os.environ.get(v):
@@ -175,6 +202,43 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------- GPU arm
+def profile_setup(args):
+    """One setup of the benchmark recipe at --n with CUDA events around every
+    setup launch; prints the time and device-counted flops per kernel class,
+    per GEMM stage and per CR level.  Used for the ncu captures under
+    profiles/ (a small n keeps a capture short)."""
+    import torch
+    import paper_1712_08872_gb300 as acr
+    from inputs import workload
+    dev = torch.device("cuda", 0)
+    acr.load_library()
+    n = args.n
+    spec, beta, _ = workload("codi_n128", n=n)
+    coef = torch.empty(7 * n ** 3, dtype=torch.float64, device=dev)
+    acr.acr_stencil_codi(n, torch.tensor(beta.ravel(), dtype=torch.float64, device=dev), coef)
+    prec = acr.ACR_FP64 if args.fp64 else acr.ACR_FP32
+    stream = torch.cuda.current_stream()
+    h = acr.acr_setup(n, coef, spec["eps"], 2.0, spec["leaf"], prec, args.rank_cap, stream,
+                      acr.ACR_FLAG_PROFILE)
+    p = acr.acr_get_profile(h)
+    inf = acr.acr_get_setup_info(h)
+    acr.acr_destroy(h)
+    print("n=%d %s setup %.1f ms, levels %d, max rank %d, factors %.3f GB"
+          % (n, "FP64" if args.fp64 else "FP32", inf.setup_ms, inf.levels, inf.max_rank,
+             inf.factor_bytes / 1e9))
+    for k in ("gemm", "orth", "eig", "leaf_inv", "other"):
+        st = getattr(p, k)
+        print("  %-9s launches %7d  %9.1f ms  %8.3f TFLOP/s"
+              % (k, st.launches, st.ms, st.flops / max(st.ms, 1e-9) / 1e9))
+    for i, nm in enumerate(p.STAGES):
+        print("    %-14s %9.1f ms  %10.3f GFLOP  %8.3f TFLOP/s"
+              % (nm, p.stage_ms[i], p.stage_flops[i] / 1e9,
+                 p.stage_flops[i] / max(p.stage_ms[i], 1e-9) / 1e9))
+    print("  inversion ms per level", [round(x, 1) for x in p.inv_ms[:inf.levels + 1]])
+    print("  update ms per level   ", [round(x, 1) for x in p.upd_ms[:inf.levels]])
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -186,9 +250,15 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--rank-cap", type=int, default=24)
+    ap.add_argument("--profile-setup", action="store_true",
+                    help="run one profiled setup (ACR_FLAG_PROFILE) at --n and print its "
+                         "per-class, per-stage and per-level times; no benchmark line")
+    ap.add_argument("--fp64", action="store_true", help="with --profile-setup: FP64 factors")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile_setup:
+        return profile_setup(args)
 
     import numpy as np
     import torch
@@ -306,8 +376,11 @@ def main():
     if dom == "gemm":
         achieved = ds.flops / (ds.ms / 1000.0) / 1e12
         peak = fp32_alu_peak_tflops(peaks.get("sm_max_mhz", 2070.0))
+        bpf, tsrc = gemm_traffic_per_flop()
+        traffic = bpf * ds.flops / ds.launches if (bpf is not None and ds.launches) else None
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None, "kernel": "k_ggemm<float>",
+                "frac": achieved / peak, "traffic": traffic, "traffic_unit": "bytes per launch",
+                "traffic_source": tsrc, "kernel": "k_ggemm/k_gdot<float> (grouped GEMM family)",
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock",
                 "launches": ds.launches, "ms_total": ds.ms}
     else:
