@@ -248,6 +248,7 @@ def main():
     ap.add_argument("--n", type=int, default=128)
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--bf16-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--rank-cap", type=int, default=24)
     ap.add_argument("--profile-setup", action="store_true",
@@ -339,6 +340,14 @@ def main():
                 "setup_ms": inf64[-1][1].setup_ms, "max_rank": inf64[-1][1].max_rank,
                 "factor_gb": inf64[-1][1].factor_bytes / 1e9}
 
+    # BF16-stored factors (setup as FP32, factors rounded to bfloat16)
+    bf16 = None
+    if args.bf16_steps > 0:
+        msb, infb, _ = timed(acr.ACR_BF16, args.bf16_steps)
+        bf16 = {"s": msb / 1000.0, "iterations": infb[-1][0].iterations,
+                "rel_residual": infb[-1][0].rel_residual, "setup_ms": infb[-1][1].setup_ms,
+                "factor_gb": infb[-1][1].factor_bytes / 1e9}
+
     # end to end through the public API: pinned host inputs -> device,
     # assembly, setup, solve, solution -> host
     e2e = None
@@ -394,25 +403,30 @@ def main():
                                  for i, nm in enumerate(prof.STAGES)}
 
     # apply (hot loop of the solve): HBM roofline
-    h = acr.acr_setup(n, coef, eps, eta, leaf, acr.ACR_FP32, args.rank_cap, stream)
-    z = torch.empty_like(f_d)
-    for _ in range(3):
-        acr.acr_apply(h, f_d, z, 1, stream)
-    torch.cuda.synchronize()
-    ea = torch.cuda.Event(enable_timing=True)
-    eb = torch.cuda.Event(enable_timing=True)
-    ea.record(stream)
-    for _ in range(10):
-        acr.acr_apply(h, f_d, z, 1, stream)
-    eb.record(stream)
-    torch.cuda.synchronize()
-    apply_ms = ea.elapsed_time(eb) / 10
-    ainfo = acr.acr_get_setup_info(h)
-    acr.acr_destroy(h)
-    apply_gbs = ainfo.apply_bytes / (apply_ms / 1000.0) / 1e9
-    apply_roof = {"bound": "hbm", "achieved": apply_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                  "frac": apply_gbs / peaks["hbm_gbs"], "ms": apply_ms,
-                  "bytes_per_apply": ainfo.apply_bytes, "peak_source": peak_src}
+    def apply_roofline(prec):
+        h = acr.acr_setup(n, coef, eps, eta, leaf, prec, args.rank_cap, stream)
+        z = torch.empty_like(f_d)
+        for _ in range(3):
+            acr.acr_apply(h, f_d, z, 1, stream)
+        torch.cuda.synchronize()
+        ea = torch.cuda.Event(enable_timing=True)
+        eb = torch.cuda.Event(enable_timing=True)
+        ea.record(stream)
+        for _ in range(10):
+            acr.acr_apply(h, f_d, z, 1, stream)
+        eb.record(stream)
+        torch.cuda.synchronize()
+        apply_ms = ea.elapsed_time(eb) / 10
+        ainfo = acr.acr_get_setup_info(h)
+        acr.acr_destroy(h)
+        apply_gbs = ainfo.apply_bytes / (apply_ms / 1000.0) / 1e9
+        return {"bound": "hbm", "achieved": apply_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": apply_gbs / peaks["hbm_gbs"], "ms": apply_ms,
+                "bytes_per_apply": ainfo.apply_bytes, "peak_source": peak_src}
+
+    apply_roof = apply_roofline(acr.ACR_FP32)
+    if args.bf16_steps > 0:
+        apply_roof["bf16"] = apply_roofline(acr.ACR_BF16)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -432,7 +446,7 @@ def main():
             "iterations": solve_info.iterations, "rel_residual": solve_info.rel_residual,
             "setup_s": setup_info.setup_ms / 1000.0, "solve_s": solve_info.solve_ms / 1000.0,
             "max_rank": setup_info.max_rank, "factor_gb": setup_info.factor_bytes / 1e9,
-            "fp64_plain": fp64,
+            "fp64_plain": fp64, "bf16_factors": bf16,
             "speedup_vs_fp64": (fp64["s"] / (ms / 1000.0)) if fp64 else None,
             "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks,
             "roofline": roof, "apply_roofline": apply_roof, "cpu_baseline": cpu}

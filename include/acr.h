@@ -54,10 +54,14 @@ typedef enum {
 
 /* Arithmetic form of the H-matrix factors and of the setup / apply
  * arithmetic.  FP64: everything in double.  FP32: factors stored and
- * multiplied in float with float accumulation.  In every form the dense
- * leaf inverses, the small recompression cores and the Krylov iteration are
- * FP64. */
-typedef enum { ACR_FP64 = 0, ACR_FP32 = 1 } acr_precision;
+ * multiplied in float with float accumulation.  BF16: the setup runs exactly
+ * as in FP32; when it ends every stored factor (dense leaves, U, V) is
+ * rounded to bfloat16 (round to nearest even), halving the factor memory and
+ * the bytes an apply reads; the apply multiplies in float.  In every form
+ * the dense leaf inverses, the small recompression cores and the Krylov
+ * iteration are FP64.  (Reduced-precision storage is not in the paper, whose
+ * H-arithmetic is double precision throughout, Sec. 5.) */
+typedef enum { ACR_FP64 = 0, ACR_FP32 = 1, ACR_BF16 = 2 } acr_precision;
 
 typedef enum { ACR_PCG = 0, ACR_GMRES = 1 } acr_krylov;
 

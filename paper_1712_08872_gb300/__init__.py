@@ -6,7 +6,7 @@ entry-point names.  Importing this package does not load the library; the
 first call does, and fails loudly if it is missing.
 """
 from .acr import (  # noqa: F401
-    ACR_FP64, ACR_FP32, ACR_PCG, ACR_GMRES, AcrError, Grid, Options, SetupInfo,
+    ACR_FP64, ACR_FP32, ACR_BF16, ACR_PCG, ACR_GMRES, AcrError, Grid, Options, SetupInfo,
     SolveInfo, load_library, acr_stencil_poisson, acr_stencil_codi, acr_spmv, acr_setup,
     acr_apply, acr_apply_transpose, acr_krylov_solve, acr_krylov_solve_plain,
     acr_get_setup_info, acr_get_profile, acr_structure_query, ACR_FLAG_PROFILE,

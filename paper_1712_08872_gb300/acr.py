@@ -12,7 +12,7 @@ import os
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_lib", "libacr.so")
 
-ACR_FP64, ACR_FP32 = 0, 1
+ACR_FP64, ACR_FP32, ACR_BF16 = 0, 1, 2
 ACR_PCG, ACR_GMRES = 0, 1
 
 _STATUS = {0: "ok", 1: "invalid argument", 2: "out of device memory", 3: "CUDA error",

@@ -9,9 +9,10 @@
 //                + sum of U_l[rows of c] tv_l over low-rank leaves covering c)
 // Every stored dense entry and every U, V entry up to the block's rank is
 // read exactly once; the vectors are FP64.  FP64 factors accumulate in FP64;
-// FP32 factors multiply in FP32 and add short FP32 partial sums (at most 16
-// products) into FP64 accumulators, keeping the slow FP64 pipe off the
-// per-entry path.
+// FP32 and BF16 factors multiply in FP32 and add short FP32 partial sums (at
+// most 16 products) into FP64 accumulators, keeping the slow FP64 pipe off
+// the per-entry path.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <type_traits>
@@ -21,6 +22,11 @@
 namespace acr {
 
 namespace {
+
+// factor entry as the multiply type: double for FP64 factors, float otherwise
+__device__ __forceinline__ double ld(double v) { return v; }
+__device__ __forceinline__ float ld(float v) { return v; }
+__device__ __forceinline__ float ld(__nv_bfloat16 v) { return __bfloat162float(v); }
 
 template <typename T>
 __global__ void __launch_bounds__(128) k_lr_proj(MatvecDev mv, T* const* __restrict__ U,
@@ -41,15 +47,15 @@ __global__ void __launch_bounds__(128) k_lr_proj(MatvecDev mv, T* const* __restr
   for (int j = warp; j < k; j += 4) {
     const T* col = base + (int64_t)j * rows;
     double s = 0.0;
-    if (std::is_same<T, float>::value) {
+    if (!std::is_same<T, double>::value) {
       for (int i0 = lane; i0 < rows; i0 += 32 * 16) {
         float sf = 0.f;
         const int iend = min(rows, i0 + 32 * 16);
-        for (int i = i0; i < iend; i += 32) sf += (float)col[i] * (float)xp[start + i];
+        for (int i = i0; i < iend; i += 32) sf += (float)ld(col[i]) * (float)xp[start + i];
         s += (double)sf;
       }
     } else {
-      for (int i = lane; i < rows; i += 32) s += (double)col[i] * xp[start + i];
+      for (int i = lane; i < rows; i += 32) s += (double)ld(col[i]) * xp[start + i];
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
@@ -77,48 +83,37 @@ __global__ void __launch_bounds__(256) k_hmv_rows(MatvecDev mv, T* const* __rest
   const bool have = D[p] != nullptr && xp != nullptr;
   if (have && i < lsz) {
     const T* Dp = D[p];
-    constexpr bool f32 = std::is_same<T, float>::value;
-    if (!trans) {
-      for (int e = mv.d_ptr[c]; e < mv.d_ptr[c + 1]; ++e) {
-        const T* blk = Dp + (int64_t)mv.d_leaf[e] * lsz * lsz;
-        const double* xs = xp + mv.d_col[e];
-        if (f32) {
-          float sf = 0.f;
-          for (int j = g; j < lsz; j += 4) sf += (float)blk[i + (int64_t)j * lsz] * (float)xs[j];
-          acc += (double)sf;
-        } else {
-          for (int j = g; j < lsz; j += 4) acc += (double)blk[i + (int64_t)j * lsz] * xs[j];
-        }
+    constexpr bool f32 = !std::is_same<T, double>::value;
+    // sum_j M[i + j*ld] * v[j] over j = g, g+4, ... < len (stride-1 rows when
+    // tr is false, else the transposed access M[j + i*ld])
+    auto dotv = [&](const T* M, int ldm, bool tr, const double* v, int len) {
+      if (f32) {
+        float sf = 0.f;
+        for (int j = g; j < len; j += 4)
+          sf += (float)ld(M[tr ? j + (int64_t)i * ldm : i + (int64_t)j * ldm]) * (float)v[j];
+        acc += (double)sf;
+      } else {
+        for (int j = g; j < len; j += 4)
+          acc += (double)ld(M[tr ? j + (int64_t)i * ldm : i + (int64_t)j * ldm]) * v[j];
       }
+    };
+    if (!trans) {
+      for (int e = mv.d_ptr[c]; e < mv.d_ptr[c + 1]; ++e)
+        dotv(Dp + (int64_t)mv.d_leaf[e] * lsz * lsz, lsz, false, xp + mv.d_col[e], lsz);
       const T* Up = U[p];
       for (int e = mv.l_ptr[c]; e < mv.l_ptr[c + 1]; ++e) {
         const int l = mv.l_leaf[e];
-        const int k = rank[p][l];
-        const int m = mv.lr_m[l];
-        const T* ub = Up + mv.lr_row0[l] * mv.kc + mv.l_rowoff[e];
-        const double* t = tv + ((int64_t)p * mv.nl + l) * mv.kc;
-        if (f32) {
-          float sf = 0.f;
-          for (int j = g; j < k; j += 4) sf += (float)ub[i + (int64_t)j * m] * (float)t[j];
-          acc += (double)sf;
-        } else {
-          for (int j = g; j < k; j += 4) acc += (double)ub[i + (int64_t)j * m] * t[j];
-        }
+        dotv(Up + mv.lr_row0[l] * mv.kc + mv.l_rowoff[e], mv.lr_m[l], false,
+             tv + ((int64_t)p * mv.nl + l) * mv.kc, rank[p][l]);
       }
     } else {
-      for (int e = mv.dt_ptr[c]; e < mv.dt_ptr[c + 1]; ++e) {
-        const T* blk = Dp + (int64_t)mv.dt_leaf[e] * lsz * lsz;
-        const double* xs = xp + mv.dt_row[e];
-        for (int j = g; j < lsz; j += 4) acc += (double)blk[j + (int64_t)i * lsz] * xs[j];
-      }
+      for (int e = mv.dt_ptr[c]; e < mv.dt_ptr[c + 1]; ++e)
+        dotv(Dp + (int64_t)mv.dt_leaf[e] * lsz * lsz, lsz, true, xp + mv.dt_row[e], lsz);
       const T* Vp = V[p];
       for (int e = mv.lt_ptr[c]; e < mv.lt_ptr[c + 1]; ++e) {
         const int l = mv.lt_leaf[e];
-        const int k = rank[p][l];
-        const int n = mv.lr_n[l];
-        const T* vb = Vp + mv.lr_col0[l] * mv.kc + mv.lt_coloff[e];
-        const double* t = tv + ((int64_t)p * mv.nl + l) * mv.kc;
-        for (int j = g; j < k; j += 4) acc += (double)vb[i + (int64_t)j * n] * t[j];
+        dotv(Vp + mv.lr_col0[l] * mv.kc + mv.lt_coloff[e], mv.lr_n[l], false,
+             tv + ((int64_t)p * mv.nl + l) * mv.kc, rank[p][l]);
       }
     }
   }
@@ -169,7 +164,21 @@ __global__ void k_copy_planes(double* const* __restrict__ dst, const double* con
     d[i] = s ? s[i] : 0.0;
 }
 
+__global__ void k_to_bf16(const float* __restrict__ in, __nv_bfloat16* __restrict__ out,
+                          int64_t count) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count;
+       e += (int64_t)gridDim.x * blockDim.x)
+    out[e] = __float2bfloat16_rn(in[e]);
+}
+
 }  // namespace
+
+void launch_to_bf16(const float* in, void* out, int64_t count, cudaStream_t st) {
+  if (count <= 0) return;
+  const int blocks = (int)std::min<int64_t>((count + 255) / 256, 152 * 16);
+  k_to_bf16<<<blocks, 256, 0, st>>>(in, (__nv_bfloat16*)out, count);
+  ACR_LAUNCHED(1);
+}
 
 template <typename T>
 void launch_hmatvec(const MatvecDev& mv, T* const* dense, T* const* U, T* const* V,
@@ -214,5 +223,10 @@ template void launch_hmatvec<double>(const MatvecDev&, double* const*, double* c
 template void launch_hmatvec<float>(const MatvecDev&, float* const*, float* const*, float* const*,
                                     const int* const*, const double* const*, double* const*,
                                     double, double, bool, double*, int, cudaStream_t);
+template void launch_hmatvec<__nv_bfloat16>(const MatvecDev&, __nv_bfloat16* const*,
+                                            __nv_bfloat16* const*, __nv_bfloat16* const*,
+                                            const int* const*, const double* const*,
+                                            double* const*, double, double, bool, double*, int,
+                                            cudaStream_t);
 
 }  // namespace acr

@@ -8,6 +8,7 @@
 // column-major per leaf with kc = rank capacity, and one int rank per
 // low-rank leaf.  Vectors inside the apply are FP64 in cluster order, one
 // plane after another.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -19,6 +20,7 @@
 #include <memory>
 #include <stdexcept>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include <nvtx3/nvToolsExt.h>
@@ -116,8 +118,8 @@ class EngineBase {
 template <typename T>
 class Engine : public EngineBase {
  public:
-  Engine(int n_, double eps_, double eta_, int leaf_, int kc_, int flags_) : eps(eps_), eta(eta_),
-      leaf(leaf_), kc(kc_) {
+  Engine(int n_, double eps_, double eta_, int leaf_, int kc_, int flags_, bool bf16_ = false)
+      : eps(eps_), eta(eta_), leaf(leaf_), kc(kc_), bf16(bf16_ && std::is_same<T, float>::value) {
     profiling = (flags_ & ACR_FLAG_PROFILE) != 0;
     n = n_;
     n2 = n * n;
@@ -131,7 +133,9 @@ class Engine : public EngineBase {
  private:
   double eps, eta;
   int leaf, kc;
+  bool bf16;                         // stored factors rounded to bfloat16 after the setup
   int n2 = 0;
+  size_t store_bytes() const { return bf16 ? 2 : sizeof(T); }
   Structure S;
   StructDev sd;
   MatvecPlan mvp;
@@ -231,6 +235,41 @@ class Engine : public EngineBase {
       if (it->dense == h.dense) { heap.erase(it); break; }
     cudaFree(h.dense); cudaFree(h.U); cudaFree(h.V); cudaFree(h.rank);
     h = HM();
+  }
+  // BF16 form: round every H-matrix still held after the setup (the stored
+  // factors) to bfloat16, replacing its dense / U / V arrays
+  void convert_bf16(cudaStream_t st) {
+    const size_t dn = std::max<size_t>((size_t)S.dleaf.size() * S.lsz * S.lsz, 1);
+    const size_t un = std::max<size_t>((size_t)S.sumM * kc, 1);
+    const size_t vn = std::max<size_t>((size_t)S.sumN * kc, 1);
+    for (HM& h : heap) {
+      HM b = h;
+      b.dense = b.U = b.V = nullptr;
+      try {
+        b.dense = dmalloc(dn * 2);
+        b.U = dmalloc(un * 2);
+        b.V = dmalloc(vn * 2);
+      } catch (...) {
+        cudaFree(b.dense); cudaFree(b.U); cudaFree(b.V);   // cudaFree(nullptr) is a no-op
+        throw;
+      }
+      launch_to_bf16((const float*)h.dense, b.dense, (int64_t)dn, st);
+      launch_to_bf16((const float*)h.U, b.U, (int64_t)un, st);
+      launch_to_bf16((const float*)h.V, b.V, (int64_t)vn, st);
+      ACR_CUDA(cudaStreamSynchronize(st));
+      // every reference moves to the new arrays before the old ones are
+      // freed (a later allocation may reuse a freed address)
+      auto remap = [&](HM& r) {
+        if (r.dense && r.dense == h.dense) r = b;
+      };
+      for (HM& r : D) remap(r);
+      for (Level& lev : levels) {
+        for (HM& r : lev.L) remap(r);
+        for (HM& r : lev.U) remap(r);
+      }
+      cudaFree(h.dense); cudaFree(h.U); cudaFree(h.V);
+      h = b;
+    }
   }
   void release() {
     for (HM& h : heap) { cudaFree(h.dense); cudaFree(h.U); cudaFree(h.V); cudaFree(h.rank); }
@@ -758,6 +797,7 @@ void Engine<T>::setup(const double* coef, cudaStream_t st) {
     if (profiling && r < 16)
       prof.inv_ms[r] = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   }
+  if (bf16) convert_bf16(st);
   ACR_CUDA(cudaEventRecord(e1, st));
   ACR_CUDA(cudaEventSynchronize(e1));
   float ms = 0;
@@ -809,7 +849,7 @@ void Engine<T>::collect_info() {
       used += (int64_t)rk[l] * (mvp.lr_m[l] + mvp.lr_n[l]);
     }
     hm_used[h.dense] = used;
-    bytes += used * (int64_t)sizeof(T);
+    bytes += used * (int64_t)store_bytes();
   };
   for (const Level& lev : levels) {
     for (int i : lev.red) account(D[i]);
@@ -819,7 +859,8 @@ void Engine<T>::collect_info() {
   info.max_rank = mx;
   info.avg_rank = cnt ? (double)sumr / cnt : 0.0;
   info.factor_bytes = bytes + 2 * N * (int64_t)sizeof(double);
-  int64_t per = ((int64_t)S.dleaf.size() * S.lsz * S.lsz + (S.sumM + S.sumN) * kc) * sizeof(T);
+  int64_t per = ((int64_t)S.dleaf.size() * S.lsz * S.lsz + (S.sumM + S.sumN) * kc) *
+                (int64_t)store_bytes();
   info.factor_capacity_bytes = per * (int64_t)heap.size() + 2 * N * (int64_t)sizeof(double);
 }
 
@@ -846,7 +887,7 @@ void Engine<T>::build_apply_program() {
         abytes += (int64_t)n2 * 8 * (beta != 0.0 ? 2 : 1);
         if (H[p].dense && x[p]) {
           const int64_t u = hm_used.count(H[p].dense) ? hm_used[H[p].dense] : 0;
-          abytes += u * (int64_t)sizeof(T) + (int64_t)n2 * 8;
+          abytes += u * (int64_t)store_bytes() + (int64_t)n2 * 8;
           aflops += 2 * u;
         }
       }
@@ -993,7 +1034,12 @@ void Engine<T>::run_steps(const std::vector<ApplyStep>& steps, cudaStream_t st) 
   for (const ApplyStep& s : steps) {
     const int P = s.P;
     void** t = s.tabs;
-    if (s.kind == 0) {
+    if (s.kind == 0 && bf16) {
+      using B = __nv_bfloat16;
+      launch_hmatvec<B>(mvd, (B* const*)t, (B* const*)(t + P), (B* const*)(t + 2 * P),
+                        (const int* const*)(t + 3 * P), (const double* const*)(t + 4 * P),
+                        (double* const*)(t + 5 * P), s.alpha, s.beta, s.trans, tvscr, P, st);
+    } else if (s.kind == 0) {
       launch_hmatvec<T>(mvd, (T* const*)t, (T* const*)(t + P), (T* const*)(t + 2 * P),
                         (const int* const*)(t + 3 * P), (const double* const*)(t + 4 * P),
                         (double* const*)(t + 5 * P), s.alpha, s.beta, s.trans, tvscr, P, st);
@@ -1308,7 +1354,8 @@ acr_status acr_setup(const acr_grid* grid, const double* coef, const acr_options
   if (out) *out = nullptr;
   if (!grid_ok(grid) || !coef || !opt || !out) return ACR_ERR_INVALID_ARG;
   if (!(opt->eps > 0.0 && opt->eps < 1.0) || !(opt->eta > 0.0) || opt->leaf < 1 ||
-      (opt->precision != ACR_FP64 && opt->precision != ACR_FP32) || opt->rank_cap < 0 ||
+      (opt->precision != ACR_FP64 && opt->precision != ACR_FP32 &&
+       opt->precision != ACR_BF16) || opt->rank_cap < 0 ||
       opt->rank_cap > 48)
     return ACR_ERR_INVALID_ARG;
   const int kc = opt->rank_cap == 0 ? 32 : opt->rank_cap;
@@ -1319,7 +1366,8 @@ acr_status acr_setup(const acr_grid* grid, const double* coef, const acr_options
     if (opt->precision == ACR_FP64)
       h->e = new acr::Engine<double>(grid->nx, opt->eps, opt->eta, opt->leaf, kc, opt->flags);
     else
-      h->e = new acr::Engine<float>(grid->nx, opt->eps, opt->eta, opt->leaf, kc, opt->flags);
+      h->e = new acr::Engine<float>(grid->nx, opt->eps, opt->eta, opt->leaf, kc, opt->flags,
+                                    opt->precision == ACR_BF16);
     h->e->setup(coef, stream);
     return 0;
   });

@@ -108,6 +108,8 @@ void launch_hmatvec(const MatvecDev& mv, T* const* dense, T* const* U, T* const*
                     const int* const* rank, const double* const* x, double* const* y,
                     double alpha, double beta, bool trans, double* tv, int P, cudaStream_t st);
 
+// out[e] = bfloat16(in[e]) (round to nearest even), e < count; out is __nv_bfloat16*
+void launch_to_bf16(const float* in, void* out, int64_t count, cudaStream_t st);
 void launch_permute(const double* in, double* out, const int* perm, int n2, int nplanes,
                     bool to_cluster, cudaStream_t st);
 // y_p -= a_p .* x_p + b_p .* z_p (diagonal couplings; null pointers skipped)

@@ -57,14 +57,6 @@ constexpr int STAGE_BYTES = 36864;   // shared staging of one K-chunk (A and B p
 
 // One CTA computes the (m x n) output tile of one group for one plane:
 //   C = beta C + sum_items coef * op(A)[rows] op(B)
-// Large tiles (m, n > 32) use 4x4 register blocking over 64x64; every other
-// tile spreads its m*n outputs over the threads and, when there are fewer
-// outputs than threads, splits each K-chunk across the spare threads and
-// reduces the partial sums in shared memory.  K-chunks are exact (no zero
-// padding) and sized to the staging buffer, so thin long products stream
-// their operands in a few large coalesced chunks.
-// One CTA computes the (m x n) output tile of one group for one plane:
-//   C = beta C + sum_items coef * op(A)[rows] op(B)
 // Items are concatenated along K in a shared staging buffer (each item's
 // coefficient folded into its A panel, rows outside the item zero), so a
 // group of many thin items costs one barrier pair per full chunk.  Large
