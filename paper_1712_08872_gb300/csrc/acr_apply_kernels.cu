@@ -29,41 +29,96 @@ __device__ __forceinline__ float ld(float v) { return v; }
 __device__ __forceinline__ float ld(__nv_bfloat16 v) { return __bfloat162float(v); }
 
 template <typename T>
-__global__ void __launch_bounds__(128) k_lr_proj(MatvecDev mv, T* const* __restrict__ U,
+using AccT = typename std::conditional<std::is_same<T, double>::value, double, float>::type;
+
+constexpr int MAXQ = 256;   // most low-rank leaves covering one chunk
+
+// Partial projections, one CTA per (leaf-size column chunk c, plane p): for
+// every low-rank leaf l whose columns cover chunk c, the piece of
+// tv_l = V_l^T x over those columns (transposed: U_l^T x over the rows of
+// chunk c), stored as segment seg_ptr[l] + offset / lsz; the consumer sums a
+// leaf's segments in order.  The x chunk and the leaves' descriptors are
+// staged in shared memory; groups of 8 lanes take (leaf, column) pairs, each
+// lane 8 of the chunk's rows.
+template <typename T>
+__global__ void __launch_bounds__(256) k_lr_proj(MatvecDev mv, T* const* __restrict__ U,
                                                  T* const* __restrict__ V,
                                                  const int* const* __restrict__ rank,
                                                  const double* const* __restrict__ x, double* tv,
                                                  bool trans) {
-  const int l = blockIdx.x, p = blockIdx.y;
-  const T* Vb = trans ? U[p] : V[p];
+  using Acc = AccT<T>;
+  __shared__ Acc xs[64];
+  __shared__ int64_t s_off[MAXQ];
+  __shared__ int s_ld[MAXQ], s_seg[MAXQ], s_cum[MAXQ + 1];
+  const int c = blockIdx.x, p = blockIdx.y;
+  const T* Fb = trans ? U[p] : V[p];
   const double* xp = x[p];
-  if (!Vb || !xp) return;
-  const int k = rank[p][l];
-  const int rows = trans ? mv.lr_m[l] : mv.lr_n[l];
-  const int start = trans ? mv.lr_t0[l] : mv.lr_s0[l];
-  const T* base = Vb + (trans ? mv.lr_row0[l] : mv.lr_col0[l]) * mv.kc;
-  double* out = tv + ((int64_t)p * mv.nl + l) * mv.kc;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int j = warp; j < k; j += 4) {
-    const T* col = base + (int64_t)j * rows;
-    double s = 0.0;
-    if (!std::is_same<T, double>::value) {
-      for (int i0 = lane; i0 < rows; i0 += 32 * 16) {
-        float sf = 0.f;
-        const int iend = min(rows, i0 + 32 * 16);
-        for (int i = i0; i < iend; i += 32) sf += (float)ld(col[i]) * (float)xp[start + i];
-        s += (double)sf;
+  if (!Fb || !xp) return;
+  const int lsz = mv.lsz, kc = mv.kc;
+  const int* ptr = trans ? mv.l_ptr : mv.lt_ptr;
+  const int* lf = trans ? mv.l_leaf : mv.lt_leaf;
+  const int* lo = trans ? mv.l_rowoff : mv.lt_coloff;
+  const int* sptr = trans ? mv.segt_ptr : mv.seg_ptr;
+  const int nseg = trans ? mv.nsegt : mv.nseg;
+  const int q0 = ptr[c], nq = min(ptr[c + 1] - q0, MAXQ);
+  if (threadIdx.x < lsz) xs[threadIdx.x] = (Acc)xp[(int64_t)c * lsz + threadIdx.x];
+  for (int q = threadIdx.x; q < nq; q += 256) {
+    const int l = lf[q0 + q];
+    s_cum[q + 1] = rank[p][l];
+    s_ld[q] = trans ? mv.lr_m[l] : mv.lr_n[l];
+    s_off[q] = (trans ? mv.lr_row0[l] : mv.lr_col0[l]) * kc + lo[q0 + q];
+    s_seg[q] = sptr[l] + lo[q0 + q] / lsz;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    s_cum[0] = 0;
+    for (int q = 0; q < nq; ++q) s_cum[q + 1] += s_cum[q];
+  }
+  __syncthreads();
+  // 8-lane groups: group w (32 per CTA) takes pairs w, w + 32, ...; lane
+  // r of a group the rows r + 8 t (partial sums of at most 8 products)
+  const int grp = threadIdx.x >> 3, r = threadIdx.x & 7;
+  const int total = s_cum[nq];
+  for (int t0 = 0; t0 < total; t0 += 32) {
+    const int t = t0 + grp;
+    double d = 0.0;
+    int q = 0, j = 0;
+    if (t < total) {
+      int lo_q = 0, hi_q = nq;   // the q with s_cum[q] <= t < s_cum[q + 1]
+      while (hi_q - lo_q > 1) {
+        const int mid = (lo_q + hi_q) >> 1;
+        if (s_cum[mid] <= t) lo_q = mid; else hi_q = mid;
       }
-    } else {
-      for (int i = lane; i < rows; i += 32) s += (double)ld(col[i]) * xp[start + i];
-    }
+      q = lo_q;
+      j = t - s_cum[q];
+      const T* col = Fb + s_off[q] + (int64_t)j * s_ld[q];
+      Acc v = Acc(0);
+      if (lsz == 64) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) out[j] = s;
+        for (int u = 0; u < 8; ++u) v += (Acc)ld(col[r + 8 * u]) * xs[r + 8 * u];
+      } else {
+        for (int i = r; i < lsz; i += 8) v += (Acc)ld(col[i]) * xs[i];
+      }
+      d = (double)v;
+    }
+    // the loop bound is uniform over the CTA, so every lane reaches the shuffles
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+    if (t < total && r == 0) tv[((int64_t)p * nseg + s_seg[q]) * kc + j] = d;
   }
 }
 
-template <typename T>
+// One CTA per (leaf-size row chunk c, plane p): y[c] = beta y[c] + alpha
+// (dense leaves of block row c times x + U_l[rows of c] tv_l over the
+// low-rank leaves covering c); transposed: the block column's dense leaves
+// transposed and V_l[cols of c] tv_l.  The x segments and tv vectors the
+// chunk needs are staged in shared memory first (converted once to the
+// multiply type), with the chunk's leaf descriptors (rank, offset, leading
+// dimension).  Thread t owns row t % 64: of each dense leaf the columns
+// t / 64 + 4 j, of the low-rank leaves every fourth one (starting at t / 64)
+// with all its columns.  LSZ > 0 fixes the leaf size at compile time
+// (unrolled, 16 loads in flight).
+template <typename T, int LSZ>
 __global__ void __launch_bounds__(256) k_hmv_rows(MatvecDev mv, T* const* __restrict__ D,
                                                   T* const* __restrict__ U,
                                                   T* const* __restrict__ V,
@@ -72,58 +127,104 @@ __global__ void __launch_bounds__(256) k_hmv_rows(MatvecDev mv, T* const* __rest
                                                   double* const* __restrict__ y, double alpha,
                                                   double beta, const double* __restrict__ tv,
                                                   bool trans) {
+  using Acc = AccT<T>;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  Acc* xs = reinterpret_cast<Acc*>(smraw);
+  __shared__ double part[4][64];
   const int c = blockIdx.x, p = blockIdx.y;
   double* yp = y[p];
   if (!yp) return;
   const double* xp = x[p];
-  const int lsz = mv.lsz;
-  const int i = threadIdx.x % 64, g = threadIdx.x / 64;
-  __shared__ double part[4][64];
-  double acc = 0.0;
+  const int lsz = LSZ > 0 ? LSZ : mv.lsz;
+  const int i = threadIdx.x & 63, g = threadIdx.x >> 6;
   const bool have = D[p] != nullptr && xp != nullptr;
+  const int* dptr = trans ? mv.dt_ptr : mv.d_ptr;
+  const int* dleaf = trans ? mv.dt_leaf : mv.d_leaf;
+  const int* dcol = trans ? mv.dt_row : mv.d_col;
+  const int* lptr = trans ? mv.lt_ptr : mv.l_ptr;
+  const int* lleaf = trans ? mv.lt_leaf : mv.l_leaf;
+  const int d0 = dptr[c], nd = dptr[c + 1] - d0;
+  const int l0 = lptr[c], nlc = lptr[c + 1] - l0;
+  const int kc = mv.kc;
+  Acc* ts = xs + nd * lsz;
+  // per-leaf descriptors of this chunk, loaded once in parallel
+  __shared__ int64_t s_off[MAXQ];
+  __shared__ int s_ld[MAXQ], s_k[MAXQ], s_leaf[MAXQ];
+  if (have) {
+    for (int q = threadIdx.x; q < nd && q < MAXQ; q += 256) s_leaf[q] = dleaf[d0 + q];
+    for (int q = threadIdx.x; q < nlc && q < MAXQ; q += 256) {
+      const int l = lleaf[l0 + q];
+      s_k[q] = rank[p][l];
+      s_ld[q] = trans ? mv.lr_n[l] : mv.lr_m[l];
+      s_off[q] = trans ? mv.lr_col0[l] * kc + mv.lt_coloff[l0 + q]
+                       : mv.lr_row0[l] * kc + mv.l_rowoff[l0 + q];
+    }
+    for (int e = threadIdx.x; e < nd * lsz; e += 256) {
+      const int q = e / lsz, j = e - q * lsz;
+      xs[e] = (Acc)xp[dcol[d0 + q] + j];
+    }
+    const int* sptr = trans ? mv.segt_ptr : mv.seg_ptr;
+    const int nseg = trans ? mv.nsegt : mv.nseg;
+    for (int e = threadIdx.x; e < nlc * kc; e += 256) {
+      const int q = e / kc, j = e - q * kc;
+      const int l = lleaf[l0 + q];
+      double v = 0.0;
+      if (j < rank[p][l])
+        for (int sg = sptr[l]; sg < sptr[l + 1]; ++sg) v += tv[((int64_t)p * nseg + sg) * kc + j];
+      ts[e] = (Acc)v;
+    }
+  }
+  __syncthreads();
+  double acc = 0.0;
   if (have && i < lsz) {
     const T* Dp = D[p];
-    constexpr bool f32 = !std::is_same<T, double>::value;
-    // sum_j M[i + j*ld] * v[j] over j = g, g+4, ... < len (stride-1 rows when
-    // tr is false, else the transposed access M[j + i*ld])
-    auto dotv = [&](const T* M, int ldm, bool tr, const double* v, int len) {
-      if (f32) {
-        float sf = 0.f;
-        for (int j = g; j < len; j += 4)
-          sf += (float)ld(M[tr ? j + (int64_t)i * ldm : i + (int64_t)j * ldm]) * (float)v[j];
-        acc += (double)sf;
+    for (int q = 0; q < nd; ++q) {
+      const T* blk = Dp + (int64_t)(q < MAXQ ? s_leaf[q] : dleaf[d0 + q]) * lsz * lsz;
+      const Acc* xq = xs + q * lsz;
+      Acc sp = Acc(0);
+      if (LSZ > 0) {
+#pragma unroll
+        for (int t = 0; t < (LSZ > 0 ? LSZ : 64) / 4; ++t) {
+          const int j = g + 4 * t;
+          sp += (Acc)ld(blk[trans ? j + i * LSZ : i + j * LSZ]) * xq[j];
+        }
       } else {
-        for (int j = g; j < len; j += 4)
-          acc += (double)ld(M[tr ? j + (int64_t)i * ldm : i + (int64_t)j * ldm]) * v[j];
+        for (int j = g; j < lsz; j += 4)
+          sp += (Acc)ld(blk[trans ? j + (int64_t)i * lsz : i + (int64_t)j * lsz]) * xq[j];
       }
-    };
-    if (!trans) {
-      for (int e = mv.d_ptr[c]; e < mv.d_ptr[c + 1]; ++e)
-        dotv(Dp + (int64_t)mv.d_leaf[e] * lsz * lsz, lsz, false, xp + mv.d_col[e], lsz);
-      const T* Up = U[p];
-      for (int e = mv.l_ptr[c]; e < mv.l_ptr[c + 1]; ++e) {
-        const int l = mv.l_leaf[e];
-        dotv(Up + mv.lr_row0[l] * mv.kc + mv.l_rowoff[e], mv.lr_m[l], false,
-             tv + ((int64_t)p * mv.nl + l) * mv.kc, rank[p][l]);
+      acc += (double)sp;
+    }
+    // low-rank leaves: thread group g takes leaves g, g+4, ...; all of a
+    // leaf's columns, partial sums of at most 16 products
+    const T* Fp = trans ? V[p] : U[p];
+    for (int q = g; q < nlc; q += 4) {
+      int k, ldm;
+      int64_t off;
+      if (q < MAXQ) {
+        k = s_k[q]; ldm = s_ld[q]; off = s_off[q];
+      } else {
+        const int l = lleaf[l0 + q];
+        k = rank[p][l];
+        ldm = trans ? mv.lr_n[l] : mv.lr_m[l];
+        off = trans ? mv.lr_col0[l] * kc + mv.lt_coloff[l0 + q] : mv.lr_row0[l] * kc + mv.l_rowoff[l0 + q];
       }
-    } else {
-      for (int e = mv.dt_ptr[c]; e < mv.dt_ptr[c + 1]; ++e)
-        dotv(Dp + (int64_t)mv.dt_leaf[e] * lsz * lsz, lsz, true, xp + mv.dt_row[e], lsz);
-      const T* Vp = V[p];
-      for (int e = mv.lt_ptr[c]; e < mv.lt_ptr[c + 1]; ++e) {
-        const int l = mv.lt_leaf[e];
-        dotv(Vp + mv.lr_col0[l] * mv.kc + mv.lt_coloff[e], mv.lr_n[l], false,
-             tv + ((int64_t)p * mv.nl + l) * mv.kc, rank[p][l]);
+      const T* fb = Fp + off + i;
+      const Acc* tq = ts + q * kc;
+      for (int j0 = 0; j0 < k; j0 += 16) {
+        Acc sp = Acc(0);
+        const int j1 = min(k, j0 + 16);
+        for (int j = j0; j < j1; ++j) sp += (Acc)ld(fb[(int64_t)j * ldm]) * tq[j];
+        acc += (double)sp;
       }
     }
   }
   part[g][i] = acc;
   __syncthreads();
   if (g == 0 && i < lsz) {
-    const double s = part[0][i] + part[1][i] + part[2][i] + part[3][i];
+    const double sum = part[0][i] + part[1][i] + part[2][i] + part[3][i];
     double* yc = yp + (int64_t)c * lsz;
     const double old = (beta != 0.0) ? beta * yc[i] : 0.0;
-    yc[i] = old + (have ? alpha * s : 0.0);
+    yc[i] = old + (have ? alpha * sum : 0.0);
   }
 }
 
@@ -185,9 +286,28 @@ void launch_hmatvec(const MatvecDev& mv, T* const* dense, T* const* U, T* const*
                     const int* const* rank, const double* const* x, double* const* y,
                     double alpha, double beta, bool trans, double* tv, int P, cudaStream_t st) {
   if (P <= 0) return;
-  if (mv.nl > 0) k_lr_proj<T><<<dim3(mv.nl, P), 128, 0, st>>>(mv, U, V, rank, x, tv, trans);
-  k_hmv_rows<T><<<dim3(mv.nchunks, P), 256, 0, st>>>(mv, dense, U, V, rank, x, y, alpha, beta, tv,
-                                                     trans);
+  using Acc = AccT<T>;
+  const size_t sm_rows = ((size_t)mv.max_d * mv.lsz + (size_t)mv.max_l * mv.kc) * sizeof(Acc);
+  static bool attr_set = false;   // per instantiation: allow the largest staging buffers
+  if (!attr_set) {
+    ACR_CUDA(cudaFuncSetAttribute(k_hmv_rows<T, 64>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    ACR_CUDA(cudaFuncSetAttribute(k_hmv_rows<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  200 * 1024));
+    attr_set = true;
+  }
+  if (mv.max_l > MAXQ || mv.lsz > 64)
+    throw CudaError{cudaErrorInvalidConfiguration, "more low-rank leaves per chunk than staged"};
+  if (sm_rows > 200 * 1024)
+    throw CudaError{cudaErrorInvalidConfiguration, "apply staging exceeds shared memory"};
+  if (mv.nl > 0)
+    k_lr_proj<T><<<dim3(mv.nchunks, P), 256, 0, st>>>(mv, U, V, rank, x, tv, trans);
+  if (mv.lsz == 64)
+    k_hmv_rows<T, 64><<<dim3(mv.nchunks, P), 256, sm_rows, st>>>(mv, dense, U, V, rank, x, y,
+                                                                   alpha, beta, tv, trans);
+  else
+    k_hmv_rows<T, 0><<<dim3(mv.nchunks, P), 256, sm_rows, st>>>(mv, dense, U, V, rank, x, y,
+                                                                  alpha, beta, tv, trans);
   ACR_LAUNCHED(mv.nl > 0 ? 2 : 1);
 }
 

@@ -619,6 +619,17 @@ void Engine<T>::setup(const double* coef, cudaStream_t st) {
   mvd.lr_row0 = sd.row0;
   mvd.lr_col0 = sd.col0;
   mvd.nchunks = S.nleafcl; mvd.lsz = S.lsz; mvd.nl = sd.nl; mvd.kc = kc;
+  mvd.max_d = mvd.max_l = mvd.max_lr_rows = 0;
+  for (int c = 0; c < S.nleafcl; ++c) {
+    mvd.max_d = std::max({mvd.max_d, mvp.d_ptr[c + 1] - mvp.d_ptr[c], mvp.dt_ptr[c + 1] - mvp.dt_ptr[c]});
+    mvd.max_l = std::max({mvd.max_l, mvp.l_ptr[c + 1] - mvp.l_ptr[c], mvp.lt_ptr[c + 1] - mvp.lt_ptr[c]});
+  }
+  for (size_t l = 0; l < mvp.lr_m.size(); ++l)
+    mvd.max_lr_rows = std::max({mvd.max_lr_rows, mvp.lr_m[l], mvp.lr_n[l]});
+  mvd.seg_ptr = (const int32_t*)upload(mvp.seg_ptr, owned);
+  mvd.segt_ptr = (const int32_t*)upload(mvp.segt_ptr, owned);
+  mvd.nseg = mvp.seg_ptr.back();
+  mvd.nsegt = mvp.segt_ptr.back();
   std::vector<double> coefs{1.0, -1.0};
   d_coefs = (double*)upload(coefs, owned);
   d_err = (int*)dmalloc(sizeof(int));
@@ -872,7 +883,8 @@ void Engine<T>::build_apply_program() {
   Tv = (double*)dmalloc(sizeof(double) * N); owned.push_back(Tv);
   maxP = 1;
   for (const Level& lev : levels) maxP = std::max<int>(maxP, (int)std::max(lev.red.size(), lev.black.size()));
-  tvscr = (double*)dmalloc(sizeof(double) * (size_t)maxP * std::max(sd.nl, 1) * kc);
+  tvscr = (double*)dmalloc(sizeof(double) * (size_t)maxP *
+                          std::max({mvd.nseg, mvd.nsegt, 1}) * kc);
   owned.push_back(tvscr);
   auto vec = [&](double* base, int k) -> double* { return (k >= 0 && k < n) ? base + (int64_t)k * n2 : nullptr; };
   // hmatvec tables: dense, U, V, rank, x, y (6 * P pointers)

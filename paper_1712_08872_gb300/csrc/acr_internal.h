@@ -98,10 +98,16 @@ struct MatvecDev {
   const int32_t *lr_m, *lr_n, *lr_t0, *lr_s0;
   const int64_t *lr_row0, *lr_col0;
   int nchunks, lsz, nl, kc;
+  int max_d, max_l;      // most dense / low-rank leaves of one row (or column) chunk
+  int max_lr_rows;       // largest row or column count of a low-rank leaf
+  // projection segments: leaf l's V rows (transposed: U rows) in leaf-size
+  // pieces, numbered seg_ptr[l] + piece
+  const int32_t *seg_ptr, *segt_ptr;
+  int nseg, nsegt;
 };
 
 // y_p = beta*y_p + alpha*op(H_p) x_p for P planes; op = H or H^T.
-// tv: scratch of P*nl*kc doubles.  Null H_p skips the plane (y_p scaled
+// tv: scratch of P*max(nseg,nsegt)*kc doubles.  Null H_p skips the plane (y_p scaled
 // by beta only if beta != 1).
 template <typename T>
 void launch_hmatvec(const MatvecDev& mv, T* const* dense, T* const* U, T* const* V,

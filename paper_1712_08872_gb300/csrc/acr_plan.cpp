@@ -683,6 +683,12 @@ void MatvecPlan::build(const Structure& S) {
   csr(lr, lro, l_ptr, l_leaf, l_rowoff);
   csr(dc, dco, dt_ptr, dt_leaf, dt_row);
   csr(lc, lco, lt_ptr, lt_leaf, lt_coloff);
+  auto segs = [&](const std::vector<int32_t>& rows, std::vector<int32_t>& ptr) {
+    ptr.assign(rows.size() + 1, 0);
+    for (size_t l = 0; l < rows.size(); ++l) ptr[l + 1] = ptr[l] + (rows[l] + lsz - 1) / lsz;
+  };
+  segs(lr_n, seg_ptr);
+  segs(lr_m, segt_ptr);
 }
 
 }  // namespace acr

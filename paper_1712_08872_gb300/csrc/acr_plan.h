@@ -151,6 +151,11 @@ struct MatvecPlan {
   std::vector<int32_t> dt_ptr, dt_leaf, dt_row;  // transposed: dense leaves of block column c
   std::vector<int32_t> lt_ptr, lt_leaf, lt_coloff;
   std::vector<int32_t> lr_m, lr_n, lr_t0, lr_s0; // per lr leaf: sizes and row / col start
+  // projection segments: every low-rank leaf's V (transposed: U) rows cut
+  // at the leaf-size chunks they cover; segment r of leaf l is number
+  // seg_ptr[l] + r (rows r*lsz .. (r+1)*lsz of the leaf)
+  std::vector<int32_t> seg_ptr;    // over lr_n (tv = V^T x)
+  std::vector<int32_t> segt_ptr;   // over lr_m (tv = U^T x)
   void build(const Structure& S);
 };
 
