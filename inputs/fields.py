@@ -83,20 +83,31 @@ def uniform_rhs(n, seed, nrhs=1):
 
 
 # Workloads of the benchmark suite: the PDE, its coefficient field and the
-# preconditioner / Krylov settings.  eta for the n=64 and n=128 cases is n/2
-# (the memory-optimal admissibility the paper reports for planes of this
-# size); the n=16 case uses the eta it is specified with.
+# preconditioner / Krylov settings.  eta = 2 (the paper's strong setting) for
+# the cases that do not specify it; the n=16 case uses the eta it is
+# specified with.  poisson_grad_n96 is the differentiable solve: kappa as in
+# poisson_grf_n16, the observation u_obs solved from a second field (seed
+# 100), finite-difference cells drawn with seed 101.
 WORKLOADS = {
     "poisson_grf_n16": dict(pde="poisson", n=16, field="grf", field_seed=0,
                             rhs_seed=1, eps=1e-6, eta=1.0, leaf=32,
                             krylov="pcg", rtol=1e-10),
     "poisson_boxes_n64": dict(pde="poisson", n=64, field="boxes", field_seed=10,
-                              rhs_seed=11, eps=1e-2, eta=32.0, leaf=64,
+                              rhs_seed=11, eps=1e-2, eta=2.0, leaf=64,
                               krylov="pcg", rtol=1e-8),
     "codi_n128": dict(pde="codi", n=128, field="codi", field_seed=None,
-                      rhs_seed=20, eps=1e-2, eta=64.0, leaf=64,
+                      rhs_seed=20, eps=1e-2, eta=2.0, leaf=64,
                       krylov="gmres", rtol=1e-8, restart=30),
+    "poisson_grad_n96": dict(pde="poisson", n=96, field="grf", field_seed=0,
+                             rhs_seed=1, obs_seed=100, fd_seed=101, fd_cells=20,
+                             eps=1e-2, eta=2.0, leaf=64, krylov="pcg", rtol=1e-10),
 }
+
+
+def fd_cells(n, seed, count):
+    """``count`` distinct node indices drawn uniformly (finite-difference
+    checks of a gradient)."""
+    return np.random.default_rng(seed).choice(n ** 3, size=count, replace=False)
 
 
 def workload(name, n=None):

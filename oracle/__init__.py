@@ -17,6 +17,8 @@ variable coefficients", JCAM 2017):
                     Sec. 4.2): setup (elimination) and apply (substitution).
 * ``krylov``     -- FP64 preconditioned CG and right-preconditioned GMRES(m)
                     (Sec. 5.3, Sec. 7).
+* ``adjoint``    -- dL/dkappa of a Poisson solve by the adjoint of the Sec. 6
+                    assembly (no counterpart in the paper).
 
 Only the test-suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import this package.  The product path (the CUDA library
