@@ -195,6 +195,28 @@ acr_status acr_krylov_solve(acr_handle* h, const double* coef, int32_t method, i
                             double rtol, int32_t maxit, const double* f, double* u,
                             int32_t nrhs, acr_solve_info* info, cudaStream_t stream);
 
+/* Adjoint solve A^T u = f (the adjoint step of a differentiated solve; the
+ * paper has no counterpart): the same Krylov iteration with the transposed
+ * 7-point operator and the transposed preconditioner M^{-T}
+ * (acr_apply_transpose).  Arguments, results and errors as
+ * acr_krylov_solve. */
+acr_status acr_krylov_solve_transpose(acr_handle* h, const double* coef, int32_t method,
+                                      int32_t restart, double rtol, int32_t maxit,
+                                      const double* f, double* u, int32_t nrhs,
+                                      acr_solve_info* info, cudaStream_t stream);
+
+/* y = A^T x for the 7-point operator (FP64), nrhs vectors back to back. */
+acr_status acr_spmv_transpose(const acr_grid* grid, const double* coef, const double* x,
+                              double* y, int32_t nrhs, cudaStream_t stream);
+
+/* Adjoint kappa-gradient of the Sec. 6 operator (Eq. poissonEquation, as
+ * assembled by acr_stencil_poisson; no counterpart in the paper):
+ * grad[p] = -lambda^T (dA/dkappa_p) u, N doubles each (device).  With
+ * A u = f and A^T lambda = dL/du this is dL/dkappa.  Errors: INVALID_ARG,
+ * CUDA. */
+acr_status acr_kappa_gradient(const acr_grid* grid, const double* kappa, const double* lambda,
+                              const double* u, double* grad, cudaStream_t stream);
+
 /* Same Krylov iteration with no preconditioner (h not needed): the
  * reference for iteration counts. */
 acr_status acr_krylov_solve_plain(const acr_grid* grid, const double* coef, int32_t method,

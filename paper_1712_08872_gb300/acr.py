@@ -92,6 +92,10 @@ def load_library(path=LIB_PATH):
                              ctypes.POINTER(SolveInfo), _P],
         "acr_krylov_solve_plain": [ctypes.POINTER(Grid), _P, I32, I32, F64, I32, _P, _P,
                                    ctypes.POINTER(SolveInfo), _P],
+        "acr_krylov_solve_transpose": [_P, _P, I32, I32, F64, I32, _P, _P, I32,
+                                       ctypes.POINTER(SolveInfo), _P],
+        "acr_spmv_transpose": [ctypes.POINTER(Grid), _P, _P, _P, I32, _P],
+        "acr_kappa_gradient": [ctypes.POINTER(Grid), _P, _P, _P, _P, _P],
         "acr_krylov_solve_plain_noalloc": [ctypes.POINTER(Grid), _P, F64, I32, _P, _P,
                                            ctypes.POINTER(SolveInfo), _P],
         "acr_get_setup_info": [_P, ctypes.POINTER(SetupInfo)],
@@ -161,6 +165,21 @@ def acr_spmv(n, coef, x, y, nrhs=1, stream=None):
                                     _stream(stream)), "acr_spmv")
 
 
+def acr_spmv_transpose(n, coef, x, y, nrhs=1, stream=None):
+    N = n ** 3
+    _check(load_library().acr_spmv_transpose(ctypes.byref(_grid(n)), _dev(coef, 7 * N, "coef"),
+                                              _dev(x, nrhs * N, "x"), _dev(y, nrhs * N, "y"),
+                                              nrhs, _stream(stream)), "acr_spmv_transpose")
+
+
+def acr_kappa_gradient(n, kappa, lam, u, grad, stream=None):
+    N = n ** 3
+    _check(load_library().acr_kappa_gradient(ctypes.byref(_grid(n)), _dev(kappa, N, "kappa"),
+                                              _dev(lam, N, "lambda"), _dev(u, N, "u"),
+                                              _dev(grad, N, "grad"), _stream(stream)),
+           "acr_kappa_gradient")
+
+
 def acr_setup(n, coef, eps, eta, leaf, precision=ACR_FP64, rank_cap=0, stream=None, flags=0):
     """Returns an opaque handle (int); release it with acr_destroy."""
     N = n ** 3
@@ -190,6 +209,18 @@ def acr_krylov_solve(handle, coef, method, restart, rtol, maxit, f, u, stream=No
                                          ctypes.byref(info), _stream(stream))
     if check:
         _check(st, "acr_krylov_solve")
+    return info, st
+
+
+def acr_krylov_solve_transpose(handle, coef, method, restart, rtol, maxit, f, u, stream=None,
+                               check=True):
+    info = SolveInfo()
+    st = load_library().acr_krylov_solve_transpose(_P(handle), _dev(coef, None, "coef"), method,
+                                                   restart, rtol, maxit, _dev(f, None, "f"),
+                                                   _dev(u, None, "u"), 1, ctypes.byref(info),
+                                                   _stream(stream))
+    if check:
+        _check(st, "acr_krylov_solve_transpose")
     return info, st
 
 

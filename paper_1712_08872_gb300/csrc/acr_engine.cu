@@ -1083,6 +1083,7 @@ struct Krylov {
   int n;
   const double* coef;
   EngineBase* E;
+  bool trans = false;        // solve A^T u = f with the transposed preconditioner
   double* partial = nullptr;
   double* dres = nullptr;
   double* dcoef = nullptr;
@@ -1104,9 +1105,12 @@ struct Krylov {
     dcoef = dbuf(64);
     ACR_CUDA(cudaMallocHost(&hpin, 128 * sizeof(double)));
   }
-  void A(const double* x, double* y) { launch_spmv(coef, x, y, n, st); }
+  void A(const double* x, double* y) {
+    if (trans) launch_spmv_transpose(coef, x, y, n, st);
+    else launch_spmv(coef, x, y, n, st);
+  }
   void M(const double* x, double* y) {
-    if (E) E->apply(x, y, false, st);
+    if (E) E->apply(x, y, trans, st);
     else ACR_CUDA(cudaMemcpyAsync(y, x, N * sizeof(double), cudaMemcpyDeviceToDevice, st));
   }
   // queue <V_j, w> for j < nv into dres[off..], no sync
@@ -1415,7 +1419,7 @@ acr_status acr_apply_transpose(acr_handle* h, const double* r, double* z, int32_
 static acr_status krylov_common(acr::EngineBase* E, const acr_grid* grid, const double* coef,
                                 int32_t method, int32_t restart, double rtol, int32_t maxit,
                                 const double* f, double* u, acr_solve_info* info,
-                                cudaStream_t stream) {
+                                cudaStream_t stream, bool trans = false) {
   if (!grid_ok(grid) || !coef || !f || !u || !(rtol > 0.0) || maxit < 1 ||
       (method != ACR_PCG && method != ACR_GMRES))
     return ACR_ERR_INVALID_ARG;
@@ -1426,6 +1430,7 @@ static acr_status krylov_common(acr::EngineBase* E, const acr_grid* grid, const 
     K.N = (int64_t)grid->nx * grid->nx * grid->nx;
     K.coef = coef;
     K.E = E;
+    K.trans = trans;
     K.init();
     cudaEvent_t e0, e1;
     ACR_CUDA(cudaEventCreate(&e0));
@@ -1449,6 +1454,35 @@ acr_status acr_krylov_solve(acr_handle* h, const double* coef, int32_t method, i
                             int32_t nrhs, acr_solve_info* info, cudaStream_t stream) {
   if (!h || !h->e || nrhs != 1) return ACR_ERR_INVALID_ARG;
   return krylov_common(h->e, &h->grid, coef, method, restart, rtol, maxit, f, u, info, stream);
+}
+
+acr_status acr_krylov_solve_transpose(acr_handle* h, const double* coef, int32_t method,
+                                      int32_t restart, double rtol, int32_t maxit,
+                                      const double* f, double* u, int32_t nrhs,
+                                      acr_solve_info* info, cudaStream_t stream) {
+  if (!h || !h->e || nrhs != 1) return ACR_ERR_INVALID_ARG;
+  return krylov_common(h->e, &h->grid, coef, method, restart, rtol, maxit, f, u, info, stream,
+                       true);
+}
+
+acr_status acr_spmv_transpose(const acr_grid* grid, const double* coef, const double* x,
+                              double* y, int32_t nrhs, cudaStream_t stream) {
+  if (!grid_ok(grid) || !coef || !x || !y || nrhs < 1) return ACR_ERR_INVALID_ARG;
+  return guarded([&] {
+    const int64_t N = (int64_t)grid->nx * grid->nx * grid->nx;
+    for (int k = 0; k < nrhs; ++k)
+      acr::launch_spmv_transpose(coef, x + k * N, y + k * N, grid->nx, stream);
+    return 0;
+  });
+}
+
+acr_status acr_kappa_gradient(const acr_grid* grid, const double* kappa, const double* lambda,
+                              const double* u, double* grad, cudaStream_t stream) {
+  if (!grid_ok(grid) || !kappa || !lambda || !u || !grad) return ACR_ERR_INVALID_ARG;
+  return guarded([&] {
+    acr::launch_kappa_grad(kappa, lambda, u, grad, grid->nx, stream);
+    return 0;
+  });
 }
 
 acr_status acr_krylov_solve_plain(const acr_grid* grid, const double* coef, int32_t method,

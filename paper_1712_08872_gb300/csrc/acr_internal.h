@@ -129,6 +129,11 @@ void launch_copy_planes(double* const* dst, const double* const* src, int n2, in
 void launch_stencil_poisson(const double* kappa, double* coef, int n, cudaStream_t st);
 void launch_stencil_codi(const double* beta, double* coef, int n, cudaStream_t st);
 void launch_spmv(const double* coef, const double* x, double* y, int n, cudaStream_t st);
+void launch_spmv_transpose(const double* coef, const double* x, double* y, int n,
+                           cudaStream_t st);
+// grad = -lambda^T (dA/dkappa) u for the harmonic-mean Poisson stencil
+void launch_kappa_grad(const double* kappa, const double* lam, const double* u, double* grad,
+                       int n, cudaStream_t st);
 // out[0..nv) = <V_j, w>, V_j = V + j*ldv; deterministic two-stage reduction
 void launch_multidot(const double* V, int64_t ldv, int nv, const double* w, int64_t N,
                      double* partial, double* out, cudaStream_t st);

@@ -1,5 +1,6 @@
 // 7-point assembly (Sec. 6 Eq. poissonEquation, Sec. 7 Eq. codi), the FP64
-// 7-point SpMV and the FP64 vector kernels of the Krylov drivers
+// 7-point SpMV and its transpose, the adjoint kappa-gradient of the Poisson
+// stencil, and the FP64 vector kernels of the Krylov drivers
 // (Sec. 5.3 CG, Sec. 7 GMRES).  Reductions are two-stage with a fixed
 // order, so results are bitwise reproducible run to run.
 #include <cuda_runtime.h>
@@ -79,6 +80,57 @@ __global__ void k_spmv(const double* __restrict__ coef, const double* __restrict
   }
 }
 
+// y = A^T x: row p of A^T holds the coefficients that point at p from its
+// neighbours (the east coefficient of p-1, the west one of p+1, ...)
+__global__ void k_spmv_transpose(const double* __restrict__ coef, const double* __restrict__ x,
+                                 double* __restrict__ y, int n) {
+  const int64_t N = (int64_t)n * n * n;
+  const int64_t n2 = (int64_t)n * n;
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < N;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    const int ix = (int)(p % n), iy = (int)((p / n) % n), iz = (int)(p / n2);
+    double s = coef[p] * x[p];
+    if (ix > 0) s += coef[2 * N + p - 1] * x[p - 1];
+    if (ix < n - 1) s += coef[N + p + 1] * x[p + 1];
+    if (iy > 0) s += coef[4 * N + p - n] * x[p - n];
+    if (iy < n - 1) s += coef[3 * N + p + n] * x[p + n];
+    if (iz > 0) s += coef[6 * N + p - n2] * x[p - n2];
+    if (iz < n - 1) s += coef[5 * N + p + n2] * x[p + n2];
+    y[p] = s;
+  }
+}
+
+// grad_p = -lambda^T (dA/dkappa_p) u for the harmonic-mean Poisson stencil:
+// each of the six faces of p contributes dk/dkappa_p times
+// (lambda_p - lambda_q)(u_p - u_q) (interior face, k the harmonic mean of
+// kappa_p and kappa_q, dk/dkappa_p = 2 kappa_q^2 / (kappa_p + kappa_q)^2) or
+// lambda_p u_p (boundary face, k = kappa_p); all over h^2.
+__global__ void k_kappa_grad(const double* __restrict__ kap, const double* __restrict__ lam,
+                             const double* __restrict__ u, double* __restrict__ grad, int n) {
+  const int64_t N = (int64_t)n * n * n;
+  const int64_t n2 = (int64_t)n * n;
+  const double h = 1.0 / (n + 1), ih2 = 1.0 / (h * h);
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < N;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    const int ix = (int)(p % n), iy = (int)((p / n) % n), iz = (int)(p / n2);
+    const double kp = kap[p], lp = lam[p], up = u[p];
+    const int64_t nb[6] = {p - 1, p + 1, p - n, p + n, p - n2, p + n2};
+    const bool in[6] = {ix > 0, ix < n - 1, iy > 0, iy < n - 1, iz > 0, iz < n - 1};
+    double g = 0.0;
+#pragma unroll
+    for (int d = 0; d < 6; ++d) {
+      if (in[d]) {
+        const int64_t q = nb[d];
+        const double kq = kap[q], sk = kp + kq;
+        g += 2.0 * kq * kq / (sk * sk) * (lp - lam[q]) * (up - u[q]);
+      } else {
+        g += lp * up;
+      }
+    }
+    grad[p] = -g * ih2;
+  }
+}
+
 __global__ void k_multidot_partial(const double* __restrict__ V, int64_t ldv,
                                    const double* __restrict__ w, int64_t N,
                                    double* __restrict__ partial) {
@@ -155,6 +207,18 @@ void launch_stencil_codi(const double* beta, double* coef, int n, cudaStream_t s
 
 void launch_spmv(const double* coef, const double* x, double* y, int n, cudaStream_t st) {
   k_spmv<<<grid_for((int64_t)n * n * n), 256, 0, st>>>(coef, x, y, n);
+  ACR_LAUNCHED(1);
+}
+
+void launch_spmv_transpose(const double* coef, const double* x, double* y, int n,
+                           cudaStream_t st) {
+  k_spmv_transpose<<<grid_for((int64_t)n * n * n), 256, 0, st>>>(coef, x, y, n);
+  ACR_LAUNCHED(1);
+}
+
+void launch_kappa_grad(const double* kappa, const double* lam, const double* u, double* grad,
+                       int n, cudaStream_t st) {
+  k_kappa_grad<<<grid_for((int64_t)n * n * n), 256, 0, st>>>(kappa, lam, u, grad, n);
   ACR_LAUNCHED(1);
 }
 
