@@ -155,6 +155,13 @@ acr_status acr_stencil_poisson(const acr_grid* grid, const double* kappa, double
 acr_status acr_stencil_codi(const acr_grid* grid, const double* beta, double* coef,
                             cudaStream_t stream);
 
+/* a1 for Sec. 8, Eq. (HelmVarVel): stencil of -Lap u - sigma u with the
+ * 7-point Laplacian (the paper discretises with 27-point trilinear
+ * elements); sigma: N doubles, (omega / c)^2 per node.  The operator is
+ * indefinite once sigma exceeds the smallest Laplacian eigenvalue. */
+acr_status acr_stencil_helmholtz(const acr_grid* grid, const double* sigma, double* coef,
+                                 cudaStream_t stream);
+
 /* y = A x for the 7-point operator (FP64), x and y N doubles each, nrhs
  * vectors back to back. */
 acr_status acr_spmv(const acr_grid* grid, const double* coef, const double* x, double* y,

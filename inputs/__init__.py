@@ -12,5 +12,5 @@ on the unit cube, spacing ``h = 1/(n+1)``, node ``(ix, iy, iz)`` at
 """
 from .fields import (  # noqa: F401
     grid_coords, gaussian_field_kappa, box_inclusions_kappa, codi_beta,
-    uniform_rhs, workload, WORKLOADS, fd_cells,
+    uniform_rhs, workload, WORKLOADS, fd_cells, layered_speed, helmholtz_omega,
 )

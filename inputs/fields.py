@@ -66,6 +66,23 @@ def box_inclusions_kappa(n, seed, nbox=40, high=1.0e4, side=(0.05, 0.25)):
     return kap
 
 
+def layered_speed(n, seed, layers=8, c_range=(1.0, 3.0)):
+    """Piecewise-constant wave speed c(x) in ``layers`` slabs normal to x:
+    the layers - 1 interfaces are sorted U(0, 1) positions, each slab's c is
+    U[c_range].  Evaluated at the grid nodes, shape (n**3,)."""
+    rng = np.random.default_rng(seed)
+    cuts = np.sort(rng.uniform(0.0, 1.0, size=layers - 1))
+    speeds = rng.uniform(c_range[0], c_range[1], size=layers)
+    x, _, _ = grid_coords(n)
+    return speeds[np.searchsorted(cuts, x)]
+
+
+def helmholtz_omega(n, points_per_wavelength=10.0):
+    """Angular frequency giving ``points_per_wavelength`` grid spacings per
+    wavelength at c = 1: 2 pi / (ppw h), h = 1/(n+1)."""
+    return 2.0 * np.pi * (n + 1) / points_per_wavelength
+
+
 def codi_beta(n, magnitude=50.0):
     """Convection velocity beta = magnitude*(1,1,1)*(1 + 0.5 sin(2 pi x) sin(2 pi y))
     at the grid nodes, shape (3, n**3)."""
@@ -98,6 +115,9 @@ WORKLOADS = {
     "codi_n128": dict(pde="codi", n=128, field="codi", field_seed=None,
                       rhs_seed=20, eps=1e-2, eta=2.0, leaf=64,
                       krylov="gmres", rtol=1e-8, restart=30),
+    "helmholtz_n64": dict(pde="helmholtz", n=64, field="layers", field_seed=30,
+                          rhs_seed=31, nrhs=32, eps=1e-5, eta=2.0, leaf=64,
+                          krylov="gmres", rtol=1e-8, restart=30),
     "poisson_grad_n96": dict(pde="poisson", n=96, field="grf", field_seed=0,
                              rhs_seed=1, obs_seed=100, fd_seed=101, fd_cells=20,
                              eps=1e-2, eta=2.0, leaf=64, krylov="pcg", rtol=1e-10),
@@ -114,8 +134,9 @@ def workload(name, n=None):
     """Return (spec, coefficient array, rhs) for a named workload.
 
     ``n`` overrides the grid size (same recipe, same seeds) for scaled-down
-    parity cases.  The coefficient array is kappa (n**3,) for Poisson and
-    beta (3, n**3) for convection-diffusion.
+    parity cases.  The coefficient array is kappa (n**3,) for Poisson, beta
+    (3, n**3) for convection-diffusion and the shift sigma = (omega/c)^2
+    (n**3,) for Helmholtz; f is (nrhs, n**3) for multi-RHS workloads.
     """
     spec = dict(WORKLOADS[name])
     if n is not None:
@@ -123,9 +144,16 @@ def workload(name, n=None):
     nn = spec["n"]
     if spec["field"] == "grf":
         coef = gaussian_field_kappa(nn, spec["field_seed"])
+    elif spec["field"] == "layers":
+        # the shift sigma = (omega / c)^2 of -Lap u - sigma u
+        coef = (helmholtz_omega(nn) / layered_speed(nn, spec["field_seed"])) ** 2
     elif spec["field"] == "boxes":
         coef = box_inclusions_kappa(nn, spec["field_seed"])
     else:
         coef = codi_beta(nn)
-    f = uniform_rhs(nn, spec["rhs_seed"])
+    if spec.get("nrhs", 1) > 1:
+        # seeds rhs_seed, rhs_seed + 1, ... one per right-hand side
+        f = np.stack([uniform_rhs(nn, spec["rhs_seed"] + k) for k in range(spec["nrhs"])])
+    else:
+        f = uniform_rhs(nn, spec["rhs_seed"])
     return spec, coef, f

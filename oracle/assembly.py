@@ -71,6 +71,20 @@ def stencil_codi(beta, n):
     return {k: v.ravel() for k, v in st.items()}
 
 
+def stencil_helmholtz(sigma, n):
+    """Stencil of -Lap u - sigma u, sigma = (omega/c(x))^2 per node (Sec. 8,
+    Eq. HelmVarVel), with the second-order 7-point Laplacian in place of the
+    paper's 27-point trilinear elements; Dirichlet 0.  Indefinite once sigma
+    exceeds the smallest Laplacian eigenvalue."""
+    h = 1.0 / (n + 1)
+    sig = np.asarray(sigma, dtype=np.float64).ravel()
+    st = {"c": np.full(n ** 3, 6.0 / (h * h)) - sig}
+    for name, (axis, d) in zip(NAMES[1:], _DIRS):
+        inside = ~np.isnan(_shift(np.zeros((n, n, n)), axis, d))
+        st[name] = np.where(inside, -1.0 / (h * h), 0.0).ravel()
+    return st
+
+
 def stencil_matrix(st, n):
     """Sparse CSR matrix of a stencil (natural ordering, x fastest)."""
     N = n ** 3

@@ -83,6 +83,7 @@ def load_library(path=LIB_PATH):
     sig = {
         "acr_stencil_poisson": [ctypes.POINTER(Grid), _P, _P, _P],
         "acr_stencil_codi": [ctypes.POINTER(Grid), _P, _P, _P],
+        "acr_stencil_helmholtz": [ctypes.POINTER(Grid), _P, _P, _P],
         "acr_spmv": [ctypes.POINTER(Grid), _P, _P, _P, I32, _P],
         "acr_setup": [ctypes.POINTER(Grid), _P, ctypes.POINTER(Options), _P,
                       ctypes.POINTER(_P)],
@@ -156,6 +157,13 @@ def acr_stencil_codi(n, beta, coef, stream=None):
     _check(load_library().acr_stencil_codi(ctypes.byref(_grid(n)), _dev(beta, 3 * N, "beta"),
                                             _dev(coef, 7 * N, "coef"), _stream(stream)),
            "acr_stencil_codi")
+
+
+def acr_stencil_helmholtz(n, sigma, coef, stream=None):
+    N = n ** 3
+    _check(load_library().acr_stencil_helmholtz(ctypes.byref(_grid(n)), _dev(sigma, N, "sigma"),
+                                                 _dev(coef, 7 * N, "coef"), _stream(stream)),
+           "acr_stencil_helmholtz")
 
 
 def acr_spmv(n, coef, x, y, nrhs=1, stream=None):

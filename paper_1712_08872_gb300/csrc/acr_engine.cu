@@ -1355,6 +1355,15 @@ acr_status acr_stencil_codi(const acr_grid* grid, const double* beta, double* co
   });
 }
 
+acr_status acr_stencil_helmholtz(const acr_grid* grid, const double* sigma, double* coef,
+                            cudaStream_t stream) {
+  if (!grid_ok(grid) || !sigma || !coef) return ACR_ERR_INVALID_ARG;
+  return guarded([&] {
+    acr::launch_stencil_helmholtz(sigma, coef, grid->nx, stream);
+    return 0;
+  });
+}
+
 acr_status acr_spmv(const acr_grid* grid, const double* coef, const double* x, double* y,
                     int32_t nrhs, cudaStream_t stream) {
   if (!grid_ok(grid) || !coef || !x || !y || nrhs < 1) return ACR_ERR_INVALID_ARG;

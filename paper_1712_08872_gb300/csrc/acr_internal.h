@@ -128,6 +128,7 @@ void launch_copy_planes(double* const* dst, const double* const* src, int n2, in
 // ------------------------------------------------------------ Krylov
 void launch_stencil_poisson(const double* kappa, double* coef, int n, cudaStream_t st);
 void launch_stencil_codi(const double* beta, double* coef, int n, cudaStream_t st);
+void launch_stencil_helmholtz(const double* sigma, double* coef, int n, cudaStream_t st);
 void launch_spmv(const double* coef, const double* x, double* y, int n, cudaStream_t st);
 void launch_spmv_transpose(const double* coef, const double* x, double* y, int n,
                            cudaStream_t st);

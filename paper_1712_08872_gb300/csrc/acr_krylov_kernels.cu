@@ -62,6 +62,22 @@ __global__ void k_stencil_codi(const double* __restrict__ beta, double* __restri
   }
 }
 
+// Sec. 8 Eq. (HelmVarVel) with the 7-point Laplacian: -Lap u - sigma u,
+// sigma = (omega / c)^2 per node
+__global__ void k_stencil_helmholtz(const double* __restrict__ sigma, double* __restrict__ coef,
+                                    int n) {
+  const int64_t N = (int64_t)n * n * n;
+  const double h = 1.0 / (n + 1), ih2 = 1.0 / (h * h);
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < N;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    const int ix = (int)(p % n), iy = (int)((p / n) % n), iz = (int)(p / ((int64_t)n * n));
+    const bool in[6] = {ix > 0, ix < n - 1, iy > 0, iy < n - 1, iz > 0, iz < n - 1};
+#pragma unroll
+    for (int d = 0; d < 6; ++d) coef[(d + 1) * N + p] = in[d] ? -ih2 : 0.0;
+    coef[p] = 6.0 * ih2 - sigma[p];
+  }
+}
+
 __global__ void k_spmv(const double* __restrict__ coef, const double* __restrict__ x,
                        double* __restrict__ y, int n) {
   const int64_t N = (int64_t)n * n * n;
@@ -202,6 +218,11 @@ void launch_stencil_poisson(const double* kappa, double* coef, int n, cudaStream
 
 void launch_stencil_codi(const double* beta, double* coef, int n, cudaStream_t st) {
   k_stencil_codi<<<grid_for((int64_t)n * n * n), 256, 0, st>>>(beta, coef, n);
+  ACR_LAUNCHED(1);
+}
+
+void launch_stencil_helmholtz(const double* sigma, double* coef, int n, cudaStream_t st) {
+  k_stencil_helmholtz<<<grid_for((int64_t)n * n * n), 256, 0, st>>>(sigma, coef, n);
   ACR_LAUNCHED(1);
 }
 

@@ -1,11 +1,12 @@
 """Pins for the oracle's 7-point assembly (Sec. 6 Eq. poissonEquation,
-Sec. 7 Eq. codi)."""
+Sec. 7 Eq. codi, Sec. 8 Eq. HelmVarVel)."""
 import numpy as np
 import pytest
 import scipy.sparse as sp
 
-from inputs import gaussian_field_kappa, codi_beta, grid_coords
-from oracle.assembly import (stencil_poisson, stencil_codi, stencil_matrix,
+from inputs import (gaussian_field_kappa, codi_beta, grid_coords, layered_speed,
+                    helmholtz_omega)
+from oracle.assembly import (stencil_poisson, stencil_codi, stencil_helmholtz, stencil_matrix,
                              stencil_apply, plane_blocks)
 
 
@@ -123,3 +124,42 @@ def test_plane_blocks_reassemble():
         if k < n - 1:
             B[k * n2:(k + 1) * n2, (k + 1) * n2:(k + 2) * n2] = np.diag(Ud[k])
     assert np.array_equal(A, B)
+
+
+@pytest.mark.parametrize("abc", [(1, 1, 1), (3, 2, 1)])
+def test_helmholtz_closed_form_eigenpairs(abc):
+    """Constant shift: the Laplacian's sine eigenvectors with eigenvalue
+    lambda_abc - sigma (a negative one for the low modes at 10 points per
+    wavelength: the operator is indefinite)."""
+    n = 9
+    h = 1.0 / (n + 1)
+    x, y, z = grid_coords(n)
+    a, b, c = abc
+    v = np.sin(a * np.pi * x) * np.sin(b * np.pi * y) * np.sin(c * np.pi * z)
+    lam = 4 / h ** 2 * (np.sin(a * np.pi * h / 2) ** 2 + np.sin(b * np.pi * h / 2) ** 2
+                        + np.sin(c * np.pi * h / 2) ** 2)
+    sigma = helmholtz_omega(n) ** 2
+    st = stencil_helmholtz(np.full(n ** 3, sigma), n)
+    Av = stencil_apply(st, n, v)
+    assert np.linalg.norm(Av - (lam - sigma) * v) <= 1e-12 * lam * np.linalg.norm(v)
+    if abc == (1, 1, 1):
+        assert lam - sigma < 0
+
+
+def test_helmholtz_shift_enters_the_diagonal_only():
+    n = 6
+    sig = (helmholtz_omega(n) / layered_speed(n, 30)) ** 2
+    A = stencil_matrix(stencil_helmholtz(sig, n), n)
+    L = stencil_matrix(stencil_poisson(np.ones(n ** 3), n), n)
+    assert abs(A - L + sp.diags(sig)).max() <= 1e-12 * abs(L).max()
+
+
+def test_layered_speed_has_eight_slabs_in_range():
+    n = 40
+    c = layered_speed(n, 30)
+    x, _, _ = grid_coords(n)
+    assert c.min() >= 1.0 and c.max() <= 3.0
+    # constant across y and z, piecewise constant in x with at most 8 values
+    c3 = c.reshape(n, n, n)
+    assert np.all(c3 == c3[:1, :1, :])
+    assert len(np.unique(c)) <= 8 and len(np.unique(c)) >= 2

@@ -4,8 +4,8 @@ import pytest
 import scipy.fft
 import scipy.sparse.linalg as sla
 
-from inputs import gaussian_field_kappa, codi_beta, uniform_rhs
-from oracle.assembly import (stencil_poisson, stencil_codi, stencil_matrix,
+from inputs import gaussian_field_kappa, codi_beta, uniform_rhs, layered_speed, helmholtz_omega
+from oracle.assembly import (stencil_poisson, stencil_codi, stencil_helmholtz, stencil_matrix,
                              plane_blocks)
 from oracle.cr import cr_setup, cr_apply, levels
 from oracle.hstructure import Structure
@@ -14,13 +14,15 @@ from oracle.hstructure import Structure
 def _problem(kind, n, seed=0):
     if kind == "poisson":
         st = stencil_poisson(gaussian_field_kappa(n, seed), n)
+    elif kind == "helmholtz":
+        st = stencil_helmholtz((helmholtz_omega(n) / layered_speed(n, 30)) ** 2, n)
     else:
         st = stencil_codi(codi_beta(n), n)
     return st, stencil_matrix(st, n)
 
 
 @pytest.mark.parametrize("n", [2, 3, 4, 5, 7, 8, 12, 16])
-@pytest.mark.parametrize("kind", ["poisson", "codi"])
+@pytest.mark.parametrize("kind", ["poisson", "codi", "helmholtz"])
 def test_dense_cr_equals_direct_solve(kind, n):
     st, A = _problem(kind, n)
     f = uniform_rhs(n, 1)
