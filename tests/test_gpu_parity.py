@@ -25,9 +25,10 @@ import numpy as np
 import pytest
 import scipy.sparse.linalg as sla
 
-from inputs import workload, codi_beta, uniform_rhs, gaussian_field_kappa
-from oracle.assembly import (stencil_poisson, stencil_codi, stencil_apply, stencil_matrix,
-                             plane_blocks, NAMES)
+from inputs import (workload, codi_beta, uniform_rhs, gaussian_field_kappa, layered_speed,
+                    helmholtz_omega)
+from oracle.assembly import (stencil_poisson, stencil_codi, stencil_helmholtz, stencil_apply,
+                             stencil_matrix, plane_blocks, NAMES)
 from oracle.cr import cr_setup, cr_apply
 from oracle.hstructure import Structure
 
@@ -58,6 +59,11 @@ def operator(acr, kind, n, seed=0):
         st = stencil_poisson(kap, n)
         coef = torch.empty(7 * n ** 3, dtype=torch.float64, device="cuda:0")
         acr.acr_stencil_poisson(n, T(kap), coef)
+    elif kind == "helmholtz":
+        sig = (helmholtz_omega(n) / layered_speed(n, 30)) ** 2
+        st = stencil_helmholtz(sig, n)
+        coef = torch.empty(7 * n ** 3, dtype=torch.float64, device="cuda:0")
+        acr.acr_stencil_helmholtz(n, T(sig), coef)
     else:
         beta = codi_beta(n)
         st = stencil_codi(beta, n)
@@ -66,7 +72,8 @@ def operator(acr, kind, n, seed=0):
     return st, coef
 
 
-@pytest.mark.parametrize("kind,n", [("poisson", 7), ("poisson", 16), ("codi", 9), ("codi", 32)])
+@pytest.mark.parametrize("kind,n", [("poisson", 7), ("poisson", 16), ("codi", 9), ("codi", 32),
+                                    ("helmholtz", 9), ("helmholtz", 32)])
 def test_assembly_and_spmv(acr, kind, n):
     st, coef = operator(acr, kind, n)
     ref = np.concatenate([st[k] for k in NAMES])
@@ -165,10 +172,12 @@ def apply_tol(prec, eps, n, F=None, r=None, z=None):
 APPLY_CASES = [("poisson", 8, 1.0, 16, 1e-10), ("codi", 8, 2.0, 8, 1e-3),
                ("poisson", 16, 1.0, 32, 1e-6), ("codi", 16, 2.0, 32, 1e-2),
                ("poisson", 16, 2.0, 16, 1e-2)]
+# indefinite Helmholtz (10 points per wavelength, 8-layer medium), FP64
+APPLY_CASES_HELM = [("helmholtz", 8, 2.0, 16, 1e-5), ("helmholtz", 16, 2.0, 32, 1e-5)]
 # eta = 16 puts plane couplings inside admissible blocks (exact ranks up to
 # the interface length) and deepens the H-arithmetic; FP64 parity holds,
 # the FP32 form is checked by its FP64 Krylov outcome below.
-APPLY_CASES_FP64 = APPLY_CASES + [("codi", 16, 16.0, 32, 1e-2)]
+APPLY_CASES_FP64 = APPLY_CASES + [("codi", 16, 16.0, 32, 1e-2)] + APPLY_CASES_HELM
 
 
 # the BF16 form is meant for coarse preconditioners (eps >= 1e-3)
@@ -299,6 +308,35 @@ def _direct_and_cond(name, n):
     st = stencil_codi(cin, n) if spec["pde"] == "codi" else stencil_poisson(cin, n)
     A = stencil_matrix(st, n)
     return sla.splu(A.tocsc()).solve(f), cond_estimate(A, its=25)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_helmholtz_recipe_small_grid(acr, prec):
+    """The indefinite Helmholtz recipe at n = 32 (eps 1e-5, GMRES(30) to
+    1e-8), first right-hand side: the oracle's SpMV confirms the residual and
+    the solution is within 10 cond rtol of the direct solve; unpreconditioned
+    GMRES(30) does not converge on it."""
+    n = 32
+    spec, sig, F = workload("helmholtz_n64", n=n)
+    f = F[0]
+    st = stencil_helmholtz(sig, n)
+    coef = torch.empty(7 * n ** 3, dtype=torch.float64, device="cuda:0")
+    acr.acr_stencil_helmholtz(n, T(sig), coef)
+    h = acr.Handle(n, coef, spec["eps"], spec["eta"], 32, prec, 48)
+    u = torch.zeros(n ** 3, dtype=torch.float64, device="cuda:0")
+    info, status = acr.acr_krylov_solve(h.h, coef, acr.ACR_GMRES, 30, spec["rtol"], 300, T(f), u)
+    torch.cuda.synchronize()
+    h.close()
+    A = stencil_matrix(st, n)
+    uh = u.cpu().numpy()
+    assert rel(A @ uh, f) <= spec["rtol"] * 1.0001
+    assert info.iterations <= (5 if prec == 0 else 12)
+    ue = sla.splu(A.tocsc()).solve(f)
+    assert rel(uh, ue) <= 10 * cond_estimate(A, its=25) * spec["rtol"]
+    u0 = torch.zeros(n ** 3, dtype=torch.float64, device="cuda:0")
+    info0, st0 = acr.acr_krylov_solve_plain(n, coef, acr.ACR_GMRES, 30, spec["rtol"], 300,
+                                            T(f), u0, check=False)
+    assert st0 != 0
 
 
 def test_full_size_codi_n128_fp32(acr):
