@@ -249,6 +249,8 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--bf16-steps", type=int, default=1)
+    ap.add_argument("--no-batch", action="store_true",
+                    help="skip the multi-right-hand-side measurements")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--rank-cap", type=int, default=24)
     ap.add_argument("--profile-setup", action="store_true",
@@ -428,6 +430,67 @@ def main():
     if args.bf16_steps > 0:
         apply_roof["bf16"] = apply_roofline(acr.ACR_BF16)
 
+    # batching: the multi-RHS apply at the benchmark size (factors streamed
+    # once per group of 8 right-hand sides), and the indefinite Helmholtz
+    # recipe's 32 right-hand sides solved in lockstep vs one at a time
+    batch = None
+    if not args.no_batch:
+        h = acr.acr_setup(n, coef, eps, eta, leaf, acr.ACR_FP32, args.rank_cap, stream)
+        nr = 8
+        Rm = f_d.repeat(nr)
+        Zm = torch.empty_like(Rm)
+        for _ in range(2):
+            acr.acr_apply(h, Rm, Zm, nr, stream)
+        torch.cuda.synchronize()
+        ea = torch.cuda.Event(enable_timing=True)
+        eb = torch.cuda.Event(enable_timing=True)
+        ea.record(stream)
+        for _ in range(5):
+            acr.acr_apply(h, Rm, Zm, nr, stream)
+        eb.record(stream)
+        torch.cuda.synchronize()
+        multi_ms = ea.elapsed_time(eb) / 5
+        acr.acr_destroy(h)
+        hs, sig, Fh = workload("helmholtz_n64")
+        nh, nrh = hs["n"], Fh.shape[0]
+        Nh = nh ** 3
+        ch = torch.empty(7 * Nh, dtype=torch.float64, device=dev)
+        acr.acr_stencil_helmholtz(nh, torch.tensor(sig, dtype=torch.float64, device=dev), ch)
+        Fd = torch.tensor(Fh.ravel(), dtype=torch.float64, device=dev)
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e2 = torch.cuda.Event(enable_timing=True)
+        e3 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        hh = acr.acr_setup(nh, ch, hs["eps"], hs["eta"], hs["leaf"], acr.ACR_FP32, 48, stream)
+        e1.record(stream)
+        Ub = torch.zeros(nrh * Nh, dtype=torch.float64, device=dev)
+        ib, sb = acr.acr_krylov_solve(hh, ch, acr.ACR_GMRES, hs["restart"], hs["rtol"], 500, Fd,
+                                      Ub, stream, check=False, nrhs=nrh)
+        e2.record(stream)
+        Us = torch.zeros(nrh * Nh, dtype=torch.float64, device=dev)
+        its_seq = 0
+        for k in range(nrh):
+            ik, _ = acr.acr_krylov_solve(hh, ch, acr.ACR_GMRES, hs["restart"], hs["rtol"], 500,
+                                         Fd[k * Nh:(k + 1) * Nh], Us[k * Nh:(k + 1) * Nh],
+                                         stream, check=False)
+            its_seq = max(its_seq, ik.iterations)
+        e3.record(stream)
+        torch.cuda.synchronize()
+        acr.acr_destroy(hh)
+        batch = {"apply_n128_8rhs_ms": multi_ms, "apply_n128_ms_per_rhs": multi_ms / nr,
+                 "apply_n128_single_ms": apply_roof["ms"],
+                 "helmholtz": {"workload": "helmholtz_n64 (8-layer medium, 10 points per "
+                                           "wavelength, eps 1e-5, FP32 factors)",
+                               "nrhs": nrh, "setup_s": e0.elapsed_time(e1) / 1000.0,
+                               "lockstep_solve_s": e1.elapsed_time(e2) / 1000.0,
+                               "lockstep_iterations": ib.iterations,
+                               "lockstep_converged": bool(ib.converged),
+                               "max_rel_residual": ib.rel_residual,
+                               "one_at_a_time_solve_s": e2.elapsed_time(e3) / 1000.0,
+                               "one_at_a_time_max_iterations": its_seq}}
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         dt, it = oracle_sample()
@@ -449,7 +512,8 @@ def main():
             "fp64_plain": fp64, "bf16_factors": bf16,
             "speedup_vs_fp64": (fp64["s"] / (ms / 1000.0)) if fp64 else None,
             "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks,
-            "roofline": roof, "apply_roofline": apply_roof, "cpu_baseline": cpu}
+            "roofline": roof, "apply_roofline": apply_roof, "batching": batch,
+            "cpu_baseline": cpu}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:

@@ -181,7 +181,9 @@ acr_status acr_setup(const acr_grid* grid, const double* coef, const acr_options
 /* a9-a10, Sec. 4.1 substitution: z = M^{-1} r, M the ACR factorisation;
  * forward then backward sweep of batched H-matrix-vector products.  r, z:
  * nrhs * N doubles (natural ordering); r is not modified; r == z is
- * allowed.  No host synchronisation. */
+ * allowed.  Right-hand sides are processed in groups of up to 8 that share
+ * one pass over the stored factors (H-matrix times matrix), so nrhs vectors
+ * cost far less than nrhs calls.  No host synchronisation. */
 acr_status acr_apply(acr_handle* h, const double* r, double* z, int32_t nrhs,
                      cudaStream_t stream);
 
@@ -195,9 +197,13 @@ acr_status acr_apply_transpose(acr_handle* h, const double* r, double* z, int32_
  * with right preconditioning.  coef: the 7-point operator (7*N doubles,
  * normally the one the handle was built from).  u holds x0 on entry and
  * the solution on exit.  info (host pointer, may be NULL) receives the
- * iteration count and final true residual.  nrhs must be 1 in this
- * version.  Errors: NOT_CONVERGED after maxit (u holds the last iterate),
- * BREAKDOWN. */
+ * iteration count and final true residual.  nrhs (1..64) systems with the
+ * same operator: f and u hold nrhs vectors N doubles apart; GMRES runs them
+ * in lockstep (each its own Krylov space; the preconditioner applies,
+ * SpMVs, dots and updates of all systems share launches), PCG one after
+ * another; info then reports the largest iteration count and residual and
+ * converged = all converged.  maxit counts lockstep iterations.  Errors:
+ * NOT_CONVERGED after maxit (u holds the last iterate), BREAKDOWN. */
 acr_status acr_krylov_solve(acr_handle* h, const double* coef, int32_t method, int32_t restart,
                             double rtol, int32_t maxit, const double* f, double* u,
                             int32_t nrhs, acr_solve_info* info, cudaStream_t stream);

@@ -210,11 +210,11 @@ def acr_apply_transpose(handle, r, z, nrhs=1, stream=None):
 
 
 def acr_krylov_solve(handle, coef, method, restart, rtol, maxit, f, u, stream=None,
-                     check=True):
+                     check=True, nrhs=1):
     info = SolveInfo()
     st = load_library().acr_krylov_solve(_P(handle), _dev(coef, None, "coef"), method, restart,
-                                         rtol, maxit, _dev(f, None, "f"), _dev(u, None, "u"), 1,
-                                         ctypes.byref(info), _stream(stream))
+                                         rtol, maxit, _dev(f, None, "f"), _dev(u, None, "u"),
+                                         nrhs, ctypes.byref(info), _stream(stream))
     if check:
         _check(st, "acr_krylov_solve")
     return info, st
@@ -308,11 +308,11 @@ class Handle:
         self.h = None
         self.h = acr_setup(n, coef, eps, eta, leaf, precision, rank_cap, stream, flags)
 
-    def apply(self, r, z, stream=None):
-        acr_apply(self.h, r, z, 1, stream)
+    def apply(self, r, z, stream=None, nrhs=1):
+        acr_apply(self.h, r, z, nrhs, stream)
 
-    def apply_transpose(self, r, z, stream=None):
-        acr_apply_transpose(self.h, r, z, 1, stream)
+    def apply_transpose(self, r, z, stream=None, nrhs=1):
+        acr_apply_transpose(self.h, r, z, nrhs, stream)
 
     def info(self):
         return acr_get_setup_info(self.h)

@@ -8,7 +8,9 @@
 //                sum of dense leaves of block row c times x
 //                + sum of U_l[rows of c] tv_l over low-rank leaves covering c)
 // Every stored dense entry and every U, V entry up to the block's rank is
-// read exactly once; the vectors are FP64.  FP64 factors accumulate in FP64;
+// read exactly once per group of R right-hand sides (R = 1, 2, 4 or 8: the
+// multi-RHS apply multiplies each loaded entry into all R vectors, which sit
+// vs doubles apart); the vectors are FP64.  FP64 factors accumulate in FP64;
 // FP32 and BF16 factors multiply in FP32 and add short FP32 partial sums (at
 // most 16 products) into FP64 accumulators, keeping the slow FP64 pipe off
 // the per-entry path.
@@ -40,14 +42,14 @@ constexpr int MAXQ = 256;   // most low-rank leaves covering one chunk
 // leaf's segments in order.  The x chunk and the leaves' descriptors are
 // staged in shared memory; groups of 8 lanes take (leaf, column) pairs, each
 // lane 8 of the chunk's rows.
-template <typename T>
+template <typename T, int R>
 __global__ void __launch_bounds__(256) k_lr_proj(MatvecDev mv, T* const* __restrict__ U,
                                                  T* const* __restrict__ V,
                                                  const int* const* __restrict__ rank,
                                                  const double* const* __restrict__ x, double* tv,
-                                                 bool trans) {
+                                                 bool trans, int64_t vs, int64_t tvs) {
   using Acc = AccT<T>;
-  __shared__ Acc xs[64];
+  __shared__ Acc xs[R][64];
   __shared__ int64_t s_off[MAXQ];
   __shared__ int s_ld[MAXQ], s_seg[MAXQ], s_cum[MAXQ + 1];
   const int c = blockIdx.x, p = blockIdx.y;
@@ -61,7 +63,10 @@ __global__ void __launch_bounds__(256) k_lr_proj(MatvecDev mv, T* const* __restr
   const int* sptr = trans ? mv.segt_ptr : mv.seg_ptr;
   const int nseg = trans ? mv.nsegt : mv.nseg;
   const int q0 = ptr[c], nq = min(ptr[c + 1] - q0, MAXQ);
-  if (threadIdx.x < lsz) xs[threadIdx.x] = (Acc)xp[(int64_t)c * lsz + threadIdx.x];
+  for (int e = threadIdx.x; e < R * lsz; e += 256) {
+    const int rr = R == 1 ? 0 : e / lsz, i = e - rr * lsz;
+    xs[rr][i] = (Acc)xp[rr * vs + (int64_t)c * lsz + i];
+  }
   for (int q = threadIdx.x; q < nq; q += 256) {
     const int l = lf[q0 + q];
     s_cum[q + 1] = rank[p][l];
@@ -81,7 +86,9 @@ __global__ void __launch_bounds__(256) k_lr_proj(MatvecDev mv, T* const* __restr
   const int total = s_cum[nq];
   for (int t0 = 0; t0 < total; t0 += 32) {
     const int t = t0 + grp;
-    double d = 0.0;
+    double d[R];
+#pragma unroll
+    for (int rr = 0; rr < R; ++rr) d[rr] = 0.0;
     int q = 0, j = 0;
     if (t < total) {
       int lo_q = 0, hi_q = nq;   // the q with s_cum[q] <= t < s_cum[q + 1]
@@ -92,19 +99,33 @@ __global__ void __launch_bounds__(256) k_lr_proj(MatvecDev mv, T* const* __restr
       q = lo_q;
       j = t - s_cum[q];
       const T* col = Fb + s_off[q] + (int64_t)j * s_ld[q];
-      Acc v = Acc(0);
+      Acc v[R];
+#pragma unroll
+      for (int rr = 0; rr < R; ++rr) v[rr] = Acc(0);
       if (lsz == 64) {
 #pragma unroll
-        for (int u = 0; u < 8; ++u) v += (Acc)ld(col[r + 8 * u]) * xs[r + 8 * u];
+        for (int u = 0; u < 8; ++u) {
+          const Acc f = (Acc)ld(col[r + 8 * u]);
+#pragma unroll
+          for (int rr = 0; rr < R; ++rr) v[rr] += f * xs[rr][r + 8 * u];
+        }
       } else {
-        for (int i = r; i < lsz; i += 8) v += (Acc)ld(col[i]) * xs[i];
+        for (int i = r; i < lsz; i += 8) {
+          const Acc f = (Acc)ld(col[i]);
+#pragma unroll
+          for (int rr = 0; rr < R; ++rr) v[rr] += f * xs[rr][i];
+        }
       }
-      d = (double)v;
+#pragma unroll
+      for (int rr = 0; rr < R; ++rr) d[rr] = (double)v[rr];
     }
     // the loop bound is uniform over the CTA, so every lane reaches the shuffles
 #pragma unroll
-    for (int o = 4; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
-    if (t < total && r == 0) tv[((int64_t)p * nseg + s_seg[q]) * kc + j] = d;
+    for (int rr = 0; rr < R; ++rr) {
+#pragma unroll
+      for (int o = 4; o > 0; o >>= 1) d[rr] += __shfl_xor_sync(0xffffffffu, d[rr], o);
+      if (t < total && r == 0) tv[rr * tvs + ((int64_t)p * nseg + s_seg[q]) * kc + j] = d[rr];
+    }
   }
 }
 
@@ -118,7 +139,7 @@ __global__ void __launch_bounds__(256) k_lr_proj(MatvecDev mv, T* const* __restr
 // t / 64 + 4 j, of the low-rank leaves every fourth one (starting at t / 64)
 // with all its columns.  LSZ > 0 fixes the leaf size at compile time
 // (unrolled, 16 loads in flight).
-template <typename T, int LSZ>
+template <typename T, int LSZ, int R>
 __global__ void __launch_bounds__(256) k_hmv_rows(MatvecDev mv, T* const* __restrict__ D,
                                                   T* const* __restrict__ U,
                                                   T* const* __restrict__ V,
@@ -126,11 +147,11 @@ __global__ void __launch_bounds__(256) k_hmv_rows(MatvecDev mv, T* const* __rest
                                                   const double* const* __restrict__ x,
                                                   double* const* __restrict__ y, double alpha,
                                                   double beta, const double* __restrict__ tv,
-                                                  bool trans) {
+                                                  bool trans, int64_t vs, int64_t tvs) {
   using Acc = AccT<T>;
   extern __shared__ __align__(16) unsigned char smraw[];
   Acc* xs = reinterpret_cast<Acc*>(smraw);
-  __shared__ double part[4][64];
+  __shared__ double part[R][4][64];
   const int c = blockIdx.x, p = blockIdx.y;
   double* yp = y[p];
   if (!yp) return;
@@ -146,7 +167,8 @@ __global__ void __launch_bounds__(256) k_hmv_rows(MatvecDev mv, T* const* __rest
   const int d0 = dptr[c], nd = dptr[c + 1] - d0;
   const int l0 = lptr[c], nlc = lptr[c + 1] - l0;
   const int kc = mv.kc;
-  Acc* ts = xs + nd * lsz;
+  const int xstride = nd * lsz, tstride = nlc * kc;   // per right-hand side
+  Acc* ts = xs + R * xstride;
   // per-leaf descriptors of this chunk, loaded once in parallel
   __shared__ int64_t s_off[MAXQ];
   __shared__ int s_ld[MAXQ], s_k[MAXQ], s_leaf[MAXQ];
@@ -159,40 +181,53 @@ __global__ void __launch_bounds__(256) k_hmv_rows(MatvecDev mv, T* const* __rest
       s_off[q] = trans ? mv.lr_col0[l] * kc + mv.lt_coloff[l0 + q]
                        : mv.lr_row0[l] * kc + mv.l_rowoff[l0 + q];
     }
-    for (int e = threadIdx.x; e < nd * lsz; e += 256) {
-      const int q = e / lsz, j = e - q * lsz;
-      xs[e] = (Acc)xp[dcol[d0 + q] + j];
+    for (int e = threadIdx.x; e < R * xstride; e += 256) {
+      const int rr = R == 1 ? 0 : e / xstride, e1 = e - rr * xstride;
+      const int q = e1 / lsz, j = e1 - q * lsz;
+      xs[e] = (Acc)xp[rr * vs + dcol[d0 + q] + j];
     }
     const int* sptr = trans ? mv.segt_ptr : mv.seg_ptr;
     const int nseg = trans ? mv.nsegt : mv.nseg;
-    for (int e = threadIdx.x; e < nlc * kc; e += 256) {
-      const int q = e / kc, j = e - q * kc;
+    for (int e = threadIdx.x; e < R * tstride; e += 256) {
+      const int rr = R == 1 ? 0 : e / tstride, e1 = e - rr * tstride;
+      const int q = e1 / kc, j = e1 - q * kc;
       const int l = lleaf[l0 + q];
       double v = 0.0;
       if (j < rank[p][l])
-        for (int sg = sptr[l]; sg < sptr[l + 1]; ++sg) v += tv[((int64_t)p * nseg + sg) * kc + j];
+        for (int sg = sptr[l]; sg < sptr[l + 1]; ++sg)
+          v += tv[rr * tvs + ((int64_t)p * nseg + sg) * kc + j];
       ts[e] = (Acc)v;
     }
   }
   __syncthreads();
-  double acc = 0.0;
+  double acc[R];
+#pragma unroll
+  for (int rr = 0; rr < R; ++rr) acc[rr] = 0.0;
   if (have && i < lsz) {
     const T* Dp = D[p];
     for (int q = 0; q < nd; ++q) {
       const T* blk = Dp + (int64_t)(q < MAXQ ? s_leaf[q] : dleaf[d0 + q]) * lsz * lsz;
       const Acc* xq = xs + q * lsz;
-      Acc sp = Acc(0);
+      Acc sp[R];
+#pragma unroll
+      for (int rr = 0; rr < R; ++rr) sp[rr] = Acc(0);
       if (LSZ > 0) {
 #pragma unroll
         for (int t = 0; t < (LSZ > 0 ? LSZ : 64) / 4; ++t) {
           const int j = g + 4 * t;
-          sp += (Acc)ld(blk[trans ? j + i * LSZ : i + j * LSZ]) * xq[j];
+          const Acc f = (Acc)ld(blk[trans ? j + i * LSZ : i + j * LSZ]);
+#pragma unroll
+          for (int rr = 0; rr < R; ++rr) sp[rr] += f * xq[rr * xstride + j];
         }
       } else {
-        for (int j = g; j < lsz; j += 4)
-          sp += (Acc)ld(blk[trans ? j + (int64_t)i * lsz : i + (int64_t)j * lsz]) * xq[j];
+        for (int j = g; j < lsz; j += 4) {
+          const Acc f = (Acc)ld(blk[trans ? j + (int64_t)i * lsz : i + (int64_t)j * lsz]);
+#pragma unroll
+          for (int rr = 0; rr < R; ++rr) sp[rr] += f * xq[rr * xstride + j];
+        }
       }
-      acc += (double)sp;
+#pragma unroll
+      for (int rr = 0; rr < R; ++rr) acc[rr] += (double)sp[rr];
     }
     // low-rank leaves: thread group g takes leaves g, g+4, ...; all of a
     // leaf's columns, partial sums of at most 16 products
@@ -211,20 +246,30 @@ __global__ void __launch_bounds__(256) k_hmv_rows(MatvecDev mv, T* const* __rest
       const T* fb = Fp + off + i;
       const Acc* tq = ts + q * kc;
       for (int j0 = 0; j0 < k; j0 += 16) {
-        Acc sp = Acc(0);
+        Acc sp[R];
+#pragma unroll
+        for (int rr = 0; rr < R; ++rr) sp[rr] = Acc(0);
         const int j1 = min(k, j0 + 16);
-        for (int j = j0; j < j1; ++j) sp += (Acc)ld(fb[(int64_t)j * ldm]) * tq[j];
-        acc += (double)sp;
+        for (int j = j0; j < j1; ++j) {
+          const Acc f = (Acc)ld(fb[(int64_t)j * ldm]);
+#pragma unroll
+          for (int rr = 0; rr < R; ++rr) sp[rr] += f * tq[rr * tstride + j];
+        }
+#pragma unroll
+        for (int rr = 0; rr < R; ++rr) acc[rr] += (double)sp[rr];
       }
     }
   }
-  part[g][i] = acc;
+#pragma unroll
+  for (int rr = 0; rr < R; ++rr) part[rr][g][i] = acc[rr];
   __syncthreads();
-  if (g == 0 && i < lsz) {
-    const double sum = part[0][i] + part[1][i] + part[2][i] + part[3][i];
-    double* yc = yp + (int64_t)c * lsz;
-    const double old = (beta != 0.0) ? beta * yc[i] : 0.0;
-    yc[i] = old + (have ? alpha * sum : 0.0);
+  for (int e = threadIdx.x; e < R * 64; e += 256) {
+    const int rr = e >> 6, ii = e & 63;
+    if (ii >= lsz || (R == 1 && e >= 64)) continue;
+    const double sum = part[rr][0][ii] + part[rr][1][ii] + part[rr][2][ii] + part[rr][3][ii];
+    double* yc = yp + rr * vs + (int64_t)c * lsz;
+    const double old = (beta != 0.0) ? beta * yc[ii] : 0.0;
+    yc[ii] = old + (have ? alpha * sum : 0.0);
   }
 }
 
@@ -242,11 +287,16 @@ __global__ void k_permute(const double* __restrict__ in, double* __restrict__ ou
 __global__ void k_diag_update(double* const* __restrict__ y, const double* const* __restrict__ a,
                               const double* const* __restrict__ x,
                               const double* const* __restrict__ b,
-                              const double* const* __restrict__ z, int n2, double sgn) {
+                              const double* const* __restrict__ z, int n2, double sgn,
+                              int64_t vs) {
   const int p = blockIdx.y;
+  const int64_t o = blockIdx.z * vs;   // right-hand side blockIdx.z
   double* yp = y[p];
   if (!yp) return;
+  yp += o;
   const double *ap = a[p], *xp = x[p], *bp = b[p], *zp = z[p];
+  if (xp) xp += o;
+  if (zp) zp += o;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += gridDim.x * blockDim.x) {
     double s = 0.0;
     if (ap && xp) s += ap[i] * xp[i];
@@ -256,11 +306,14 @@ __global__ void k_diag_update(double* const* __restrict__ y, const double* const
 }
 
 __global__ void k_copy_planes(double* const* __restrict__ dst, const double* const* __restrict__ src,
-                              int n2) {
+                              int n2, int64_t vs) {
   const int p = blockIdx.y;
+  const int64_t o = blockIdx.z * vs;   // right-hand side blockIdx.z
   double* d = dst[p];
   const double* s = src[p];
   if (!d) return;
+  d += o;
+  if (s) s += o;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += gridDim.x * blockDim.x)
     d[i] = s ? s[i] : 0.0;
 }
@@ -281,34 +334,50 @@ void launch_to_bf16(const float* in, void* out, int64_t count, cudaStream_t st) 
   ACR_LAUNCHED(1);
 }
 
-template <typename T>
-void launch_hmatvec(const MatvecDev& mv, T* const* dense, T* const* U, T* const* V,
-                    const int* const* rank, const double* const* x, double* const* y,
-                    double alpha, double beta, bool trans, double* tv, int P, cudaStream_t st) {
-  if (P <= 0) return;
+template <typename T, int R>
+static void hmatvec_r(const MatvecDev& mv, T* const* dense, T* const* U, T* const* V,
+                      const int* const* rank, const double* const* x, double* const* y,
+                      double alpha, double beta, bool trans, double* tv, int P, int64_t vs,
+                      int64_t tvs, cudaStream_t st) {
   using Acc = AccT<T>;
-  const size_t sm_rows = ((size_t)mv.max_d * mv.lsz + (size_t)mv.max_l * mv.kc) * sizeof(Acc);
+  const size_t sm_rows =
+      ((size_t)mv.max_d * mv.lsz + (size_t)mv.max_l * mv.kc) * R * sizeof(Acc);
   static bool attr_set = false;   // per instantiation: allow the largest staging buffers
   if (!attr_set) {
-    ACR_CUDA(cudaFuncSetAttribute(k_hmv_rows<T, 64>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    ACR_CUDA(cudaFuncSetAttribute(k_hmv_rows<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  200 * 1024));
+    ACR_CUDA(cudaFuncSetAttribute(k_hmv_rows<T, 64, R>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, 180 * 1024));
+    ACR_CUDA(cudaFuncSetAttribute(k_hmv_rows<T, 0, R>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, 180 * 1024));
     attr_set = true;
   }
   if (mv.max_l > MAXQ || mv.lsz > 64)
     throw CudaError{cudaErrorInvalidConfiguration, "more low-rank leaves per chunk than staged"};
-  if (sm_rows > 200 * 1024)
+  if (sm_rows > 180 * 1024)
     throw CudaError{cudaErrorInvalidConfiguration, "apply staging exceeds shared memory"};
   if (mv.nl > 0)
-    k_lr_proj<T><<<dim3(mv.nchunks, P), 256, 0, st>>>(mv, U, V, rank, x, tv, trans);
+    k_lr_proj<T, R><<<dim3(mv.nchunks, P), 256, 0, st>>>(mv, U, V, rank, x, tv, trans, vs, tvs);
   if (mv.lsz == 64)
-    k_hmv_rows<T, 64><<<dim3(mv.nchunks, P), 256, sm_rows, st>>>(mv, dense, U, V, rank, x, y,
-                                                                   alpha, beta, tv, trans);
+    k_hmv_rows<T, 64, R><<<dim3(mv.nchunks, P), 256, sm_rows, st>>>(
+        mv, dense, U, V, rank, x, y, alpha, beta, tv, trans, vs, tvs);
   else
-    k_hmv_rows<T, 0><<<dim3(mv.nchunks, P), 256, sm_rows, st>>>(mv, dense, U, V, rank, x, y,
-                                                                  alpha, beta, tv, trans);
+    k_hmv_rows<T, 0, R><<<dim3(mv.nchunks, P), 256, sm_rows, st>>>(
+        mv, dense, U, V, rank, x, y, alpha, beta, tv, trans, vs, tvs);
   ACR_LAUNCHED(mv.nl > 0 ? 2 : 1);
+}
+
+template <typename T>
+void launch_hmatvec(const MatvecDev& mv, T* const* dense, T* const* U, T* const* V,
+                    const int* const* rank, const double* const* x, double* const* y,
+                    double alpha, double beta, bool trans, double* tv, int P, int nr,
+                    int64_t vs, int64_t tvs, cudaStream_t st) {
+  if (P <= 0) return;
+  switch (nr) {
+    case 1: hmatvec_r<T, 1>(mv, dense, U, V, rank, x, y, alpha, beta, trans, tv, P, vs, tvs, st); break;
+    case 2: hmatvec_r<T, 2>(mv, dense, U, V, rank, x, y, alpha, beta, trans, tv, P, vs, tvs, st); break;
+    case 4: hmatvec_r<T, 4>(mv, dense, U, V, rank, x, y, alpha, beta, trans, tv, P, vs, tvs, st); break;
+    case 8: hmatvec_r<T, 8>(mv, dense, U, V, rank, x, y, alpha, beta, trans, tv, P, vs, tvs, st); break;
+    default: throw CudaError{cudaErrorInvalidValue, "right-hand-side group must be 1, 2, 4 or 8"};
+  }
 }
 
 void launch_permute(const double* in, double* out, const int* perm, int n2, int nplanes,
@@ -321,32 +390,29 @@ void launch_permute(const double* in, double* out, const int* perm, int n2, int 
 
 void launch_diag_update(double* const* y, const double* const* a, const double* const* x,
                         const double* const* b, const double* const* z, int n2, int P,
-                        double sgn, cudaStream_t st) {
+                        double sgn, int nr, int64_t vs, cudaStream_t st) {
   if (P <= 0) return;
-  dim3 grid((n2 + 255) / 256 < 64 ? (n2 + 255) / 256 : 64, P);
-  k_diag_update<<<grid, 256, 0, st>>>(y, a, x, b, z, n2, sgn);
+  dim3 grid((n2 + 255) / 256 < 64 ? (n2 + 255) / 256 : 64, P, nr);
+  k_diag_update<<<grid, 256, 0, st>>>(y, a, x, b, z, n2, sgn, vs);
   ACR_LAUNCHED(1);
 }
 
-void launch_copy_planes(double* const* dst, const double* const* src, int n2, int P,
-                        cudaStream_t st) {
+void launch_copy_planes(double* const* dst, const double* const* src, int n2, int P, int nr,
+                        int64_t vs, cudaStream_t st) {
   if (P <= 0) return;
-  dim3 grid((n2 + 255) / 256 < 64 ? (n2 + 255) / 256 : 64, P);
-  k_copy_planes<<<grid, 256, 0, st>>>(dst, src, n2);
+  dim3 grid((n2 + 255) / 256 < 64 ? (n2 + 255) / 256 : 64, P, nr);
+  k_copy_planes<<<grid, 256, 0, st>>>(dst, src, n2, vs);
   ACR_LAUNCHED(1);
 }
 
-template void launch_hmatvec<double>(const MatvecDev&, double* const*, double* const*,
-                                     double* const*, const int* const*, const double* const*,
-                                     double* const*, double, double, bool, double*, int,
-                                     cudaStream_t);
-template void launch_hmatvec<float>(const MatvecDev&, float* const*, float* const*, float* const*,
-                                    const int* const*, const double* const*, double* const*,
-                                    double, double, bool, double*, int, cudaStream_t);
-template void launch_hmatvec<__nv_bfloat16>(const MatvecDev&, __nv_bfloat16* const*,
-                                            __nv_bfloat16* const*, __nv_bfloat16* const*,
-                                            const int* const*, const double* const*,
-                                            double* const*, double, double, bool, double*, int,
-                                            cudaStream_t);
+#define ACR_HMV_INST(T)                                                                     \
+  template void launch_hmatvec<T>(const MatvecDev&, T* const*, T* const*, T* const*,           \
+                                  const int* const*, const double* const*, double* const*,     \
+                                  double, double, bool, double*, int, int, int64_t, int64_t,   \
+                                  cudaStream_t);
+ACR_HMV_INST(double)
+ACR_HMV_INST(float)
+ACR_HMV_INST(__nv_bfloat16)
+#undef ACR_HMV_INST
 
 }  // namespace acr

@@ -107,7 +107,8 @@ class EngineBase {
  public:
   virtual ~EngineBase() {}
   virtual void setup(const double* coef, cudaStream_t st) = 0;
-  virtual void apply(const double* r, double* z, bool trans, cudaStream_t st) = 0;
+  // z = M^-1 r (M^-T r when trans) for nrhs vectors N doubles apart
+  virtual void apply(const double* r, double* z, bool trans, cudaStream_t st, int nrhs = 1) = 0;
   acr_setup_info info{};
   acr_profile prof{};
   bool profiling = false;
@@ -128,7 +129,7 @@ class Engine : public EngineBase {
   ~Engine() override { release(); }
 
   void setup(const double* coef, cudaStream_t st) override;
-  void apply(const double* r, double* z, bool trans, cudaStream_t st) override;
+  void apply(const double* r, double* z, bool trans, cudaStream_t st, int nrhs = 1) override;
 
  private:
   double eps, eta;
@@ -539,7 +540,9 @@ class Engine : public EngineBase {
   }
 
   void build_apply_program();
-  void run_steps(const std::vector<ApplyStep>& steps, cudaStream_t st);
+  void run_steps(const std::vector<ApplyStep>& steps, int nr, cudaStream_t st);
+  static constexpr int RB = 8;       // right-hand sides per apply pass (multi-RHS apply)
+  int64_t tvs = 0;                   // doubles of projection scratch per right-hand side
   void collect_info();
 };
 
@@ -877,14 +880,16 @@ void Engine<T>::collect_info() {
 
 template <typename T>
 void Engine<T>::build_apply_program() {
-  Fv = (double*)dmalloc(sizeof(double) * N); owned.push_back(Fv);
-  Gv = (double*)dmalloc(sizeof(double) * N); owned.push_back(Gv);
-  Uv = (double*)dmalloc(sizeof(double) * N); owned.push_back(Uv);
-  Tv = (double*)dmalloc(sizeof(double) * N); owned.push_back(Tv);
+  // work vectors for up to RB right-hand sides, N doubles apart; the step
+  // tables hold the pointers of the first one
+  Fv = (double*)dmalloc(sizeof(double) * N * RB); owned.push_back(Fv);
+  Gv = (double*)dmalloc(sizeof(double) * N * RB); owned.push_back(Gv);
+  Uv = (double*)dmalloc(sizeof(double) * N * RB); owned.push_back(Uv);
+  Tv = (double*)dmalloc(sizeof(double) * N * RB); owned.push_back(Tv);
   maxP = 1;
   for (const Level& lev : levels) maxP = std::max<int>(maxP, (int)std::max(lev.red.size(), lev.black.size()));
-  tvscr = (double*)dmalloc(sizeof(double) * (size_t)maxP *
-                          std::max({mvd.nseg, mvd.nsegt, 1}) * kc);
+  tvs = (int64_t)maxP * std::max({mvd.nseg, mvd.nsegt, 1}) * kc;
+  tvscr = (double*)dmalloc(sizeof(double) * (size_t)tvs * RB);
   owned.push_back(tvscr);
   auto vec = [&](double* base, int k) -> double* { return (k >= 0 && k < n) ? base + (int64_t)k * n2 : nullptr; };
   // hmatvec tables: dense, U, V, rank, x, y (6 * P pointers)
@@ -1042,7 +1047,7 @@ void Engine<T>::build_apply_program() {
 }
 
 template <typename T>
-void Engine<T>::run_steps(const std::vector<ApplyStep>& steps, cudaStream_t st) {
+void Engine<T>::run_steps(const std::vector<ApplyStep>& steps, int nr, cudaStream_t st) {
   for (const ApplyStep& s : steps) {
     const int P = s.P;
     void** t = s.tabs;
@@ -1050,27 +1055,35 @@ void Engine<T>::run_steps(const std::vector<ApplyStep>& steps, cudaStream_t st) 
       using B = __nv_bfloat16;
       launch_hmatvec<B>(mvd, (B* const*)t, (B* const*)(t + P), (B* const*)(t + 2 * P),
                         (const int* const*)(t + 3 * P), (const double* const*)(t + 4 * P),
-                        (double* const*)(t + 5 * P), s.alpha, s.beta, s.trans, tvscr, P, st);
+                        (double* const*)(t + 5 * P), s.alpha, s.beta, s.trans, tvscr, P, nr, N,
+                        tvs, st);
     } else if (s.kind == 0) {
       launch_hmatvec<T>(mvd, (T* const*)t, (T* const*)(t + P), (T* const*)(t + 2 * P),
                         (const int* const*)(t + 3 * P), (const double* const*)(t + 4 * P),
-                        (double* const*)(t + 5 * P), s.alpha, s.beta, s.trans, tvscr, P, st);
+                        (double* const*)(t + 5 * P), s.alpha, s.beta, s.trans, tvscr, P, nr, N,
+                        tvs, st);
     } else if (s.kind == 1) {
       launch_diag_update((double* const*)t, (const double* const*)(t + P),
                          (const double* const*)(t + 2 * P), (const double* const*)(t + 3 * P),
-                         (const double* const*)(t + 4 * P), n2, P, s.sgn, st);
+                         (const double* const*)(t + 4 * P), n2, P, s.sgn, nr, N, st);
     } else {
-      launch_copy_planes((double* const*)t, (const double* const*)(t + P), n2, P, st);
+      launch_copy_planes((double* const*)t, (const double* const*)(t + P), n2, P, nr, N, st);
     }
   }
 }
 
 template <typename T>
-void Engine<T>::apply(const double* r, double* z, bool trans, cudaStream_t st) {
-  launch_permute(r, Fv, sd.perm, n2, n, true, st);
-  run_steps(trans ? fwdT_steps : fwd_steps, st);
-  run_steps(trans ? bwdT_steps : bwd_steps, st);
-  launch_permute(Uv, z, sd.perm, n2, n, false, st);
+void Engine<T>::apply(const double* r, double* z, bool trans, cudaStream_t st, int nrhs) {
+  // groups of 8, 4, 2, 1 right-hand sides; each group streams the factors once
+  for (int k = 0; k < nrhs;) {
+    int R = RB;
+    while (R > nrhs - k) R >>= 1;
+    launch_permute(r + (int64_t)k * N, Fv, sd.perm, n2, n * R, true, st);
+    run_steps(trans ? fwdT_steps : fwd_steps, R, st);
+    run_steps(trans ? bwdT_steps : bwd_steps, R, st);
+    launch_permute(Uv, z + (int64_t)k * N, sd.perm, n2, n * R, false, st);
+    k += R;
+  }
 }
 
 
@@ -1282,6 +1295,184 @@ int run_gmres(Krylov& K, int m, double rtol, int maxit, const double* f, double*
   return status;
 }
 
+// GMRES(m) for nr right-hand sides of the same operator in lockstep: every
+// system keeps its own Arnoldi basis, Hessenberg matrix and Givens rotations
+// (the iteration of run_gmres), while each step's preconditioner applies
+// share passes over the factors (acr_apply's multi-RHS groups) and the
+// SpMVs, dots and vector updates of all systems run in single launches.
+// A system that has converged is frozen: its later Arnoldi vectors are
+// computed but do not enter its solution.  info: the largest iteration
+// count and residual over the systems; converged only if all converged.
+int run_gmres_batch(Krylov& K, int m, double rtol, int maxit, const double* f, double* u, int nr,
+                    acr_solve_info* info) {
+  const int64_t N = K.N;
+  if (m < 1) m = 30;
+  if (m > 60) m = 60;
+  const int64_t RN = (int64_t)nr * N;
+  double* V = K.dbuf((size_t)(m + 1) * RN);
+  double* Z = K.dbuf((size_t)m * RN);
+  double* W = K.dbuf(RN);
+  double* Rv = K.dbuf(RN);
+  const int nbp = 600;
+  double* part = K.dbuf((size_t)nbp * (m + 1) * nr);
+  double* dout = K.dbuf((size_t)(m + 1) * nr);
+  double* dco = K.dbuf((size_t)(m + 1) * nr);
+  std::vector<double> hbuf((size_t)(m + 1) * nr);
+  auto fetch = [&](int cnt) {
+    ACR_CUDA(cudaMemcpyAsync(hbuf.data(), dout, cnt * sizeof(double), cudaMemcpyDeviceToHost, K.st));
+    ACR_CUDA(cudaStreamSynchronize(K.st));
+  };
+  auto put = [&](const std::vector<double>& v) {
+    ACR_CUDA(cudaMemcpyAsync(dco, v.data(), v.size() * sizeof(double), cudaMemcpyHostToDevice, K.st));
+  };
+  auto norms = [&](const double* X, std::vector<double>& out) {   // ||X_r||
+    launch_bmultidot(X, 0, N, 1, X, N, nr, part, dout, K.st);
+    fetch(nr);
+    for (int r = 0; r < nr; ++r) out[r] = std::sqrt(std::max(hbuf[r], 0.0));
+  };
+  auto residual = [&]() {   // Rv = f - A u
+    launch_spmv(K.coef, u, W, K.n, K.st, nr);
+    ACR_CUDA(cudaMemcpyAsync(Rv, f, RN * sizeof(double), cudaMemcpyDeviceToDevice, K.st));
+    std::vector<double> one(nr, 1.0);
+    put(one);
+    launch_bmultiaxpy(Rv, W, 0, N, 1, dco, -1.0, N, nr, K.st);
+  };
+  std::vector<double> nf(nr), beta(nr), res(nr, 0.0);
+  norms(f, nf);
+  std::vector<int> its(nr, 0);
+  std::vector<char> done(nr, 0);
+  int status = S_OK;
+  for (int r = 0; r < nr; ++r)
+    if (nf[r] == 0.0) {
+      ACR_CUDA(cudaMemsetAsync(u + r * N, 0, N * sizeof(double), K.st));
+      done[r] = 1;
+    }
+  residual();
+  norms(Rv, beta);
+  for (int r = 0; r < nr; ++r) {
+    if (done[r]) continue;
+    res[r] = beta[r] / nf[r];
+    if (res[r] <= rtol) done[r] = 1;
+  }
+  int total_it = 0;
+  std::vector<double> H((size_t)nr * (m + 1) * m), cs((size_t)nr * m), sn((size_t)nr * m),
+      g((size_t)nr * (m + 1)), y((size_t)m);
+  std::vector<int> used(nr);
+  std::vector<char> stop(nr);
+  while (total_it < maxit) {
+    bool any = false;
+    for (int r = 0; r < nr; ++r) any |= !done[r];
+    if (!any) break;
+    std::fill(H.begin(), H.end(), 0.0);
+    std::fill(g.begin(), g.end(), 0.0);
+    std::vector<double> sc(nr);
+    for (int r = 0; r < nr; ++r) {
+      g[(size_t)r * (m + 1)] = beta[r];
+      sc[r] = (!done[r] && beta[r] > 0.0) ? 1.0 / beta[r] : 0.0;
+      used[r] = 0;
+      stop[r] = done[r];
+    }
+    put(sc);
+    launch_baxpby(V, Rv, dco, 0.0, N, N, nr, K.st);
+    for (int j = 0; j < m; ++j) {
+      bool active = false;
+      for (int r = 0; r < nr; ++r) active |= !stop[r];
+      if (!active) break;
+      double* Vj = V + (int64_t)j * RN;
+      double* Zj = Z + (int64_t)j * RN;
+      K.E->apply(Vj, Zj, false, K.st, nr);
+      launch_spmv(K.coef, Zj, W, K.n, K.st, nr);
+      std::vector<double> h((size_t)nr * (j + 1), 0.0);
+      for (int pass = 0; pass < 2; ++pass) {   // classical Gram-Schmidt, twice
+        launch_bmultidot(V, RN, N, j + 1, W, N, nr, part, dout, K.st);
+        fetch(nr * (j + 1));
+        std::vector<double> c((size_t)nr * (j + 1));
+        for (size_t e = 0; e < c.size(); ++e) { h[e] += hbuf[e]; c[e] = hbuf[e]; }
+        put(c);
+        launch_bmultiaxpy(W, V, RN, N, j + 1, dco, -1.0, N, nr, K.st);
+      }
+      std::vector<double> hn(nr);
+      norms(W, hn);
+      for (int r = 0; r < nr; ++r) sc[r] = (!stop[r] && hn[r] > 0.0) ? 1.0 / hn[r] : 0.0;
+      put(sc);
+      launch_baxpby(V + (int64_t)(j + 1) * RN, W, dco, 0.0, N, N, nr, K.st);
+      for (int r = 0; r < nr; ++r) {
+        if (stop[r]) continue;
+        double* Hr = H.data() + (size_t)r * (m + 1) * m;
+        double* csr = cs.data() + (size_t)r * m;
+        double* snr = sn.data() + (size_t)r * m;
+        double* gr = g.data() + (size_t)r * (m + 1);
+        for (int k = 0; k <= j; ++k) Hr[(size_t)k * m + j] = h[(size_t)r * (j + 1) + k];
+        Hr[(size_t)(j + 1) * m + j] = hn[r];
+        for (int k = 0; k < j; ++k) {
+          const double a = Hr[(size_t)k * m + j], b = Hr[(size_t)(k + 1) * m + j];
+          Hr[(size_t)k * m + j] = csr[k] * a + snr[k] * b;
+          Hr[(size_t)(k + 1) * m + j] = -snr[k] * a + csr[k] * b;
+        }
+        const double a = Hr[(size_t)j * m + j], b = Hr[(size_t)(j + 1) * m + j];
+        const double d = std::hypot(a, b);
+        if (d == 0.0) { status = S_BREAKDOWN; stop[r] = 1; continue; }
+        csr[j] = a / d; snr[j] = b / d;
+        Hr[(size_t)j * m + j] = d;
+        Hr[(size_t)(j + 1) * m + j] = 0.0;
+        gr[j + 1] = -snr[j] * gr[j];
+        gr[j] = csr[j] * gr[j];
+        ++its[r];
+        used[r] = j + 1;
+        if (std::fabs(gr[j + 1]) / nf[r] <= rtol || hn[r] == 0.0) stop[r] = 1;
+      }
+      ++total_it;
+      if (total_it >= maxit) break;
+    }
+    // u_r += Z y_r over the steps system r used
+    std::vector<double> coef((size_t)nr * m, 0.0);
+    int umax = 0;
+    for (int r = 0; r < nr; ++r) {
+      if (done[r] || used[r] == 0) continue;
+      const double* Hr = H.data() + (size_t)r * (m + 1) * m;
+      const double* gr = g.data() + (size_t)r * (m + 1);
+      for (int k = used[r] - 1; k >= 0; --k) {
+        double sacc = gr[k];
+        for (int l = k + 1; l < used[r]; ++l) sacc -= Hr[(size_t)k * m + l] * y[l];
+        y[k] = sacc / Hr[(size_t)k * m + k];
+      }
+      for (int k = 0; k < used[r]; ++k) coef[(size_t)r * m + k] = y[k];
+      umax = std::max(umax, used[r]);
+    }
+    if (umax > 0) {
+      // coefficients laid out r * umax + k for the batched update
+      std::vector<double> c2((size_t)nr * umax, 0.0);
+      for (int r = 0; r < nr; ++r)
+        for (int k = 0; k < umax; ++k) c2[(size_t)r * umax + k] = coef[(size_t)r * m + k];
+      put(c2);
+      launch_bmultiaxpy(u, Z, RN, N, umax, dco, 1.0, N, nr, K.st);
+    }
+    residual();
+    norms(Rv, beta);
+    for (int r = 0; r < nr; ++r) {
+      if (done[r]) continue;
+      res[r] = beta[r] / nf[r];
+      if (res[r] <= rtol) done[r] = 1;
+    }
+    if (status == S_BREAKDOWN) break;
+  }
+  bool all = true;
+  int itmax = 0;
+  double resmax = 0.0;
+  for (int r = 0; r < nr; ++r) {
+    all &= (nf[r] == 0.0) || res[r] <= rtol;
+    itmax = std::max(itmax, its[r]);
+    resmax = std::max(resmax, res[r]);
+  }
+  if (status == S_OK && !all) status = S_NOT_CONVERGED;
+  if (info) {
+    info->iterations = itmax;
+    info->converged = status == S_OK;
+    info->rel_residual = resmax;
+  }
+  return status;
+}
+
 }  // namespace
 
 }  // namespace acr
@@ -1409,8 +1600,7 @@ acr_status acr_apply(acr_handle* h, const double* r, double* z, int32_t nrhs,
                      cudaStream_t stream) {
   if (!h || !h->e || !r || !z || nrhs < 1) return ACR_ERR_INVALID_ARG;
   return guarded([&] {
-    const int64_t N = h->e->N;
-    for (int k = 0; k < nrhs; ++k) h->e->apply(r + k * N, z + k * N, false, stream);
+    h->e->apply(r, z, false, stream, nrhs);
     return 0;
   });
 }
@@ -1419,8 +1609,7 @@ acr_status acr_apply_transpose(acr_handle* h, const double* r, double* z, int32_
                                cudaStream_t stream) {
   if (!h || !h->e || !r || !z || nrhs < 1) return ACR_ERR_INVALID_ARG;
   return guarded([&] {
-    const int64_t N = h->e->N;
-    for (int k = 0; k < nrhs; ++k) h->e->apply(r + k * N, z + k * N, true, stream);
+    h->e->apply(r, z, true, stream, nrhs);
     return 0;
   });
 }
@@ -1428,7 +1617,7 @@ acr_status acr_apply_transpose(acr_handle* h, const double* r, double* z, int32_
 static acr_status krylov_common(acr::EngineBase* E, const acr_grid* grid, const double* coef,
                                 int32_t method, int32_t restart, double rtol, int32_t maxit,
                                 const double* f, double* u, acr_solve_info* info,
-                                cudaStream_t stream, bool trans = false) {
+                                cudaStream_t stream, bool trans = false, int nrhs = 1) {
   if (!grid_ok(grid) || !coef || !f || !u || !(rtol > 0.0) || maxit < 1 ||
       (method != ACR_PCG && method != ACR_GMRES))
     return ACR_ERR_INVALID_ARG;
@@ -1445,8 +1634,25 @@ static acr_status krylov_common(acr::EngineBase* E, const acr_grid* grid, const 
     ACR_CUDA(cudaEventCreate(&e0));
     ACR_CUDA(cudaEventCreate(&e1));
     ACR_CUDA(cudaEventRecord(e0, stream));
-    int s = method == ACR_PCG ? acr::run_pcg(K, rtol, maxit, f, u, info)
-                              : acr::run_gmres(K, restart, rtol, maxit, f, u, info);
+    int s = acr::S_OK;
+    if (nrhs > 1 && method == ACR_GMRES) {
+      s = acr::run_gmres_batch(K, restart, rtol, maxit, f, u, nrhs, info);
+    } else if (nrhs > 1) {
+      // PCG: one system after another; info reports the largest count and residual
+      acr_solve_info one{}, agg{};
+      agg.converged = 1;
+      for (int r = 0; r < nrhs && s != acr::S_BREAKDOWN; ++r) {
+        const int sr = acr::run_pcg(K, rtol, maxit, f + r * K.N, u + r * K.N, &one);
+        if (sr != acr::S_OK && s == acr::S_OK) s = sr;
+        agg.iterations = std::max(agg.iterations, one.iterations);
+        agg.rel_residual = std::max(agg.rel_residual, one.rel_residual);
+        agg.converged &= one.converged;
+      }
+      if (info) *info = agg;
+    } else {
+      s = method == ACR_PCG ? acr::run_pcg(K, rtol, maxit, f, u, info)
+                            : acr::run_gmres(K, restart, rtol, maxit, f, u, info);
+    }
     ACR_CUDA(cudaEventRecord(e1, stream));
     ACR_CUDA(cudaEventSynchronize(e1));
     float ms = 0;
@@ -1461,8 +1667,9 @@ static acr_status krylov_common(acr::EngineBase* E, const acr_grid* grid, const 
 acr_status acr_krylov_solve(acr_handle* h, const double* coef, int32_t method, int32_t restart,
                             double rtol, int32_t maxit, const double* f, double* u,
                             int32_t nrhs, acr_solve_info* info, cudaStream_t stream) {
-  if (!h || !h->e || nrhs != 1) return ACR_ERR_INVALID_ARG;
-  return krylov_common(h->e, &h->grid, coef, method, restart, rtol, maxit, f, u, info, stream);
+  if (!h || !h->e || nrhs < 1 || nrhs > 64) return ACR_ERR_INVALID_ARG;
+  return krylov_common(h->e, &h->grid, coef, method, restart, rtol, maxit, f, u, info, stream,
+                       false, nrhs);
 }
 
 acr_status acr_krylov_solve_transpose(acr_handle* h, const double* coef, int32_t method,

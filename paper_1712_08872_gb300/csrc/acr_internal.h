@@ -106,30 +106,45 @@ struct MatvecDev {
   int nseg, nsegt;
 };
 
-// y_p = beta*y_p + alpha*op(H_p) x_p for P planes; op = H or H^T.
-// tv: scratch of P*max(nseg,nsegt)*kc doubles.  Null H_p skips the plane (y_p scaled
-// by beta only if beta != 1).
+// y_p = beta*y_p + alpha*op(H_p) x_p for P planes and nr (1, 2, 4 or 8)
+// right-hand sides; op = H or H^T.  Right-hand side r of plane p lives at
+// x[p] + r*vs (y likewise).  tv: scratch of nr blocks of tvs >=
+// P*max(nseg,nsegt)*kc doubles.  A null H_p sets y_p = beta*y_p.
 template <typename T>
 void launch_hmatvec(const MatvecDev& mv, T* const* dense, T* const* U, T* const* V,
                     const int* const* rank, const double* const* x, double* const* y,
-                    double alpha, double beta, bool trans, double* tv, int P, cudaStream_t st);
+                    double alpha, double beta, bool trans, double* tv, int P, int nr,
+                    int64_t vs, int64_t tvs, cudaStream_t st);
 
 // out[e] = bfloat16(in[e]) (round to nearest even), e < count; out is __nv_bfloat16*
 void launch_to_bf16(const float* in, void* out, int64_t count, cudaStream_t st);
 void launch_permute(const double* in, double* out, const int* perm, int n2, int nplanes,
                     bool to_cluster, cudaStream_t st);
-// y_p -= a_p .* x_p + b_p .* z_p (diagonal couplings; null pointers skipped)
+// y_p += sgn (a_p .* x_p + b_p .* z_p) (diagonal couplings; null pointers
+// skipped) for nr right-hand sides vs doubles apart (a, b shared)
 void launch_diag_update(double* const* y, const double* const* a, const double* const* x,
                         const double* const* b, const double* const* z, int n2, int P,
-                        double sgn, cudaStream_t st);
-void launch_copy_planes(double* const* dst, const double* const* src, int n2, int P,
-                        cudaStream_t st);
+                        double sgn, int nr, int64_t vs, cudaStream_t st);
+// dst_p = src_p (0 where src_p is null) for nr right-hand sides vs apart
+void launch_copy_planes(double* const* dst, const double* const* src, int n2, int P, int nr,
+                        int64_t vs, cudaStream_t st);
 
 // ------------------------------------------------------------ Krylov
 void launch_stencil_poisson(const double* kappa, double* coef, int n, cudaStream_t st);
 void launch_stencil_codi(const double* beta, double* coef, int n, cudaStream_t st);
 void launch_stencil_helmholtz(const double* sigma, double* coef, int n, cudaStream_t st);
-void launch_spmv(const double* coef, const double* x, double* y, int n, cudaStream_t st);
+// y = A x for nr vectors N doubles apart
+void launch_spmv(const double* coef, const double* x, double* y, int n, cudaStream_t st,
+                 int nr = 1);
+// batched systems r < nr: out[r*nk + k] = <V[k*ldk + r*ldr], W[r*ldr]>
+void launch_bmultidot(const double* V, int64_t ldk, int64_t ldr, int nk, const double* W,
+                      int64_t N, int nr, double* partial, double* out, cudaStream_t st);
+// batched: W_r += scale * sum_k coef[r*nk + k] V[k*ldk + r*ldr]
+void launch_bmultiaxpy(double* W, const double* V, int64_t ldk, int64_t ldr, int nk,
+                       const double* coef, double scale, int64_t N, int nr, cudaStream_t st);
+// batched: Y_r = a[r] X_r + b Y_r (a on the device)
+void launch_baxpby(double* Y, const double* X, const double* a, double b, int64_t ldr, int64_t N,
+                   int nr, cudaStream_t st);
 void launch_spmv_transpose(const double* coef, const double* x, double* y, int n,
                            cudaStream_t st);
 // grad = -lambda^T (dA/dkappa) u for the harmonic-mean Poisson stencil

@@ -78,10 +78,13 @@ __global__ void k_stencil_helmholtz(const double* __restrict__ sigma, double* __
   }
 }
 
+// y = A x; vector blockIdx.y of a batch sits blockIdx.y * N doubles further
 __global__ void k_spmv(const double* __restrict__ coef, const double* __restrict__ x,
                        double* __restrict__ y, int n) {
   const int64_t N = (int64_t)n * n * n;
   const int64_t n2 = (int64_t)n * n;
+  x += blockIdx.y * N;
+  y += blockIdx.y * N;
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < N;
        p += (int64_t)gridDim.x * blockDim.x) {
     const int ix = (int)(p % n), iy = (int)((p / n) % n), iz = (int)(p / n2);
@@ -204,6 +207,54 @@ __global__ void k_axpby_dev(double* __restrict__ y, const double* __restrict__ x
     y[i] = av * x[i] + (b == 0.0 ? 0.0 : b * y[i]);
 }
 
+// Batched dots for nr independent systems: out[r*nk + k] = <V[k*ldk + r*ldr], W[r*ldr]>,
+// two stages with a fixed order (partial per block, then a final pass)
+__global__ void k_bdot_partial(const double* __restrict__ V, int64_t ldk, int64_t ldr,
+                               const double* __restrict__ W, int64_t N, int nk,
+                               double* __restrict__ partial) {
+  const int k = blockIdx.y, r = blockIdx.z;
+  const double* v = V + k * ldk + r * ldr;
+  const double* w = W + r * ldr;
+  double s = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)RB + threadIdx.x; i < N; i += (int64_t)gridDim.x * RB)
+    s += v[i] * w[i];
+  __shared__ double sh[RB];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = RB / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[((int64_t)r * nk + k) * gridDim.x + blockIdx.x] = sh[0];
+}
+
+// w_r += scale * sum_k coef[r*nk + k] V[k*ldk + r*ldr], one system per blockIdx.y
+__global__ void k_bmultiaxpy(double* __restrict__ W, const double* __restrict__ V, int64_t ldk,
+                             int64_t ldr, int nk, const double* __restrict__ coef, double scale,
+                             int64_t N) {
+  const int r = blockIdx.y;
+  double* w = W + r * ldr;
+  const double* c = coef + (int64_t)r * nk;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int k = 0; k < nk; ++k) s += c[k] * V[k * ldk + r * ldr + i];
+    w[i] += scale * s;
+  }
+}
+
+// y_r = a[r] x_r + b y_r (b == 0: y_r not read), one system per blockIdx.y
+__global__ void k_baxpby(double* __restrict__ Y, const double* __restrict__ X,
+                         const double* __restrict__ a, double b, int64_t ldr, int64_t N) {
+  const int r = blockIdx.y;
+  double* y = Y + r * ldr;
+  const double* x = X + r * ldr;
+  const double av = a[r];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = av * x[i] + (b == 0.0 ? 0.0 : b * y[i]);
+}
+
 inline int grid_for(int64_t N) {
   int64_t b = (N + 255) / 256;
   return (int)(b < 152 * 16 ? (b < 1 ? 1 : b) : 152 * 16);
@@ -226,8 +277,36 @@ void launch_stencil_helmholtz(const double* sigma, double* coef, int n, cudaStre
   ACR_LAUNCHED(1);
 }
 
-void launch_spmv(const double* coef, const double* x, double* y, int n, cudaStream_t st) {
-  k_spmv<<<grid_for((int64_t)n * n * n), 256, 0, st>>>(coef, x, y, n);
+void launch_spmv(const double* coef, const double* x, double* y, int n, cudaStream_t st,
+                 int nr) {
+  if (nr < 1) return;
+  k_spmv<<<dim3(grid_for((int64_t)n * n * n), nr), 256, 0, st>>>(coef, x, y, n);
+  ACR_LAUNCHED(1);
+}
+
+void launch_bmultidot(const double* V, int64_t ldk, int64_t ldr, int nk, const double* W,
+                      int64_t N, int nr, double* partial, double* out, cudaStream_t st) {
+  if (nk <= 0 || nr <= 0) return;
+  int nb = (int)std::min<int64_t>(RBLK, (N + RB - 1) / RB);
+  if (nb < 1) nb = 1;
+  k_bdot_partial<<<dim3(nb, nk, nr), RB, 0, st>>>(V, ldk, ldr, W, N, nk, partial);
+  k_multidot_final<<<nk * nr, RB, 0, st>>>(partial, nb, out);
+  ACR_LAUNCHED(2);
+}
+
+void launch_bmultiaxpy(double* W, const double* V, int64_t ldk, int64_t ldr, int nk,
+                       const double* coef, double scale, int64_t N, int nr, cudaStream_t st) {
+  if (nk <= 0 || nr <= 0) return;
+  k_bmultiaxpy<<<dim3(std::max(1, grid_for(N) / std::max(1, nr / 4)), nr), 256, 0, st>>>(
+      W, V, ldk, ldr, nk, coef, scale, N);
+  ACR_LAUNCHED(1);
+}
+
+void launch_baxpby(double* Y, const double* X, const double* a, double b, int64_t ldr, int64_t N,
+                   int nr, cudaStream_t st) {
+  if (nr <= 0) return;
+  k_baxpby<<<dim3(std::max(1, grid_for(N) / std::max(1, nr / 4)), nr), 256, 0, st>>>(
+      Y, X, a, b, ldr, N);
   ACR_LAUNCHED(1);
 }
 

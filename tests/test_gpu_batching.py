@@ -1,0 +1,132 @@
+"""Multi-right-hand-side apply and lockstep GMRES (through the C ABI).
+
+* A multi-RHS apply runs, per right-hand side, exactly the arithmetic of the
+  single-RHS apply (the same products in the same order), so the two agree
+  bitwise; against the oracle's apply the FP64 bar of the single apply
+  holds (10 tau).
+* The lockstep GMRES must bring every system to its rtol (the oracle's SpMV
+  confirms each residual) and agree with one-at-a-time solves to within
+  10 cond(A) rtol.
+"""
+import numpy as np
+import pytest
+import scipy.sparse.linalg as sla
+
+from inputs import workload, uniform_rhs, codi_beta
+from oracle.assembly import stencil_codi, stencil_helmholtz, stencil_matrix, plane_blocks
+from oracle.cr import cr_setup, cr_apply
+from oracle.hstructure import Structure
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def acr():
+    from paper_1712_08872_gb300 import _build
+    _build.build()
+    import paper_1712_08872_gb300 as pkg
+    pkg.load_library()
+    return pkg
+
+
+def T(x):
+    return torch.tensor(np.ascontiguousarray(x), dtype=torch.float64, device="cuda:0")
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def _codi(acr, n):
+    beta = codi_beta(n)
+    coef = torch.empty(7 * n ** 3, dtype=torch.float64, device="cuda:0")
+    acr.acr_stencil_codi(n, T(beta), coef)
+    return stencil_codi(beta, n), coef
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2])
+@pytest.mark.parametrize("trans", [False, True])
+def test_multi_rhs_apply_equals_single_applies(acr, prec, trans):
+    """11 right-hand sides = groups of 8, 2 and 1."""
+    n, nr = 16, 11
+    st, coef = _codi(acr, n)
+    N = n ** 3
+    R = np.stack([uniform_rhs(n, 40 + k) for k in range(nr)])
+    h = acr.Handle(n, coef, 1e-2, 2.0, 32, prec, 32)
+    Zm = torch.empty(nr * N, dtype=torch.float64, device="cuda:0")
+    (h.apply_transpose if trans else h.apply)(T(R.ravel()), Zm, nrhs=nr)
+    Zs = torch.empty(N, dtype=torch.float64, device="cuda:0")
+    zm = Zm.cpu().numpy().reshape(nr, N)
+    for k in range(nr):
+        (h.apply_transpose if trans else h.apply)(T(R[k]), Zs)
+        torch.cuda.synchronize()
+        assert np.array_equal(zm[k], Zs.cpu().numpy()), k
+    h.close()
+
+
+def test_multi_rhs_apply_matches_oracle(acr):
+    n, nr, eps = 16, 5, 1e-6
+    st, coef = _codi(acr, n)
+    N = n ** 3
+    R = np.stack([uniform_rhs(n, 60 + k) for k in range(nr)])
+    D, Ld, Ud = plane_blocks(st, n)
+    F = cr_setup(D, Ld, Ud, Structure(n, 2.0, 32), eps)
+    h = acr.Handle(n, coef, eps, 2.0, 32, 0, 48)
+    Z = torch.empty(nr * N, dtype=torch.float64, device="cuda:0")
+    h.apply(T(R.ravel()), Z, nrhs=nr)
+    torch.cuda.synchronize()
+    h.close()
+    z = Z.cpu().numpy().reshape(nr, N)
+    for k in range(nr):
+        assert rel(z[k], cr_apply(F, R[k])) <= 10 * max(1e-3 * eps, 1e-7)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_lockstep_gmres_helmholtz_32_rhs(acr, prec):
+    """The Helmholtz recipe's 32 right-hand sides at n = 32, solved together."""
+    n = 32
+    spec, sig, F = workload("helmholtz_n64", n=n)
+    nr, N = F.shape[0], n ** 3
+    assert nr == 32
+    A = stencil_matrix(stencil_helmholtz(sig, n), n)
+    coef = torch.empty(7 * N, dtype=torch.float64, device="cuda:0")
+    acr.acr_stencil_helmholtz(n, T(sig), coef)
+    h = acr.Handle(n, coef, spec["eps"], spec["eta"], 32, prec, 48)
+    U = torch.zeros(nr * N, dtype=torch.float64, device="cuda:0")
+    info, st = acr.acr_krylov_solve(h.h, coef, acr.ACR_GMRES, 30, spec["rtol"], 300,
+                                    T(F.ravel()), U, nrhs=nr)
+    torch.cuda.synchronize()
+    assert st == 0 and info.converged
+    u = U.cpu().numpy().reshape(nr, N)
+    lu = sla.splu(A.tocsc())
+    for k in range(nr):
+        assert rel(A @ u[k], F[k]) <= spec["rtol"] * 1.0001, k
+    # one-at-a-time solves of three of the systems agree
+    for k in (0, 13, 31):
+        uk = torch.zeros(N, dtype=torch.float64, device="cuda:0")
+        acr.acr_krylov_solve(h.h, coef, acr.ACR_GMRES, 30, spec["rtol"], 300, T(F[k]), uk)
+        ue = lu.solve(F[k])
+        assert rel(uk.cpu().numpy(), ue) <= 1e-4 and rel(u[k], ue) <= 1e-4
+    h.close()
+
+
+def test_lockstep_gmres_mixed_convergence(acr):
+    """A zero right-hand side and an easy one beside ordinary ones: the
+    converged systems are frozen and every system ends at its rtol."""
+    n = 16
+    st, coef = _codi(acr, n)
+    N = n ** 3
+    A = stencil_matrix(st, n)
+    F = np.stack([uniform_rhs(n, 70), np.zeros(N), uniform_rhs(n, 71)])
+    h = acr.Handle(n, coef, 1e-2, 2.0, 32, 1, 32)
+    U = torch.zeros(3 * N, dtype=torch.float64, device="cuda:0")
+    info, st_ = acr.acr_krylov_solve(h.h, coef, acr.ACR_GMRES, 30, 1e-10, 200, T(F.ravel()), U,
+                                     nrhs=3)
+    torch.cuda.synchronize()
+    h.close()
+    u = U.cpu().numpy().reshape(3, N)
+    assert st_ == 0
+    assert np.all(u[1] == 0.0)
+    for k in (0, 2):
+        assert rel(A @ u[k], F[k]) <= 1e-10 * 1.0001
