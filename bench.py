@@ -479,8 +479,8 @@ def main():
         e3.record(stream)
         torch.cuda.synchronize()
         acr.acr_destroy(hh)
-        batch = {"apply_n128_8rhs_ms": multi_ms, "apply_n128_ms_per_rhs": multi_ms / nr,
-                 "apply_n128_single_ms": apply_roof["ms"],
+        batch = {"apply_8rhs_ms": multi_ms, "apply_ms_per_rhs_of_8": multi_ms / nr,
+                 "apply_single_ms": apply_roof["ms"],
                  "helmholtz": {"workload": "helmholtz_n64 (8-layer medium, 10 points per "
                                            "wavelength, eps 1e-5, FP32 factors)",
                                "nrhs": nrh, "setup_s": e0.elapsed_time(e1) / 1000.0,
