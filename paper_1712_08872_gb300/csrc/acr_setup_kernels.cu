@@ -12,6 +12,8 @@
 //  * k_plane_dense / k_plane_lr -- H-format of a 7-point plane block.
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include <cstdint>
 
 #include "acr_internal.h"
@@ -64,7 +66,7 @@ constexpr int STAGE_BYTES = 36864;   // shared staging of one K-chunk (A and B p
 // spread their outputs over the threads and split each chunk's K across the
 // spare threads, reducing the partial sums in shared memory at the end.
 template <typename T, typename Acc>
-__global__ void __launch_bounds__(NT) k_ggemm(const GGroup* __restrict__ groups,
+__global__ void __launch_bounds__(NT, sizeof(Acc) == 4 ? 3 : 2) k_ggemm(const GGroup* __restrict__ groups,
                                               const GItem* __restrict__ items,
                                               T* const* __restrict__ tab,
                                               const int* const* __restrict__ rtab, int P,
@@ -85,8 +87,13 @@ __global__ void __launch_bounds__(NT) k_ggemm(const GGroup* __restrict__ groups,
   Acc* sm = reinterpret_cast<Acc*>(stage_raw);
   const Acc beta = G.beta >= 0 ? (Acc)coefs[G.beta] : Acc(0);
   const bool blocked = (m > 32 && n > 32);
-  const int lda_s = blocked ? TILE + 1 : m + 1;
-  const int ldb_s = blocked ? TILE + 1 : n + 1;
+  // tall thin tiles (16 < m <= 64, 8 < n <= 32): 4 x NB micro-tiles on 16 x 16
+  // threads over the whole K range (rows ty + 16 a, columns tx + 16 b,
+  // accumulator a * 2 + b: compile-time indices keep them in registers)
+  const int thinNB = (!blocked && m > 16 && n > 8 && n <= 32) ? (n > 16 ? 2 : 1) : 0;
+  const bool thin = thinNB > 0;
+  const int lda_s = (blocked || thin) ? TILE + 1 : m + 1;
+  const int ldb_s = blocked ? TILE + 1 : (thin ? 16 * thinNB + 1 : n + 1);
   const int KC = SE / (lda_s + ldb_s);
   Acc* As = sm;                 // As[kk * lda_s + i]
   Acc* Bs = sm + KC * lda_s;    // Bs[kk * ldb_s + j]
@@ -96,16 +103,33 @@ __global__ void __launch_bounds__(NT) k_ggemm(const GGroup* __restrict__ groups,
   const int nout = m * n;
   int OL = 1;
   while (OL < nout && OL < NT) OL <<= 1;
-  const int S = blocked ? 1 : NT / OL;
+  const int S = (blocked || thin) ? 1 : NT / OL;
   const int lane = threadIdx.x % OL, slice = threadIdx.x / OL;
   const int Q = (nout + OL - 1) / OL;
   Acc acc[16];
 #pragma unroll
   for (int q = 0; q < 16; ++q) acc[q] = Acc(0);
 
+  auto thin_loop = [&](auto nbc, int kfill) {
+    constexpr int NB = decltype(nbc)::value;
+    for (int kk = 0; kk < kfill; ++kk) {
+      Acc av[4], bv[NB];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) av[a] = As[kk * lda_s + ty + 16 * a];
+#pragma unroll
+      for (int b = 0; b < NB; ++b) bv[b] = Bs[kk * ldb_s + tx + 16 * b];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < NB; ++b) acc[a * 2 + b] += av[a] * bv[b];
+    }
+  };
   auto compute = [&](int kfill) {
     __syncthreads();
-    if (blocked) {
+    if (thin) {
+      if (thinNB == 2) thin_loop(std::integral_constant<int, 2>(), kfill);
+      else thin_loop(std::integral_constant<int, 1>(), kfill);
+    } else if (blocked) {
       for (int kk = 0; kk < kfill; ++kk) {
         Acc av[4], bv[4];
 #pragma unroll
@@ -158,7 +182,19 @@ __global__ void __launch_bounds__(NT) k_ggemm(const GGroup* __restrict__ groups,
       // C(r0+i, j) += cf * B(i, j)  or  cf * A(i, j): straight into the accumulators
       fl += (long long)rows * n;
       const bool ai = I.aflags & FL_IDENT;
-      if (blocked) {
+      if (thin) {
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          const int i = ty + 16 * a - r0;
+          if (i < 0 || i >= rows) continue;
+#pragma unroll
+          for (int b = 0; b < 2; ++b) {
+            const int j = tx + 16 * b;
+            if (b < thinNB && j < n)
+              acc[a * 2 + b] += cf * (ai ? (Acc)B[i + (int64_t)j * I.ldb] : (Acc)A[i + (int64_t)j * I.lda]);
+          }
+        }
+      } else if (blocked) {
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
           const int i = ty + 16 * a - r0;
@@ -269,7 +305,22 @@ __global__ void __launch_bounds__(NT) k_ggemm(const GGroup* __restrict__ groups,
   }
   if (kfill > 0) compute(kfill);
 
-  if (blocked) {
+  if (thin) {
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const int i = ty + 16 * a;
+      if (i >= m) continue;
+#pragma unroll
+      for (int b = 0; b < 2; ++b) {
+        const int j = tx + 16 * b;
+        if (b >= thinNB || j >= n) continue;
+        T* c = C + i + (int64_t)j * G.ldc;
+        Acc v = acc[a * 2 + b];
+        if (G.beta >= 0) v += beta * (Acc)(*c);
+        *c = (T)v;
+      }
+    }
+  } else if (blocked) {
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
       const int i = ty + 16 * a;
