@@ -178,6 +178,20 @@ acr_status acr_spmv(const acr_grid* grid, const double* coef, const double* x, d
 acr_status acr_setup(const acr_grid* grid, const double* coef, const acr_options* opt,
                      cudaStream_t stream, acr_handle** out);
 
+/* Autotuner of the leaf size n_min (the paper picks it by hand, Sec. 4.3;
+ * no counterpart there): for every candidate leaf size, build the
+ * factorisation of coef with opt (opt->leaf ignored) and solve one probe
+ * system A u = A 1 from u = 0 with `method` (GMRES(restart) or PCG) to
+ * rtol; time setup + solve with CUDA events on `stream`.  *best_leaf
+ * receives the fastest candidate, times_ms[i] (host, n_cand doubles) the
+ * time of cand[i] in ms, or -1 where that candidate failed (unsupported
+ * leaf, rank cap, no convergence in 1000 iterations).  Errors: INVALID_ARG;
+ * UNSUPPORTED if every candidate failed; OOM, CUDA. */
+acr_status acr_autotune_leaf(const acr_grid* grid, const double* coef, const acr_options* opt,
+                             int32_t method, int32_t restart, double rtol, const int32_t* cand,
+                             int32_t n_cand, int32_t* best_leaf, double* times_ms,
+                             cudaStream_t stream);
+
 /* a9-a10, Sec. 4.1 substitution: z = M^{-1} r, M the ACR factorisation;
  * forward then backward sweep of batched H-matrix-vector products.  r, z:
  * nrhs * N doubles (natural ordering); r is not modified; r == z is

@@ -12,6 +12,6 @@ from .acr import (  # noqa: F401
     acr_get_setup_info, acr_get_profile, acr_structure_query, ACR_FLAG_PROFILE,
     KernelStat, Profile, acr_destroy, acr_status_string, Handle, acr_launch_count,
     acr_krylov_solve_plain_noalloc, acr_noalloc_max_unknowns, acr_krylov_solve_transpose,
-    acr_spmv_transpose, acr_kappa_gradient, acr_stencil_helmholtz,
+    acr_spmv_transpose, acr_kappa_gradient, acr_stencil_helmholtz, acr_autotune_leaf,
 )
 from .autograd import ACRPoissonSolve, acr_poisson_solve  # noqa: F401

@@ -96,6 +96,9 @@ def load_library(path=LIB_PATH):
         "acr_krylov_solve_transpose": [_P, _P, I32, I32, F64, I32, _P, _P, I32,
                                        ctypes.POINTER(SolveInfo), _P],
         "acr_spmv_transpose": [ctypes.POINTER(Grid), _P, _P, _P, I32, _P],
+        "acr_autotune_leaf": [ctypes.POINTER(Grid), _P, ctypes.POINTER(Options), I32, I32, F64,
+                              ctypes.POINTER(I32), I32, ctypes.POINTER(I32),
+                              ctypes.POINTER(F64), _P],
         "acr_kappa_gradient": [ctypes.POINTER(Grid), _P, _P, _P, _P, _P],
         "acr_krylov_solve_plain_noalloc": [ctypes.POINTER(Grid), _P, F64, I32, _P, _P,
                                            ctypes.POINTER(SolveInfo), _P],
@@ -178,6 +181,22 @@ def acr_spmv_transpose(n, coef, x, y, nrhs=1, stream=None):
     _check(load_library().acr_spmv_transpose(ctypes.byref(_grid(n)), _dev(coef, 7 * N, "coef"),
                                               _dev(x, nrhs * N, "x"), _dev(y, nrhs * N, "y"),
                                               nrhs, _stream(stream)), "acr_spmv_transpose")
+
+
+def acr_autotune_leaf(n, coef, eps, eta, precision, rank_cap, method, restart, rtol,
+                      candidates=(32, 64), stream=None):
+    """Fastest leaf size among ``candidates`` by timed setup + probe solve.
+    Returns (best_leaf, [ms per candidate, -1 where it failed])."""
+    N = n ** 3
+    opt = Options(eps, eta, 0, precision, rank_cap, 0)
+    cand = (ctypes.c_int32 * len(candidates))(*candidates)
+    times = (ctypes.c_double * len(candidates))()
+    best = ctypes.c_int32(0)
+    _check(load_library().acr_autotune_leaf(ctypes.byref(_grid(n)), _dev(coef, 7 * N, "coef"),
+                                             ctypes.byref(opt), method, restart, rtol, cand,
+                                             len(candidates), ctypes.byref(best), times,
+                                             _stream(stream)), "acr_autotune_leaf")
+    return best.value, list(times)
 
 
 def acr_kappa_gradient(n, kappa, lam, u, grad, stream=None):

@@ -1760,4 +1760,57 @@ void acr_destroy(acr_handle* h) {
   delete h;
 }
 
+acr_status acr_autotune_leaf(const acr_grid* grid, const double* coef, const acr_options* opt,
+                             int32_t method, int32_t restart, double rtol, const int32_t* cand,
+                             int32_t n_cand, int32_t* best_leaf, double* times_ms,
+                             cudaStream_t stream) {
+  if (!grid_ok(grid) || !coef || !opt || !cand || n_cand < 1 || !best_leaf || !times_ms ||
+      !(rtol > 0.0) || (method != ACR_PCG && method != ACR_GMRES))
+    return ACR_ERR_INVALID_ARG;
+  const int64_t N = (int64_t)grid->nx * grid->nx * grid->nx;
+  double *ones = nullptr, *f = nullptr, *u = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  acr_status st = guarded([&] {
+    ones = (double*)acr::dmalloc(N * sizeof(double));
+    f = (double*)acr::dmalloc(N * sizeof(double));
+    u = (double*)acr::dmalloc(N * sizeof(double));
+    ACR_CUDA(cudaEventCreate(&e0));
+    ACR_CUDA(cudaEventCreate(&e1));
+    std::vector<double> h1((size_t)N, 1.0);
+    ACR_CUDA(cudaMemcpyAsync(ones, h1.data(), N * sizeof(double), cudaMemcpyHostToDevice, stream));
+    acr::launch_spmv(coef, ones, f, grid->nx, stream);     // probe right-hand side A 1
+    ACR_CUDA(cudaStreamSynchronize(stream));
+    return 0;
+  });
+  double best = -1.0;
+  for (int i = 0; i < n_cand && st == ACR_OK; ++i) {
+    times_ms[i] = -1.0;
+    acr_options o = *opt;
+    o.leaf = cand[i];
+    o.flags = 0;
+    acr_handle* h = nullptr;
+    if (cudaEventRecord(e0, stream) != cudaSuccess) { st = ACR_ERR_CUDA; break; }
+    acr_status s1 = acr_setup(grid, coef, &o, stream, &h);
+    if (s1 == ACR_ERR_CUDA || s1 == ACR_ERR_OOM) { st = s1; break; }
+    if (s1 != ACR_OK) continue;   // this leaf size is not usable here
+    cudaMemsetAsync(u, 0, N * sizeof(double), stream);
+    acr_solve_info info{};
+    acr_status s2 = acr_krylov_solve(h, coef, method, restart, rtol, 1000, f, u, 1, &info, stream);
+    cudaEventRecord(e1, stream);
+    cudaEventSynchronize(e1);
+    acr_destroy(h);
+    if (s2 == ACR_ERR_CUDA) { st = s2; break; }
+    if (s2 != ACR_OK) continue;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    times_ms[i] = ms;
+    if (best < 0.0 || ms < best) { best = ms; *best_leaf = cand[i]; }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(ones); cudaFree(f); cudaFree(u);
+  if (st == ACR_OK && best < 0.0) st = ACR_ERR_UNSUPPORTED;
+  return st;
+}
+
 }  // extern "C"

@@ -130,3 +130,14 @@ def test_lockstep_gmres_mixed_convergence(acr):
     assert np.all(u[1] == 0.0)
     for k in (0, 2):
         assert rel(A @ u[k], F[k]) <= 1e-10 * 1.0001
+
+
+def test_autotune_leaf_picks_the_fastest_candidate(acr):
+    n = 32
+    st, coef = _codi(acr, n)
+    best, times = acr.acr_autotune_leaf(n, coef, 1e-2, 2.0, acr.ACR_FP32, 32, acr.ACR_GMRES, 30,
+                                        1e-8, candidates=(16, 32, 64, 128))
+    assert best in (16, 32, 64)
+    ok = [t for t in times[:3] if t > 0]
+    assert len(ok) == 3 and times[(16, 32, 64).index(best)] == min(ok)
+    assert times[3] == -1.0          # leaves above 64 points are not supported
