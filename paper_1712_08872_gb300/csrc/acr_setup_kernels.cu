@@ -66,7 +66,7 @@ constexpr int STAGE_BYTES = 36864;   // shared staging of one K-chunk (A and B p
 // spread their outputs over the threads and split each chunk's K across the
 // spare threads, reducing the partial sums in shared memory at the end.
 template <typename T, typename Acc>
-__global__ void __launch_bounds__(NT, sizeof(Acc) == 4 ? 3 : 2) k_ggemm(const GGroup* __restrict__ groups,
+__global__ void __launch_bounds__(NT, sizeof(Acc) == 4 ? 4 : 2) k_ggemm(const GGroup* __restrict__ groups,
                                               const GItem* __restrict__ items,
                                               T* const* __restrict__ tab,
                                               const int* const* __restrict__ rtab, int P,
