@@ -498,7 +498,7 @@ __global__ void __launch_bounds__(NT) k_gdot(const GGroup* __restrict__ groups,
 // its group's output in 4 x 8 tiles with lanes striding the contraction;
 // no shared memory, no barriers.
 template <typename T, typename Acc>
-__global__ void __launch_bounds__(NT) k_gdot_warp(const GGroup* __restrict__ groups,
+__global__ void __launch_bounds__(NT, sizeof(Acc) == 4 ? 4 : 1) k_gdot_warp(const GGroup* __restrict__ groups,
                                                   const GItem* __restrict__ items,
                                                   T* const* __restrict__ tab,
                                                   const int* const* __restrict__ rtab, int P,
