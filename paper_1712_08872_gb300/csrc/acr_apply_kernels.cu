@@ -181,22 +181,29 @@ __global__ void __launch_bounds__(256) k_hmv_rows(MatvecDev mv, T* const* __rest
       s_off[q] = trans ? mv.lr_col0[l] * kc + mv.lt_coloff[l0 + q]
                        : mv.lr_row0[l] * kc + mv.l_rowoff[l0 + q];
     }
-    for (int e = threadIdx.x; e < R * xstride; e += 256) {
-      const int rr = R == 1 ? 0 : e / xstride, e1 = e - rr * xstride;
-      const int q = e1 / lsz, j = e1 - q * lsz;
-      xs[e] = (Acc)xp[rr * vs + dcol[d0 + q] + j];
+    // each staged entry resolves its indices once and serves all R vectors
+    for (int e = threadIdx.x; e < xstride; e += 256) {
+      const int q = e / lsz, j = e - q * lsz;
+      const double* src = xp + dcol[d0 + q] + j;
+#pragma unroll
+      for (int rr = 0; rr < R; ++rr) xs[rr * xstride + e] = (Acc)src[rr * vs];
     }
     const int* sptr = trans ? mv.segt_ptr : mv.seg_ptr;
     const int nseg = trans ? mv.nsegt : mv.nseg;
-    for (int e = threadIdx.x; e < R * tstride; e += 256) {
-      const int rr = R == 1 ? 0 : e / tstride, e1 = e - rr * tstride;
-      const int q = e1 / kc, j = e1 - q * kc;
+    for (int e = threadIdx.x; e < tstride; e += 256) {
+      const int q = e / kc, j = e - q * kc;
       const int l = lleaf[l0 + q];
-      double v = 0.0;
+      double v[R];
+#pragma unroll
+      for (int rr = 0; rr < R; ++rr) v[rr] = 0.0;
       if (j < rank[p][l])
-        for (int sg = sptr[l]; sg < sptr[l + 1]; ++sg)
-          v += tv[rr * tvs + ((int64_t)p * nseg + sg) * kc + j];
-      ts[e] = (Acc)v;
+        for (int sg = sptr[l]; sg < sptr[l + 1]; ++sg) {
+          const double* src = tv + ((int64_t)p * nseg + sg) * kc + j;
+#pragma unroll
+          for (int rr = 0; rr < R; ++rr) v[rr] += src[rr * tvs];
+        }
+#pragma unroll
+      for (int rr = 0; rr < R; ++rr) ts[rr * tstride + e] = (Acc)v[rr];
     }
   }
   __syncthreads();

@@ -622,13 +622,11 @@ void Engine<T>::setup(const double* coef, cudaStream_t st) {
   mvd.lr_row0 = sd.row0;
   mvd.lr_col0 = sd.col0;
   mvd.nchunks = S.nleafcl; mvd.lsz = S.lsz; mvd.nl = sd.nl; mvd.kc = kc;
-  mvd.max_d = mvd.max_l = mvd.max_lr_rows = 0;
+  mvd.max_d = mvd.max_l = 0;
   for (int c = 0; c < S.nleafcl; ++c) {
     mvd.max_d = std::max({mvd.max_d, mvp.d_ptr[c + 1] - mvp.d_ptr[c], mvp.dt_ptr[c + 1] - mvp.dt_ptr[c]});
     mvd.max_l = std::max({mvd.max_l, mvp.l_ptr[c + 1] - mvp.l_ptr[c], mvp.lt_ptr[c + 1] - mvp.lt_ptr[c]});
   }
-  for (size_t l = 0; l < mvp.lr_m.size(); ++l)
-    mvd.max_lr_rows = std::max({mvd.max_lr_rows, mvp.lr_m[l], mvp.lr_n[l]});
   mvd.seg_ptr = (const int32_t*)upload(mvp.seg_ptr, owned);
   mvd.segt_ptr = (const int32_t*)upload(mvp.segt_ptr, owned);
   mvd.nseg = mvp.seg_ptr.back();

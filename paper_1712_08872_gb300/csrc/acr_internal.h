@@ -99,7 +99,6 @@ struct MatvecDev {
   const int64_t *lr_row0, *lr_col0;
   int nchunks, lsz, nl, kc;
   int max_d, max_l;      // most dense / low-rank leaves of one row (or column) chunk
-  int max_lr_rows;       // largest row or column count of a low-rank leaf
   // projection segments: leaf l's V rows (transposed: U rows) in leaf-size
   // pieces, numbered seg_ptr[l] + piece
   const int32_t *seg_ptr, *segt_ptr;
