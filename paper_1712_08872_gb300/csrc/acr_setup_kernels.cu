@@ -1096,7 +1096,10 @@ void launch_ggemm(const Plan& pl, int gbeg, int gend, T* const* d_tab, const int
     dim3 grid(std::min(maxg, ng - g0), P);
     const GGroup* gr = (const GGroup*)pl.d_groups;
     const GItem* it = (const GItem*)pl.d_items;
-    if (tag == TAG_M || tag == TAG_S || tag == TAG_P) {
+    // warp per group for the inner products, and for the small-output
+    // sketch / projection stages where the multiply type is float (the FP64
+    // instance of the warp kernel holds ~200 registers: one CTA per SM)
+    if (tag == TAG_M || (sizeof(T) == 4 && (tag == TAG_S || tag == TAG_P))) {
       const int cnt = std::min(maxg, ng - g0);
       dim3 gw((cnt + NT / 32 - 1) / (NT / 32), P);
       k_gdot_warp<T, Acc><<<gw, NT, 0, st>>>(gr, it, d_tab, d_rtab, P, gbeg + g0, gbeg + g0 + cnt,
