@@ -69,7 +69,15 @@ def test_paper_128_plane_eta_256_is_weak_admissibility():
     assert weak.blocks[(c1, c2)] == "L"
 
 
-def test_survey_counts_small_case():
+def test_block_counts_n16_eta1_leaf32_by_hand():
+    """n=16, eta=1, leaf 32: bisection gives 8 leaf clusters of 4 x 8 points
+    (x 0-3, 4-7, 8-11, 12-15; y 0-7, 8-15).  No pair of the coarser
+    clusters is admissible (neighbours, or 8 x 8 quarters only h*sqrt(2)
+    apart against a diameter of 7*sqrt(2) h).  Among leaf pairs only the two
+    outer x-columns are admissible: box distance 9h against a diameter of
+    sqrt(3^2 + 7^2) h = 7.6h; columns one apart (5h) or adjacent are not.
+    That is 2 columns x 2 x 2 row choices = 8 low-rank leaves, and the other
+    64 - 8 = 56 leaf pairs are dense."""
     st = Structure(16, 1.0, 32)
     kinds = [k for _, _, k in st.leaves()]
     assert kinds.count("D") == 56 and kinds.count("L") == 8
