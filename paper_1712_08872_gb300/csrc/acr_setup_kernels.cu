@@ -788,7 +788,10 @@ __global__ void __launch_bounds__(NT) k_eig(const TInfo* __restrict__ tis, int t
     double offs = 0, tots = 0;
     for (int w = 0; w < NT / 32; ++w) { offs += red[w]; tots += red[NT / 32 + w]; }
     __syncthreads();
-    if (offs <= 1e-30 * tots || r == 1) break;
+    // converged once the off-diagonal mass is below the storage precision's
+    // need: eigenvectors to ~1e-15 (FP64 factors) or ~1e-8 (float factors)
+    const double conv = sizeof(T) == 8 ? 1e-30 : 1e-16;
+    if (offs <= conv * tots || r == 1) break;
     ++sweeps_done;
     for (int round = 0; round < nn - 1; ++round) {
       // circle method: player 0 fixed, others rotate
