@@ -226,7 +226,7 @@ acr_status acr_krylov_solve(acr_handle* h, const double* coef, int32_t method, i
  * paper has no counterpart): the same Krylov iteration with the transposed
  * 7-point operator and the transposed preconditioner M^{-T}
  * (acr_apply_transpose).  Arguments, results and errors as
- * acr_krylov_solve. */
+ * acr_krylov_solve, except that nrhs must be 1. */
 acr_status acr_krylov_solve_transpose(acr_handle* h, const double* coef, int32_t method,
                                       int32_t restart, double rtol, int32_t maxit,
                                       const double* f, double* u, int32_t nrhs,
