@@ -12,8 +12,8 @@
 // multi-RHS apply multiplies each loaded entry into all R vectors, which sit
 // vs doubles apart); the vectors are FP64.  FP64 factors accumulate in FP64;
 // FP32 and BF16 factors multiply in FP32 and add short FP32 partial sums (at
-// most 16 products) into FP64 accumulators, keeping the slow FP64 pipe off
-// the per-entry path.
+// most 16 products) into a compensated float pair (row kernel) or FP64
+// (projections), keeping the slow FP64 pipe off the per-entry path.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -33,6 +33,28 @@ __device__ __forceinline__ float ld(__nv_bfloat16 v) { return __bfloat162float(v
 template <typename T>
 using AccT = typename std::conditional<std::is_same<T, double>::value, double, float>::type;
 
+// Running sum of float partials as an unevaluated pair hi + lo (TwoSum,
+// Knuth): about 48 significant bits on the FP32 pipe, where a double
+// accumulator would send every addition and conversion to the slow FP64
+// pipe.  For double the pair degenerates to one double.
+template <typename A>
+struct RunSum {
+  double s = 0.0;
+  __device__ __forceinline__ void add(double v) { s += v; }
+  __device__ __forceinline__ double value() const { return s; }
+};
+template <>
+struct RunSum<float> {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add(float v) {
+    const float t = hi + v;
+    const float bp = t - hi;
+    lo += (hi - (t - bp)) + (v - bp);
+    hi = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
 constexpr int MAXQ = 256;   // most low-rank leaves covering one chunk
 
 // Partial projections, one CTA per (leaf-size column chunk c, plane p): for
@@ -47,7 +69,7 @@ __global__ void __launch_bounds__(256) k_lr_proj(MatvecDev mv, T* const* __restr
                                                  T* const* __restrict__ V,
                                                  const int* const* __restrict__ rank,
                                                  const double* const* __restrict__ x, double* tv,
-                                                 bool trans, int64_t vs, int64_t tvs) {
+                                                 bool trans, int64_t vs) {
   using Acc = AccT<T>;
   __shared__ Acc xs[R][64];
   __shared__ int64_t s_off[MAXQ];
@@ -124,7 +146,7 @@ __global__ void __launch_bounds__(256) k_lr_proj(MatvecDev mv, T* const* __restr
     for (int rr = 0; rr < R; ++rr) {
 #pragma unroll
       for (int o = 4; o > 0; o >>= 1) d[rr] += __shfl_xor_sync(0xffffffffu, d[rr], o);
-      if (t < total && r == 0) tv[rr * tvs + ((int64_t)p * nseg + s_seg[q]) * kc + j] = d[rr];
+      if (t < total && r == 0) tv[(((int64_t)p * nseg + s_seg[q]) * kc + j) * R + rr] = d[rr];
     }
   }
 }
@@ -147,7 +169,7 @@ __global__ void __launch_bounds__(256) k_hmv_rows(MatvecDev mv, T* const* __rest
                                                   const double* const* __restrict__ x,
                                                   double* const* __restrict__ y, double alpha,
                                                   double beta, const double* __restrict__ tv,
-                                                  bool trans, int64_t vs, int64_t tvs) {
+                                                  bool trans, int64_t vs) {
   using Acc = AccT<T>;
   extern __shared__ __align__(16) unsigned char smraw[];
   Acc* xs = reinterpret_cast<Acc*>(smraw);
@@ -198,18 +220,16 @@ __global__ void __launch_bounds__(256) k_hmv_rows(MatvecDev mv, T* const* __rest
       for (int rr = 0; rr < R; ++rr) v[rr] = 0.0;
       if (j < rank[p][l])
         for (int sg = sptr[l]; sg < sptr[l + 1]; ++sg) {
-          const double* src = tv + ((int64_t)p * nseg + sg) * kc + j;
+          const double* src = tv + (((int64_t)p * nseg + sg) * kc + j) * R;
 #pragma unroll
-          for (int rr = 0; rr < R; ++rr) v[rr] += src[rr * tvs];
+          for (int rr = 0; rr < R; ++rr) v[rr] += src[rr];
         }
 #pragma unroll
       for (int rr = 0; rr < R; ++rr) ts[rr * tstride + e] = (Acc)v[rr];
     }
   }
   __syncthreads();
-  double acc[R];
-#pragma unroll
-  for (int rr = 0; rr < R; ++rr) acc[rr] = 0.0;
+  RunSum<Acc> acc[R];
   if (have && i < lsz) {
     const T* Dp = D[p];
     for (int q = 0; q < nd; ++q) {
@@ -234,7 +254,7 @@ __global__ void __launch_bounds__(256) k_hmv_rows(MatvecDev mv, T* const* __rest
         }
       }
 #pragma unroll
-      for (int rr = 0; rr < R; ++rr) acc[rr] += (double)sp[rr];
+      for (int rr = 0; rr < R; ++rr) acc[rr].add(sp[rr]);
     }
     // low-rank leaves: thread group g takes leaves g, g+4, ...; all of a
     // leaf's columns, partial sums of at most 16 products
@@ -263,12 +283,12 @@ __global__ void __launch_bounds__(256) k_hmv_rows(MatvecDev mv, T* const* __rest
           for (int rr = 0; rr < R; ++rr) sp[rr] += f * tq[rr * tstride + j];
         }
 #pragma unroll
-        for (int rr = 0; rr < R; ++rr) acc[rr] += (double)sp[rr];
+        for (int rr = 0; rr < R; ++rr) acc[rr].add(sp[rr]);
       }
     }
   }
 #pragma unroll
-  for (int rr = 0; rr < R; ++rr) part[rr][g][i] = acc[rr];
+  for (int rr = 0; rr < R; ++rr) part[rr][g][i] = acc[rr].value();
   __syncthreads();
   for (int e = threadIdx.x; e < R * 64; e += 256) {
     const int rr = e >> 6, ii = e & 63;
@@ -345,7 +365,7 @@ template <typename T, int R>
 static void hmatvec_r(const MatvecDev& mv, T* const* dense, T* const* U, T* const* V,
                       const int* const* rank, const double* const* x, double* const* y,
                       double alpha, double beta, bool trans, double* tv, int P, int64_t vs,
-                      int64_t tvs, cudaStream_t st) {
+                      cudaStream_t st) {
   using Acc = AccT<T>;
   const size_t sm_rows =
       ((size_t)mv.max_d * mv.lsz + (size_t)mv.max_l * mv.kc) * R * sizeof(Acc);
@@ -362,13 +382,13 @@ static void hmatvec_r(const MatvecDev& mv, T* const* dense, T* const* U, T* cons
   if (sm_rows > 180 * 1024)
     throw CudaError{cudaErrorInvalidConfiguration, "apply staging exceeds shared memory"};
   if (mv.nl > 0)
-    k_lr_proj<T, R><<<dim3(mv.nchunks, P), 256, 0, st>>>(mv, U, V, rank, x, tv, trans, vs, tvs);
+    k_lr_proj<T, R><<<dim3(mv.nchunks, P), 256, 0, st>>>(mv, U, V, rank, x, tv, trans, vs);
   if (mv.lsz == 64)
     k_hmv_rows<T, 64, R><<<dim3(mv.nchunks, P), 256, sm_rows, st>>>(
-        mv, dense, U, V, rank, x, y, alpha, beta, tv, trans, vs, tvs);
+        mv, dense, U, V, rank, x, y, alpha, beta, tv, trans, vs);
   else
     k_hmv_rows<T, 0, R><<<dim3(mv.nchunks, P), 256, sm_rows, st>>>(
-        mv, dense, U, V, rank, x, y, alpha, beta, tv, trans, vs, tvs);
+        mv, dense, U, V, rank, x, y, alpha, beta, tv, trans, vs);
   ACR_LAUNCHED(mv.nl > 0 ? 2 : 1);
 }
 
@@ -376,13 +396,13 @@ template <typename T>
 void launch_hmatvec(const MatvecDev& mv, T* const* dense, T* const* U, T* const* V,
                     const int* const* rank, const double* const* x, double* const* y,
                     double alpha, double beta, bool trans, double* tv, int P, int nr,
-                    int64_t vs, int64_t tvs, cudaStream_t st) {
+                    int64_t vs, cudaStream_t st) {
   if (P <= 0) return;
   switch (nr) {
-    case 1: hmatvec_r<T, 1>(mv, dense, U, V, rank, x, y, alpha, beta, trans, tv, P, vs, tvs, st); break;
-    case 2: hmatvec_r<T, 2>(mv, dense, U, V, rank, x, y, alpha, beta, trans, tv, P, vs, tvs, st); break;
-    case 4: hmatvec_r<T, 4>(mv, dense, U, V, rank, x, y, alpha, beta, trans, tv, P, vs, tvs, st); break;
-    case 8: hmatvec_r<T, 8>(mv, dense, U, V, rank, x, y, alpha, beta, trans, tv, P, vs, tvs, st); break;
+    case 1: hmatvec_r<T, 1>(mv, dense, U, V, rank, x, y, alpha, beta, trans, tv, P, vs, st); break;
+    case 2: hmatvec_r<T, 2>(mv, dense, U, V, rank, x, y, alpha, beta, trans, tv, P, vs, st); break;
+    case 4: hmatvec_r<T, 4>(mv, dense, U, V, rank, x, y, alpha, beta, trans, tv, P, vs, st); break;
+    case 8: hmatvec_r<T, 8>(mv, dense, U, V, rank, x, y, alpha, beta, trans, tv, P, vs, st); break;
     default: throw CudaError{cudaErrorInvalidValue, "right-hand-side group must be 1, 2, 4 or 8"};
   }
 }
@@ -415,7 +435,7 @@ void launch_copy_planes(double* const* dst, const double* const* src, int n2, in
 #define ACR_HMV_INST(T)                                                                     \
   template void launch_hmatvec<T>(const MatvecDev&, T* const*, T* const*, T* const*,           \
                                   const int* const*, const double* const*, double* const*,     \
-                                  double, double, bool, double*, int, int, int64_t, int64_t,   \
+                                  double, double, bool, double*, int, int, int64_t,            \
                                   cudaStream_t);
 ACR_HMV_INST(double)
 ACR_HMV_INST(float)

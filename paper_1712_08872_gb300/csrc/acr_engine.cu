@@ -1054,12 +1054,12 @@ void Engine<T>::run_steps(const std::vector<ApplyStep>& steps, int nr, cudaStrea
       launch_hmatvec<B>(mvd, (B* const*)t, (B* const*)(t + P), (B* const*)(t + 2 * P),
                         (const int* const*)(t + 3 * P), (const double* const*)(t + 4 * P),
                         (double* const*)(t + 5 * P), s.alpha, s.beta, s.trans, tvscr, P, nr, N,
-                        tvs, st);
+                        st);
     } else if (s.kind == 0) {
       launch_hmatvec<T>(mvd, (T* const*)t, (T* const*)(t + P), (T* const*)(t + 2 * P),
                         (const int* const*)(t + 3 * P), (const double* const*)(t + 4 * P),
                         (double* const*)(t + 5 * P), s.alpha, s.beta, s.trans, tvscr, P, nr, N,
-                        tvs, st);
+                        st);
     } else if (s.kind == 1) {
       launch_diag_update((double* const*)t, (const double* const*)(t + P),
                          (const double* const*)(t + 2 * P), (const double* const*)(t + 3 * P),

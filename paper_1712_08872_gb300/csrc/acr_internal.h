@@ -107,13 +107,14 @@ struct MatvecDev {
 
 // y_p = beta*y_p + alpha*op(H_p) x_p for P planes and nr (1, 2, 4 or 8)
 // right-hand sides; op = H or H^T.  Right-hand side r of plane p lives at
-// x[p] + r*vs (y likewise).  tv: scratch of nr blocks of tvs >=
-// P*max(nseg,nsegt)*kc doubles.  A null H_p sets y_p = beta*y_p.
+// x[p] + r*vs (y likewise).  tv: scratch of P*max(nseg,nsegt)*kc*nr
+// doubles (projections, right-hand side innermost).  A null H_p sets
+// y_p = beta*y_p.
 template <typename T>
 void launch_hmatvec(const MatvecDev& mv, T* const* dense, T* const* U, T* const* V,
                     const int* const* rank, const double* const* x, double* const* y,
                     double alpha, double beta, bool trans, double* tv, int P, int nr,
-                    int64_t vs, int64_t tvs, cudaStream_t st);
+                    int64_t vs, cudaStream_t st);
 
 // out[e] = bfloat16(in[e]) (round to nearest even), e < count; out is __nv_bfloat16*
 void launch_to_bf16(const float* in, void* out, int64_t count, cudaStream_t st);
