@@ -9,7 +9,8 @@
 //   A * I = A,   I * B = B,   A * G (G block diagonal),
 //   C - T1 - T2 (a formatted sum),
 // and two independent operations merged into one plan give the results of
-// running them apart.  Prints one line per case; exits 1 on a failure.
+// running them apart.  The apply's index lists (MatvecPlan) reproduce H x and
+// H^T x.  Prints one line per case; exits 1 on a failure.
 // Test infrastructure only: the GPU path never runs this.
 #include <algorithm>
 #include <cmath>
@@ -328,6 +329,61 @@ void report(const char* name, double err, double tol) {
   if (!ok) fail = true;
 }
 
+// y = H x (H^T x when trans) through the apply's index lists: per
+// leaf-size chunk the dense leaves of its block row (column) and the
+// low-rank leaves covering it, with every low-rank projection assembled
+// from per-chunk segment partials numbered seg_ptr[l] + offset / lsz --
+// the bookkeeping the GPU projection and row kernels follow.
+std::vector<double> list_matvec(const MatvecPlan& mv, const HMat& h, const std::vector<double>& x,
+                                bool trans) {
+  const int lsz = S.lsz, nc = S.nleafcl;
+  const auto& sptr = trans ? mv.segt_ptr : mv.seg_ptr;
+  std::vector<double> seg((size_t)sptr.back() * kc, 0.0);
+  const auto& pptr = trans ? mv.l_ptr : mv.lt_ptr;       // chunks the projections read
+  const auto& pleaf = trans ? mv.l_leaf : mv.lt_leaf;
+  const auto& poff = trans ? mv.l_rowoff : mv.lt_coloff;
+  for (int c = 0; c < nc; ++c)
+    for (int q = pptr[c]; q < pptr[c + 1]; ++q) {
+      const int l = pleaf[q];
+      const int rows = trans ? mv.lr_m[l] : mv.lr_n[l];
+      const double* F = trans ? &h.U[S.lr_row0[l] * kc] : &h.V[S.lr_col0[l] * kc];
+      const int sg = sptr[l] + poff[q] / lsz;
+      for (int j = 0; j < h.rank[l]; ++j) {
+        double s = 0.0;
+        for (int i = 0; i < lsz; ++i) s += F[poff[q] + i + (int64_t)j * rows] * x[(size_t)c * lsz + i];
+        seg[(size_t)sg * kc + j] = s;
+      }
+    }
+  const auto& dptr = trans ? mv.dt_ptr : mv.d_ptr;
+  const auto& dleaf = trans ? mv.dt_leaf : mv.d_leaf;
+  const auto& dcol = trans ? mv.dt_row : mv.d_col;
+  const auto& lptr = trans ? mv.lt_ptr : mv.l_ptr;
+  const auto& lleaf = trans ? mv.lt_leaf : mv.l_leaf;
+  const auto& loff = trans ? mv.lt_coloff : mv.l_rowoff;
+  std::vector<double> y((size_t)nc * lsz, 0.0);
+  for (int c = 0; c < nc; ++c)
+    for (int i = 0; i < lsz; ++i) {
+      double s = 0.0;
+      for (int e = dptr[c]; e < dptr[c + 1]; ++e) {
+        const double* blk = &h.d[(size_t)dleaf[e] * lsz * lsz];
+        for (int j = 0; j < lsz; ++j)
+          s += (trans ? blk[j + (size_t)i * lsz] : blk[i + (size_t)j * lsz]) * x[dcol[e] + j];
+      }
+      for (int e = lptr[c]; e < lptr[c + 1]; ++e) {
+        const int l = lleaf[e];
+        const int ld = trans ? mv.lr_n[l] : mv.lr_m[l];
+        const double* F = trans ? &h.V[S.lr_col0[l] * kc] : &h.U[S.lr_row0[l] * kc];
+        for (int j = 0; j < h.rank[l]; ++j) {
+          double t = 0.0;
+          for (int sg = sptr[l]; sg < sptr[l + 1]; ++sg) t += seg[(size_t)sg * kc + j];
+          s += F[loff[e] + i + (int64_t)j * ld] * t;
+        }
+      }
+      y[(size_t)c * lsz + i] = s;
+    }
+  return y;
+}
+
 OpDesc product_op(int cnode, int crole, int anode, int arole, int bnode, int brole) {
   OpDesc op;
   op.c_node = cnode; op.c_role = crole; op.alpha = -1; op.nroles = 3;
@@ -407,6 +463,24 @@ int main(int argc, char** argv) {
       std::printf("merging did not share stages\n");
       fail = true;
     }
+  }
+  {
+    // the apply's lists: H x and H^T x against the dense matrix
+    MatvecPlan mv;
+    mv.build(S);
+    HMat H = random_h(3);
+    const std::vector<double> Hd = to_dense(H);
+    const int N = S.n * S.n;
+    std::vector<double> x(N);
+    for (double& v : x) v = rnd();
+    std::vector<double> want(N, 0.0), wantT(N, 0.0);
+    for (int i = 0; i < N; ++i)
+      for (int j = 0; j < N; ++j) {
+        want[i] += Hd[(size_t)i * N + j] * x[j];
+        wantT[j] += Hd[(size_t)i * N + j] * x[i];
+      }
+    report("apply lists: H x", rel(list_matvec(mv, H, x, false), want), 1e-13);
+    report("apply lists: H^T x", rel(list_matvec(mv, H, x, true), wantT), 1e-13);
   }
   return fail ? 1 : 0;
 }
