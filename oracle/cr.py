@@ -33,12 +33,20 @@ updates are evaluated as
     T_a = [L_j X_a],  T_b = [U_j X_b]
     D_j <- [D_j - T_a U_a - T_b L_b],  L_j <- [-T_a L_a],  U_j <- [-T_b U_b].
 
+The transposed apply z = M^{-T} y (the adjoint of the substitution, used by
+adjoint solves) runs the statements of the substitution in reverse order,
+each replaced by its transpose: a statement ``b = C a`` becomes
+``abar += C^T bbar`` (and ``bbar`` is consumed when b was assigned rather
+than updated).
+
 Parity: exact CR is pinned against dense LU / numpy.linalg.solve and DST-I
-(tests/test_oracle_cr.py); ACR at eps -> 0 is pinned to the exact solve.
+(tests/test_oracle_cr.py); ACR at eps -> 0 is pinned to the exact solve; the
+transposed apply is pinned to the explicit transpose of the matrix whose
+columns are cr_apply of the unit vectors.
 """
 import numpy as np
 
-from .hformat import fmt, hinv
+from .hformat import fmt, hinv, mm, rnd, sub
 
 
 def levels(n):
@@ -53,17 +61,18 @@ def levels(n):
     return out
 
 
-def _lmul(c, M):
-    """coupling c times matrix M (c is None, a diagonal vector or a matrix)."""
+def _lmul(c, M, arith=None):
+    """coupling c times matrix M (c is None, a diagonal vector or a matrix);
+    a diagonal scaling is exact in FP64, a matrix product runs in ``arith``."""
     if isinstance(c, np.ndarray) and c.ndim == 1:
         return c[:, None] * M
-    return c @ M
+    return mm(c, M, arith)
 
 
-def _rmul(M, c):
+def _rmul(M, c, arith=None):
     if isinstance(c, np.ndarray) and c.ndim == 1:
         return M * c[None, :]
-    return M @ c
+    return mm(M, c, arith)
 
 
 def _cvec(c, v):
@@ -84,17 +93,22 @@ class CRFactors:
         self.ranks = []        # (what, level, plane, {(t,s): rank})
 
 
-def cr_setup(D, Ld, Ud, st=None, eps=None):
+def cr_setup(D, Ld, Ud, st=None, eps=None, arith=None):
     """Elimination.  D: list of n dense plane blocks (natural in-plane
     order); Ld, Ud: diagonal couplings.  With ``st`` and ``eps`` the blocks
-    are held in H-format (ACR); otherwise the elimination is exact."""
+    are held in H-format (ACR); otherwise the elimination is exact.
+    ``arith`` (H-format only): the arithmetic model of oracle.hformat --
+    float32 products and sums, stored blocks rounded to float32, FP64
+    truncation SVDs and leaf inverses; the first level's diagonal couplings
+    stay FP64 and its scalings are exact before the result is stored."""
     n = len(D)
     F = CRFactors(n)
     hmode = st is not None
+    ar = arith if hmode else None
     if hmode:
         p = np.asarray(st.perm)
         F.perm = p
-        D = [fmt(Dk[np.ix_(p, p)], st, 0, 0, eps) for Dk in D]
+        D = [fmt(Dk[np.ix_(p, p)], st, 0, 0, eps, arith=ar) for Dk in D]
         L = [Lk[p].copy() for Lk in Ld]
         U = [Uk[p].copy() for Uk in Ud]
     else:
@@ -106,11 +120,11 @@ def cr_setup(D, Ld, Ud, st=None, eps=None):
 
     def inv(M):
         if hmode:
-            return hinv(M, st, eps)
+            return hinv(M, st, eps, arith=ar)
         return np.linalg.inv(M)
 
     def f(M):
-        return fmt(M, st, 0, 0, eps) if hmode else M
+        return fmt(M, st, 0, 0, eps, arith=ar) if hmode else M
 
     for r, (s, red, black) in enumerate(levels(n)):
         lev = dict(s=s, red=red, black=black, X={}, L={}, U={})
@@ -127,25 +141,25 @@ def cr_setup(D, Ld, Ud, st=None, eps=None):
             newL = newU = None
             if r == 0:
                 if Xa is not None:
-                    newD -= _rmul(_lmul(L[j], Xa), U[a])
+                    newD = sub(newD, rnd(_rmul(_lmul(L[j], Xa), U[a]), ar), ar)
                     if L[a] is not None:
-                        newL = -_rmul(_lmul(L[j], Xa), L[a])
+                        newL = rnd(-_rmul(_lmul(L[j], Xa), L[a]), ar)
                 if Xb is not None:
-                    newD -= _rmul(_lmul(U[j], Xb), L[b])
+                    newD = sub(newD, rnd(_rmul(_lmul(U[j], Xb), L[b]), ar), ar)
                     if U[b] is not None:
-                        newU = -_rmul(_lmul(U[j], Xb), U[b])
+                        newU = rnd(-_rmul(_lmul(U[j], Xb), U[b]), ar)
                 D[j] = f(newD)
             else:
-                Ta = f(_lmul(L[j], Xa)) if Xa is not None else None
-                Tb = f(_lmul(U[j], Xb)) if Xb is not None else None
+                Ta = f(_lmul(L[j], Xa, ar)) if Xa is not None else None
+                Tb = f(_lmul(U[j], Xb, ar)) if Xb is not None else None
                 if Ta is not None:
-                    newD -= _rmul(Ta, U[a])
+                    newD = sub(newD, _rmul(Ta, U[a], ar), ar)
                     if L[a] is not None:
-                        newL = f(-_rmul(Ta, L[a]))
+                        newL = f(-_rmul(Ta, L[a], ar))
                 if Tb is not None:
-                    newD -= _rmul(Tb, L[b])
+                    newD = sub(newD, _rmul(Tb, L[b], ar), ar)
                     if U[b] is not None:
-                        newU = f(-_rmul(Tb, U[b]))
+                        newU = f(-_rmul(Tb, U[b], ar))
                 D[j] = f(newD)
             L[j], U[j] = newL, newU
         F.levels.append(lev)
@@ -187,5 +201,54 @@ def cr_apply(F, r):
     if F.perm is not None:
         res = np.empty_like(out)
         res[:, F.perm] = out
+        out = res
+    return out.ravel()
+
+
+def _tvec(c, v):
+    """c^T v for a coupling c (diagonal vector or matrix)."""
+    if isinstance(c, np.ndarray) and c.ndim == 1:
+        return c * v
+    return c.T @ v
+
+
+def cr_apply_transpose(F, y):
+    """z = M^{-T} y: the substitution of ``cr_apply`` transposed statement by
+    statement, in reverse order (see header)."""
+    n = F.n
+    Y = np.asarray(y, dtype=np.float64).reshape(n, -1)
+    m = Y.shape[1]
+    if F.perm is not None:
+        Y = Y[:, F.perm]                      # adjoint of the output un-permutation
+    ubar = [Y[k].copy() for k in range(n)]
+    gbar = {}
+    # backward sweep, transposed: levels fine to coarse
+    for lev in F.levels:
+        s = lev["s"]
+        for i in lev["red"]:
+            gbar[i] = ubar[i].copy()          # u_i = g_i - X_i (...)
+            t = -(lev["X"][i].T @ ubar[i])
+            if lev["L"][i] is not None:
+                ubar[i - s] = ubar[i - s] + _tvec(lev["L"][i], t)
+            if i + s < n and lev["U"][i] is not None:
+                ubar[i + s] = ubar[i + s] + _tvec(lev["U"][i], t)
+            ubar[i] = np.zeros(m)
+    fbar = [np.zeros(m) for _ in range(n)]
+    fbar[0] = F.X0.T @ ubar[0]                # u_0 = X_0 f_0
+    # forward sweep, transposed: levels coarse to fine, black updates first
+    for lev in reversed(F.levels):
+        s = lev["s"]
+        for j in lev["black"]:
+            a, b = j - s, j + s
+            if a >= 0 and lev["L"][j] is not None:
+                gbar[a] = gbar[a] - _tvec(lev["L"][j], fbar[j])
+            if b < n and lev["U"][j] is not None:
+                gbar[b] = gbar[b] - _tvec(lev["U"][j], fbar[j])
+        for i in lev["red"]:
+            fbar[i] = fbar[i] + lev["X"][i].T @ gbar[i]   # g_i = X_i f_i
+    out = np.stack(fbar)
+    if F.perm is not None:
+        res = np.empty_like(out)
+        res[:, F.perm] = out                  # adjoint of the input permutation
         out = res
     return out.ravel()

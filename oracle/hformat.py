@@ -22,13 +22,49 @@ formatted operation its plain definition:
   where [.] is a formatted result.  A leaf diagonal block is inverted densely
   by LU with partial pivoting (LAPACK getrf/getri through numpy).
 
+``arith`` (all functions; default FP64, the definition above) models the
+reduced-precision forms of the device path, which the paper does not have:
+with ``arith=numpy.float32`` every product of the formatted operations is
+computed in float32 arithmetic (float32 operands, float32 accumulation),
+every sum in float32, and every stored block (formatted result, leaf
+inverse) is rounded to float32; truncation SVDs and leaf inverses are still
+computed in FP64 from the float data.  It measures the accuracy that float
+arithmetic itself allows on a given problem.
+
 Parity: pinned by tests/test_oracle_hformat.py (constructed spectra,
 Eckart-Young bound, eps -> 0 equals the exact inverse, admissibility
-structure of the paper's 128^2 example).
+structure of the paper's 128^2 example); the float32 model by storage
+round-trips and the eps -> 0 limit within float32 rounding
+(tests/test_oracle_cr.py).
 """
 import numpy as np
 
 from .hstructure import Structure  # noqa: F401
+
+
+def _f64(arith):
+    return arith is None or np.dtype(arith) == np.float64
+
+
+def rnd(M, arith=None):
+    """M rounded to the precision ``arith`` (identity for FP64)."""
+    if _f64(arith):
+        return M
+    return np.asarray(M).astype(arith).astype(np.float64)
+
+
+def mm(a, b, arith=None):
+    """a @ b in the arithmetic ``arith`` (float32: operands and accumulation)."""
+    if _f64(arith):
+        return a @ b
+    return (np.asarray(a).astype(arith) @ np.asarray(b).astype(arith)).astype(np.float64)
+
+
+def sub(a, b, arith=None):
+    """a - b in the arithmetic ``arith``."""
+    if _f64(arith):
+        return a - b
+    return (np.asarray(a).astype(arith) - np.asarray(b).astype(arith)).astype(np.float64)
 
 
 def truncate_block(B, eps):
@@ -42,11 +78,11 @@ def truncate_block(B, eps):
     return (u[:, :k] * s[:k]) @ vt[:k], k
 
 
-def fmt(M, st, t, s, eps, ranks=None):
+def fmt(M, st, t, s, eps, ranks=None, arith=None):
     """Project dense block M (rows = cluster t, cols = cluster s, cluster
     order) onto the block tree rooted at (t, s).  Returns a new array; if
     ``ranks`` is a dict, the rank of every admissible leaf is recorded in it
-    under its (t, s) key."""
+    under its (t, s) key.  The result is stored in precision ``arith``."""
     out = np.array(M, dtype=np.float64, copy=True)
     rt, rs = st.clusters[t].begin, st.clusters[s].begin
     for a, b, kind in st.leaves(t, s):
@@ -58,26 +94,27 @@ def fmt(M, st, t, s, eps, ranks=None):
         out[ra, rb], k = truncate_block(out[ra, rb], eps)
         if ranks is not None:
             ranks[(a, b)] = k
-    return out
+    return rnd(out, arith)
 
 
-def hinv(A, st, eps, t=0):
+def hinv(A, st, eps, t=0, arith=None):
     """H-inverse of the formatted diagonal block A on cluster t (see header)."""
     c = st.clusters[t]
     if not c.children:
-        return np.linalg.inv(A)
+        return rnd(np.linalg.inv(A), arith)
     t1, t2 = c.children
     m1 = st.clusters[t1].size
     A11, A12 = A[:m1, :m1], A[:m1, m1:]
     A21, A22 = A[m1:, :m1], A[m1:, m1:]
-    X11 = hinv(A11, st, eps, t1)
-    T12 = fmt(X11 @ A12, st, t1, t2, eps)
-    T21 = fmt(A21 @ X11, st, t2, t1, eps)
-    S = fmt(A22 - A21 @ T12, st, t2, t2, eps)
-    X22 = hinv(S, st, eps, t2)
-    X12 = fmt(-(T12 @ X22), st, t1, t2, eps)
-    X21 = fmt(-(X22 @ T21), st, t2, t1, eps)
-    X11 = fmt(X11 - X12 @ T21, st, t1, t1, eps)
+    ar = arith
+    X11 = hinv(A11, st, eps, t1, ar)
+    T12 = fmt(mm(X11, A12, ar), st, t1, t2, eps, arith=ar)
+    T21 = fmt(mm(A21, X11, ar), st, t2, t1, eps, arith=ar)
+    S = fmt(sub(A22, mm(A21, T12, ar), ar), st, t2, t2, eps, arith=ar)
+    X22 = hinv(S, st, eps, t2, ar)
+    X12 = fmt(-mm(T12, X22, ar), st, t1, t2, eps, arith=ar)
+    X21 = fmt(-mm(X22, T21, ar), st, t2, t1, eps, arith=ar)
+    X11 = fmt(sub(X11, mm(X12, T21, ar), ar), st, t1, t1, eps, arith=ar)
     return np.block([[X11, X12], [X21, X22]])
 
 

@@ -101,3 +101,53 @@ def test_acr_error_shrinks_with_eps():
     errs = [np.linalg.norm(cr_apply(cr_setup(D, Ld, Ud, S, e), f) - ue)
             for e in (1e-1, 1e-3, 1e-6)]
     assert errs[0] > errs[1] > errs[2]
+
+
+@pytest.mark.parametrize("kind,n,hmode", [("codi", 8, True), ("codi", 6, False),
+                                          ("helmholtz", 5, False), ("poisson", 7, True)])
+def test_transposed_apply_equals_explicit_transpose(kind, n, hmode):
+    """cr_apply_transpose(F, y) equals (M^-1)^T y, M^-1 assembled column by
+    column from cr_apply of the unit vectors (ACR factors with truncation,
+    and exact CR, including non-powers of two)."""
+    from oracle.cr import cr_apply_transpose
+    st, _ = _problem(kind, n, 3)
+    D, Ld, Ud = plane_blocks(st, n)
+    if hmode:
+        F = cr_setup(D, Ld, Ud, Structure(n, 2.0, 8), 1e-3)
+    else:
+        F = cr_setup(D, Ld, Ud)
+    N = n ** 3
+    Minv = np.stack([cr_apply(F, e) for e in np.eye(N)], axis=1)
+    y = uniform_rhs(n, 9)
+    want = Minv.T @ y
+    got = cr_apply_transpose(F, y)
+    assert np.linalg.norm(got - want) <= 1e-12 * np.linalg.norm(want)
+    # and it is not the plain apply (convection makes M^-1 nonsymmetric)
+    if kind == "codi":
+        assert np.linalg.norm(cr_apply(F, y) - want) > 1e-6 * np.linalg.norm(want)
+
+
+def test_float32_arithmetic_model():
+    """The float32 arithmetic model of cr_setup(arith=float32): every stored
+    H-matrix block is a float32 value; at eps -> 0 the apply still equals the
+    direct solve, to float32 accuracy (not better: the model is in effect,
+    not worse: nothing else changed); arith=float64 is the FP64 definition."""
+    n = 8
+    st, A = _problem("poisson", n, 2)
+    D, Ld, Ud = plane_blocks(st, n)
+    S = Structure(n, 2.0, 8)
+    F32 = cr_setup(D, Ld, Ud, S, 1e-12, arith=np.float32)
+    for lev in F32.levels:
+        for d in ("X", "L", "U"):
+            for M in lev[d].values():
+                if M is not None and M.ndim == 2:
+                    assert np.array_equal(M.astype(np.float32).astype(np.float64), M)
+    assert np.array_equal(F32.X0.astype(np.float32).astype(np.float64), F32.X0)
+    f = uniform_rhs(n, 3)
+    ue = np.linalg.solve(A.toarray(), f)
+    e32 = np.linalg.norm(cr_apply(F32, f) - ue) / np.linalg.norm(ue)
+    assert 1e-9 < e32 < 1e-4, e32
+    F64 = cr_setup(D, Ld, Ud, S, 1e-12, arith=np.float64)
+    F0 = cr_setup(D, Ld, Ud, S, 1e-12)
+    assert np.array_equal(cr_apply(F64, f), cr_apply(F0, f))
+    assert np.linalg.norm(cr_apply(F0, f) - ue) <= 1e-10 * np.linalg.norm(ue)
