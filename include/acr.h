@@ -101,6 +101,11 @@ typedef struct {
                                 reads (dense leaves, U and V up to their ranks, couplings) plus
                                 its FP64 vector traffic */
   int64_t apply_flops;       /* multiply-adds x 2 of one acr_apply */
+  int64_t lr_truncations;    /* low-rank blocks the setup recompressed (all planes, all steps) */
+  int64_t sketch_overflows;  /* of those, blocks whose stacked rank (sum of the ranks of the
+                                terms summed into the block) exceeded the sketch width
+                                min(rank_cap + 8, 64): their range finder was a randomized
+                                approximation instead of exact */
 } acr_setup_info;
 
 /* Per-kernel-class setup statistics (ACR_FLAG_PROFILE).  flops counts the
@@ -261,18 +266,76 @@ acr_status acr_krylov_solve_plain(const acr_grid* grid, const double* coef, int3
  * that the library defines at file scope; each GPU that loads the library
  * holds that array until the process exits.  Grids with more than
  * acr_noalloc_max_unknowns() unknowns (about 6.2e5, n <= 85) are rejected
- * with ACR_ERR_INVALID_ARG.  The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress); make that first call
- * before any stream capture.  Every call shares the one array and keeps
- * the previous call's contents; calls that overlap on the GPU (other
- * streams, other host threads) race with each other.  The call reads a
- * few scalars back per iteration and synchronises `stream`. */
+ * with ACR_ERR_INVALID_ARG.  Every call looks up the array's device address
+ * in the current device's context (cudaGetSymbolAddress; the first call in
+ * a context also loads the library's device code there): make the first
+ * call on a device before any stream capture.  Every call shares the one
+ * array and keeps the previous call's contents; calls that overlap on the
+ * GPU (other streams, other host threads) race with each other.  The call
+ * reads a few scalars back per iteration and synchronises `stream`.
+ * info->solve_ms is HOST wall time of the call here (the allocating
+ * variant reports CUDA-event time); acr_alloc_count() does not change
+ * across a call. */
 acr_status acr_krylov_solve_plain_noalloc(const acr_grid* grid, const double* coef, double rtol,
                                           int32_t maxit, const double* f, double* u,
                                           acr_solve_info* info, cudaStream_t stream);
 
 /* Largest number of unknowns acr_krylov_solve_plain_noalloc accepts. */
 int64_t acr_noalloc_max_unknowns(void);
+
+/* ---- Batches (Sec. 5.1-5.2 run the planes of a CR level in parallel; a
+ * batch extends that data parallelism across independent problems, which the
+ * paper does not do).  `count` problems, problem i on an n[i]^3 grid with the
+ * 7-point operator coefs[i] (device, 7*n[i]^3 doubles, stencil layout above),
+ * all with the options *opt.  Problems of equal n share every launch of the
+ * setup (their planes are processed as one batch per CR level) and every
+ * launch of the apply; problems of different n run on concurrent stream
+ * branches.  All device memory is allocated here, sized by a counting pass of
+ * the setup: refactoring and applying allocate nothing and synchronise
+ * nothing, so they can be captured in a CUDA graph.  The batch keeps the
+ * coefs pointers: acr_batch_refactor re-reads them, and they must stay valid
+ * (and the caller may overwrite their contents between refactorisations).
+ * Batch vectors hold the problems back to back in batch order (n[0]^3
+ * doubles, then n[1]^3, ...).  Errors: INVALID_ARG, UNSUPPORTED, OOM, CUDA,
+ * BREAKDOWN, RANK_CAP (*out is NULL then).  acr_batch_create synchronises
+ * `stream`. */
+typedef struct acr_batch acr_batch;
+acr_status acr_batch_create(int32_t count, const int32_t* n, const double* const* coefs,
+                            const acr_options* opt, cudaStream_t stream, acr_batch** out);
+
+/* Queue a new factorisation of every problem from the current contents of
+ * its coefficient array (no allocation, no synchronisation).  Device errors
+ * (pivot breakdown, rank cap) surface at the next acr_batch_status. */
+acr_status acr_batch_refactor(acr_batch* b, cudaStream_t stream);
+
+/* Synchronise `stream` and report the device error state of the last
+ * factorisation (OK, BREAKDOWN, RANK_CAP, TIMEOUT). */
+acr_status acr_batch_status(acr_batch* b, cudaStream_t stream);
+
+/* z_i = M_i^{-1} r_i for every problem i (batch vectors, device). */
+acr_status acr_batch_apply(acr_batch* b, const double* r, double* z, cudaStream_t stream);
+
+/* Capture acr_batch_refactor followed by acr_batch_apply(r -> z) into a CUDA
+ * graph owned by the batch (replacing an earlier one).  r and z (batch
+ * vectors) and the coefficient arrays must stay valid while the graph is
+ * used.  `stream` must not be the legacy default stream. */
+acr_status acr_batch_capture(acr_batch* b, const double* r, double* z, cudaStream_t stream);
+
+/* Launch the captured graph on `stream` (INVALID_ARG if none was captured). */
+acr_status acr_batch_replay(acr_batch* b, cudaStream_t stream);
+
+/* Krylov solve (as acr_krylov_solve, one right-hand side) of problem i with
+ * its own preconditioner M_i; coef, f, u are problem i's arrays. */
+acr_status acr_batch_krylov_solve(acr_batch* b, int32_t i, const double* coef, int32_t method,
+                                  int32_t restart, double rtol, int32_t maxit, const double* f,
+                                  double* u, acr_solve_info* info, cudaStream_t stream);
+
+/* Setup statistics of the size class of problem i (all problems of that n
+ * together, as of acr_batch_create). */
+acr_status acr_batch_get_info(const acr_batch* b, int32_t i, acr_setup_info* info);
+
+/* Release a batch, its graph and all its device memory (NULL is a no-op). */
+void acr_batch_destroy(acr_batch* b);
 
 /* Setup statistics of a handle (host struct). */
 acr_status acr_get_setup_info(const acr_handle* h, acr_setup_info* info);
@@ -294,6 +357,11 @@ acr_status acr_structure_query(int32_t n, double eta, int32_t leaf, int64_t* cou
 /* Number of CUDA kernels this library has launched in the process so far
  * (all handles, all threads); for accounting in benchmarks. */
 int64_t acr_launch_count(void);
+
+/* Number of device (cudaMalloc) and pinned host (cudaMallocHost) allocations
+ * this library has made in the process so far; for checking which calls
+ * allocate. */
+int64_t acr_alloc_count(void);
 
 /* Release a handle and all its device memory (NULL is a no-op). */
 void acr_destroy(acr_handle* h);

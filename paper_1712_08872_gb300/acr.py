@@ -45,7 +45,8 @@ class SetupInfo(ctypes.Structure):
                 ("factor_capacity_bytes", ctypes.c_int64), ("n_dense_leaves", ctypes.c_int32),
                 ("n_lowrank_leaves", ctypes.c_int32), ("setup_ms", ctypes.c_double),
                 ("structure_ms", ctypes.c_double), ("apply_bytes", ctypes.c_int64),
-                ("apply_flops", ctypes.c_int64)]
+                ("apply_flops", ctypes.c_int64), ("lr_truncations", ctypes.c_int64),
+                ("sketch_overflows", ctypes.c_int64)]
 
 
 class KernelStat(ctypes.Structure):
@@ -112,8 +113,29 @@ def load_library(path=LIB_PATH):
         fn.restype = ctypes.c_int
     lib.acr_noalloc_max_unknowns.argtypes = []
     lib.acr_noalloc_max_unknowns.restype = ctypes.c_int64
+    lib.acr_batch_create.argtypes = [ctypes.c_int32, _P, _P, ctypes.POINTER(Options), _P,
+                                     ctypes.POINTER(_P)]
+    lib.acr_batch_create.restype = ctypes.c_int
+    for name in ("acr_batch_refactor", "acr_batch_status"):
+        getattr(lib, name).argtypes = [_P, _P]
+        getattr(lib, name).restype = ctypes.c_int
+    for name in ("acr_batch_apply", "acr_batch_capture"):
+        getattr(lib, name).argtypes = [_P, _P, _P, _P]
+        getattr(lib, name).restype = ctypes.c_int
+    lib.acr_batch_replay.argtypes = [_P, _P]
+    lib.acr_batch_replay.restype = ctypes.c_int
+    lib.acr_batch_krylov_solve.argtypes = [_P, ctypes.c_int32, _P, ctypes.c_int32, ctypes.c_int32,
+                                           ctypes.c_double, ctypes.c_int32, _P, _P,
+                                           ctypes.POINTER(SolveInfo), _P]
+    lib.acr_batch_krylov_solve.restype = ctypes.c_int
+    lib.acr_batch_get_info.argtypes = [_P, ctypes.c_int32, ctypes.POINTER(SetupInfo)]
+    lib.acr_batch_get_info.restype = ctypes.c_int
+    lib.acr_batch_destroy.argtypes = [_P]
+    lib.acr_batch_destroy.restype = None
     lib.acr_launch_count.argtypes = []
     lib.acr_launch_count.restype = ctypes.c_int64
+    lib.acr_alloc_count.argtypes = []
+    lib.acr_alloc_count.restype = ctypes.c_int64
     lib.acr_destroy.argtypes = [_P]
     lib.acr_destroy.restype = None
     lib.acr_status_string.argtypes = [ctypes.c_int]
@@ -309,6 +331,10 @@ def acr_launch_count():
     return int(load_library().acr_launch_count())
 
 
+def acr_alloc_count():
+    return int(load_library().acr_alloc_count())
+
+
 def acr_destroy(handle):
     if handle:
         load_library().acr_destroy(_P(handle))
@@ -349,3 +375,67 @@ class Handle:
             self.close()
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------- batches
+def acr_batch_create(ns, coefs, eps, eta, leaf, precision=ACR_FP32, rank_cap=0, stream=None):
+    """Batched setup of len(ns) problems (see include/acr.h); ``coefs`` are
+    CUDA float64 tensors of 7 n^3 entries that must outlive the batch.
+    Returns an opaque batch pointer (int)."""
+    cnt = len(ns)
+    nn = (ctypes.c_int32 * cnt)(*ns)
+    ptrs = (_P * cnt)(*[_dev(c, 7 * n ** 3, "coef") for c, n in zip(coefs, ns)])
+    opt = Options(eps, eta, leaf, precision, rank_cap, 0)
+    b = _P()
+    _check(load_library().acr_batch_create(cnt, nn, ptrs, ctypes.byref(opt), _stream(stream),
+                                            ctypes.byref(b)), "acr_batch_create")
+    return b.value
+
+
+def acr_batch_refactor(batch, stream=None):
+    _check(load_library().acr_batch_refactor(_P(batch), _stream(stream)), "acr_batch_refactor")
+
+
+def acr_batch_status(batch, stream=None, check=True):
+    st = load_library().acr_batch_status(_P(batch), _stream(stream))
+    if check:
+        _check(st, "acr_batch_status")
+    return st
+
+
+def acr_batch_apply(batch, r, z, stream=None):
+    _check(load_library().acr_batch_apply(_P(batch), _dev(r, None, "r"), _dev(z, None, "z"),
+                                           _stream(stream)), "acr_batch_apply")
+
+
+def acr_batch_capture(batch, r, z, stream):
+    _check(load_library().acr_batch_capture(_P(batch), _dev(r, None, "r"), _dev(z, None, "z"),
+                                             _stream(stream)), "acr_batch_capture")
+
+
+def acr_batch_replay(batch, stream):
+    _check(load_library().acr_batch_replay(_P(batch), _stream(stream)), "acr_batch_replay")
+
+
+def acr_batch_krylov_solve(batch, i, coef, method, restart, rtol, maxit, f, u, stream=None,
+                           check=True):
+    info = SolveInfo()
+    st = load_library().acr_batch_krylov_solve(_P(batch), i, _dev(coef, None, "coef"), method,
+                                               restart, rtol, maxit, _dev(f, None, "f"),
+                                               _dev(u, None, "u"), ctypes.byref(info),
+                                               _stream(stream))
+    if check:
+        _check(st, "acr_batch_krylov_solve")
+    return info, st
+
+
+def acr_batch_get_info(batch, i):
+    info = SetupInfo()
+    _check(load_library().acr_batch_get_info(_P(batch), i, ctypes.byref(info)),
+           "acr_batch_get_info")
+    return info
+
+
+def acr_batch_destroy(batch):
+    if batch:
+        load_library().acr_batch_destroy(_P(batch))

@@ -32,6 +32,8 @@ namespace acr {
 
 static std::atomic<int64_t> g_launches{0};
 void count_launches(int64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+static std::atomic<int64_t> g_allocs{0};
+void count_allocs(int64_t k) { g_allocs.fetch_add(k, std::memory_order_relaxed); }
 
 namespace {
 
@@ -48,6 +50,7 @@ struct DevBuf {
 void* dmalloc(size_t bytes) {
   if (bytes == 0) bytes = 16;
   void* p = nullptr;
+  count_allocs(1);
   cudaError_t e = cudaMalloc(&p, bytes);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -64,26 +67,40 @@ void* upload(const std::vector<V>& v, std::vector<void*>& owned) {
   return p;
 }
 
-// pinned host -> device ring for per-launch pointer tables
+// pinned host -> device ring for the setup's per-launch pointer tables.  A
+// counting pass sizes it (no copies); the real pass then never wraps, so it
+// needs no synchronisation and its copies can be captured in a CUDA graph
+// (the host side stays untouched afterwards).
 struct TableRing {
   char* host = nullptr;
   char* dev = nullptr;
   size_t cap = 0, off = 0;
+  bool counting = false;
+  bool fixed = false;   // sized by a counting pass: never wraps
   void init(size_t c) {
-    cap = c;
+    release();
+    cap = std::max<size_t>(c, 256);
+    count_allocs(1);
     ACR_CUDA(cudaMallocHost(&host, cap));
     dev = (char*)dmalloc(cap);
+    off = 0;
   }
   void release() {
     if (host) cudaFreeHost(host);
     if (dev) cudaFree(dev);
     host = dev = nullptr;
+    cap = off = 0;
   }
   void* push(const void* data, size_t bytes, cudaStream_t st) {
-    size_t b = (bytes + 255) & ~size_t(255);
-    if (b > cap) throw AcrError{S_OOM, "pointer table larger than staging ring"};
+    const size_t b = (bytes + 255) & ~size_t(255);
+    if (counting) {
+      off += b;
+      return reinterpret_cast<void*>(uintptr_t(1) << 44);   // never dereferenced
+    }
+    if (b > cap) throw AcrError{S_OOM, "pointer table larger than the staging ring"};
     if (off + b > cap) {
-      ACR_CUDA(cudaStreamSynchronize(st));
+      if (fixed) throw AcrError{S_OOM, "setup pointer tables exceed their sized ring"};
+      ACR_CUDA(cudaStreamSynchronize(st));   // earlier copies out of the ring are done
       off = 0;
     }
     std::memcpy(host + off, data, bytes);
@@ -101,6 +118,7 @@ struct HM {
   void* U = nullptr;
   void* V = nullptr;
   int* rank = nullptr;
+  int slot = -1;                     // arena slot (-1: not allocated)
 };
 
 class EngineBase {
@@ -116,26 +134,119 @@ class EngineBase {
   int64_t N = 0;
 };
 
+// Fixed-size H-matrix storage slots in slabs of device memory.  Every
+// H-matrix of an engine has the same layout, so a slot index is all the
+// allocator tracks; take / give are host bookkeeping in a deterministic
+// (LIFO) order, and stream order makes a slot given back reusable by later
+// launches without a synchronisation.  Slabs are allocated on demand (a
+// one-shot setup), or all at once after a counting pass has run the same
+// sequence with fake addresses (a batch, whose later refactorisations must
+// not allocate).
+struct SlotPool {
+  std::vector<char*> slabs;
+  int per_slab = 8;
+  bool fixed = false;                // every slab allocated up front: no growth
+  size_t slot_bytes = 0, off_u = 0, off_v = 0, off_r = 0;
+  int hw = 0;
+  std::vector<int> free_;
+  void layout(size_t dense_b, size_t u_b, size_t v_b, size_t rank_b) {
+    auto up = [](size_t x) { return (x + 255) & ~size_t(255); };
+    off_u = up(dense_b);
+    off_v = off_u + up(u_b);
+    off_r = off_v + up(v_b);
+    slot_bytes = off_r + up(rank_b);
+    per_slab = (int)std::max<size_t>(1, std::min<size_t>(16, (size_t(1) << 30) / slot_bytes));
+  }
+  // dry: a counting pass (no memory)
+  int take(bool dry) {
+    int q;
+    if (!free_.empty()) {
+      q = free_.back();
+      free_.pop_back();
+    } else {
+      q = hw++;
+    }
+    if (!dry) reserve(q + 1);
+    return q;
+  }
+  void reserve(int nslots) {
+    while ((int)slabs.size() * per_slab < nslots) {
+      if (fixed) throw AcrError{S_OOM, "H-matrix slots exceed their counted need"};
+      slabs.push_back((char*)dmalloc((size_t)per_slab * slot_bytes));
+    }
+  }
+  void give(int q) { free_.push_back(q); }
+  void restart() { free_.clear(); hw = 0; }
+  HM at(int q, bool dry) const {
+    char* p = dry ? reinterpret_cast<char*>(uintptr_t(1) << 45) + (size_t)q * slot_bytes
+                  : slabs[q / per_slab] + (size_t)(q % per_slab) * slot_bytes;
+    HM h;
+    h.dense = p; h.U = p + off_u; h.V = p + off_v; h.rank = (int*)(p + off_r); h.slot = q;
+    return h;
+  }
+  void release() {
+    for (char* p : slabs) cudaFree(p);
+    slabs.clear();
+  }
+};
+
 template <typename T>
 class Engine : public EngineBase {
  public:
-  Engine(int n_, double eps_, double eta_, int leaf_, int kc_, int flags_, bool bf16_ = false)
-      : eps(eps_), eta(eta_), leaf(leaf_), kc(kc_), bf16(bf16_ && std::is_same<T, float>::value) {
+  // count independent problems of the same size share every launch (their
+  // planes are batched together; plane slot = instance * n + plane)
+  Engine(int n_, double eps_, double eta_, int leaf_, int kc_, int flags_, bool bf16_ = false,
+         int count_ = 1)
+      : eps(eps_), eta(eta_), leaf(leaf_), kc(kc_), bf16(bf16_ && std::is_same<T, float>::value),
+        count(count_) {
     profiling = (flags_ & ACR_FLAG_PROFILE) != 0;
     n = n_;
     n2 = n * n;
     N = (int64_t)n2 * n;
+    vs = N * count;
   }
   ~Engine() override { release(); }
 
-  void setup(const double* coef, cudaStream_t st) override;
+  // one-shot setup of a single problem: prepare + execute + finish
+  void setup(const double* coef, cudaStream_t st) override {
+    const double* c[1] = {coef};
+    setup_multi(c, st, true);
+  }
+  void setup_multi(const double* const* coefs, cudaStream_t st, bool one_shot);
+  // host phase: structure and device tables; with count_pass also every
+  // plan and, by a counting pass, every allocation the setup makes (then
+  // execute allocates nothing and synchronises nothing)
+  void prepare(const double* const* coefs, cudaStream_t st, bool count_pass);
+  // device phase: only launches, asynchronous copies and memsets on st
+  // (no allocation, no synchronisation: capturable in a CUDA graph)
+  void execute(cudaStream_t st);
+  // execute between the two events that time the setup
+  void execute_timed(cudaStream_t st) {
+    ACR_CUDA(cudaEventRecord(ev0, st));
+    execute(st);
+    ACR_CUDA(cudaEventRecord(ev1, st));
+  }
+  // synchronise, check the device error word, statistics, apply program
+  void finish(cudaStream_t st, bool one_shot);
   void apply(const double* r, double* z, bool trans, cudaStream_t st, int nrhs = 1) override;
+  // z_i = M_i^-1 r_i for instance i alone (N doubles each)
+  void apply_instance(int i, const double* r, double* z, bool trans, cudaStream_t st);
+  // every instance at once, instance i's vectors at r[i], z[i] (N doubles
+  // each): the substitution steps are shared, only the reorderings are not
+  void apply_gather(const double* const* r, double* const* z, cudaStream_t st);
+  int instances() const { return count; }
+  // device error word -> status (synchronises st)
+  void check_err(cudaStream_t st);
 
  private:
   double eps, eta;
   int leaf, kc;
   bool bf16;                         // stored factors rounded to bfloat16 after the setup
+  int count = 1;
   int n2 = 0;
+  int64_t vs = 0;                    // doubles between right-hand sides in the work vectors
+  bool dry = false;                  // counting pass: no device work
+  std::vector<const double*> coef_in;
   size_t store_bytes() const { return bf16 ? 2 : sizeof(T); }
   Structure S;
   StructDev sd;
@@ -144,14 +255,16 @@ class Engine : public EngineBase {
   PlanParams pp{};
   std::map<std::vector<int>, std::unique_ptr<Plan>> plans;
   std::vector<void*> owned;          // structure / plan / table arrays
-  std::vector<HM> D;                 // plane blocks (X in place after inversion)
-  std::vector<HM> heap;              // every H-matrix allocated (for release)
-  double* Ld = nullptr;              // level-0 couplings, cluster order
+  std::vector<HM> D;                 // plane blocks (X in place after inversion), count * n
+  SlotPool pool, pool_b;             // T-typed H-matrices; bfloat16 copies (BF16 form)
+  bool counted = false;              // prepared by a counting pass (no allocation later)
+  std::vector<HM> live_b;            // BF16 form: the converted H-matrices
+  double* Ld = nullptr;              // level-0 couplings, cluster order, count * N
   double* Ud = nullptr;
   struct Level {
     int s;
-    std::vector<int> red, black;
-    std::vector<HM> L, U;            // per plane index (n entries), r >= 1
+    std::vector<int> red, black;     // plane slots
+    std::vector<HM> L, U;            // per plane slot, r >= 1
   };
   std::vector<Level> levels;
   TableRing ring;
@@ -159,10 +272,14 @@ class Engine : public EngineBase {
   size_t scratch_bytes = 0;
   int* scratch_ranks = nullptr;
   size_t scratch_rank_cnt = 0;
+  size_t scratch_need = 0, scratch_rank_need = 0;
   size_t scratch_budget = 0;
   double* d_coefs = nullptr;
   int* d_err = nullptr;
+  unsigned long long* d_sketch_stat = nullptr;   // truncated targets, stacked-rank overflows
   int* d_planes_all = nullptr;
+  bool has_cpl = false;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   // apply work
   double *Fv = nullptr, *Gv = nullptr, *Uv = nullptr, *Tv = nullptr, *tvscr = nullptr;
   struct ApplyStep {
@@ -172,9 +289,16 @@ class Engine : public EngineBase {
     double alpha, beta, sgn;
     void** tabs;                     // device table block
   };
-  std::vector<ApplyStep> fwd_steps, bwd_steps, fwdT_steps, bwdT_steps;
+  struct Program { std::vector<ApplyStep> fwd, bwd, fwdT, bwdT; };
+  Program prog_all;                  // every instance at once
+  std::vector<Program> prog_inst;    // one instance (count > 1)
   int maxP = 1;
   std::map<const void*, int64_t> hm_used;   // stored entries an apply reads per H-matrix
+
+  int inst_of(int slot) const { return slot / n; }
+  int plane_of(int slot) const { return slot % n; }
+  bool has_lo(int slot, int s) const { return plane_of(slot) - s >= 0; }
+  bool has_hi(int slot, int s) const { return plane_of(slot) + s < n; }
 
   // ---- optional per-kernel-class profile (CUDA events around launches)
   cudaStream_t cur_st = 0;
@@ -195,6 +319,7 @@ class Engine : public EngineBase {
   double* fl(int cls) { return profiling ? d_fl + cls : nullptr; }
   template <class F>
   void timed(int cls, F&& f, int tag = -1) {
+    if (dry) return;
     if (!profiling) { f(); return; }
     Pend pd{cls, ev(), ev(), tag};
     ACR_CUDA(cudaEventRecord(pd.a, cur_st));
@@ -219,70 +344,75 @@ class Engine : public EngineBase {
     pend.clear();
   }
 
-  HM alloc_hm() {
-    HM h;
-    size_t dn = (size_t)S.dleaf.size() * S.lsz * S.lsz;
-    size_t un = (size_t)S.sumM * kc, vn = (size_t)S.sumN * kc;
-    h.dense = dmalloc(std::max<size_t>(dn, 1) * sizeof(T));
-    h.U = dmalloc(std::max<size_t>(un, 1) * sizeof(T));
-    h.V = dmalloc(std::max<size_t>(vn, 1) * sizeof(T));
-    h.rank = (int*)dmalloc(std::max<size_t>(S.lleaf.size(), 1) * sizeof(int));
-    ACR_CUDA(cudaMemset(h.rank, 0, std::max<size_t>(S.lleaf.size(), 1) * sizeof(int)));
-    heap.push_back(h);
+  // fake address of the counting pass (never dereferenced)
+  static char* fake_base() { return reinterpret_cast<char*>(uintptr_t(1) << 45); }
+  HM alloc_hm(cudaStream_t st) {
+    const int q = pool.take(dry);
+    HM h = pool.at(q, dry);
+    if (!dry)
+      ACR_CUDA(cudaMemsetAsync(h.rank, 0, std::max<size_t>(S.lleaf.size(), 1) * sizeof(int), st));
     return h;
   }
   void free_hm(HM& h) {
-    for (auto it = heap.begin(); it != heap.end(); ++it)
-      if (it->dense == h.dense) { heap.erase(it); break; }
-    cudaFree(h.dense); cudaFree(h.U); cudaFree(h.V); cudaFree(h.rank);
+    if (h.slot >= 0) pool.give(h.slot);
     h = HM();
   }
-  // BF16 form: round every H-matrix still held after the setup (the stored
-  // factors) to bfloat16, replacing its dense / U / V arrays
+  // BF16 form: round every H-matrix held after the setup (the stored
+  // factors) to bfloat16 in the second arena; the references move to it
   void convert_bf16(cudaStream_t st) {
+    std::vector<int> live;
+    auto note = [&](const HM& r) {
+      if (r.slot >= 0 && std::find(live.begin(), live.end(), r.slot) == live.end())
+        live.push_back(r.slot);
+    };
+    for (const HM& r : D) note(r);
+    for (const Level& lev : levels) {
+      for (const HM& r : lev.L) note(r);
+      for (const HM& r : lev.U) note(r);
+    }
+    std::sort(live.begin(), live.end());
     const size_t dn = std::max<size_t>((size_t)S.dleaf.size() * S.lsz * S.lsz, 1);
     const size_t un = std::max<size_t>((size_t)S.sumM * kc, 1);
     const size_t vn = std::max<size_t>((size_t)S.sumN * kc, 1);
-    for (HM& h : heap) {
-      HM b = h;
-      b.dense = b.U = b.V = nullptr;
-      try {
-        b.dense = dmalloc(dn * 2);
-        b.U = dmalloc(un * 2);
-        b.V = dmalloc(vn * 2);
-      } catch (...) {
-        cudaFree(b.dense); cudaFree(b.U); cudaFree(b.V);   // cudaFree(nullptr) is a no-op
-        throw;
+    const size_t rn = std::max<size_t>(S.lleaf.size(), 1) * sizeof(int);
+    pool_b.restart();
+    live_b.clear();
+    std::map<int, HM> to;
+    for (int q : live) {
+      const HM h = pool.at(q, dry);
+      HM b = pool_b.at(pool_b.take(dry), dry);
+      if (!dry) {
+        launch_to_bf16((const float*)h.dense, b.dense, (int64_t)dn, st);
+        launch_to_bf16((const float*)h.U, b.U, (int64_t)un, st);
+        launch_to_bf16((const float*)h.V, b.V, (int64_t)vn, st);
+        ACR_CUDA(cudaMemcpyAsync(b.rank, h.rank, rn, cudaMemcpyDeviceToDevice, st));
       }
-      launch_to_bf16((const float*)h.dense, b.dense, (int64_t)dn, st);
-      launch_to_bf16((const float*)h.U, b.U, (int64_t)un, st);
-      launch_to_bf16((const float*)h.V, b.V, (int64_t)vn, st);
-      ACR_CUDA(cudaStreamSynchronize(st));
-      // every reference moves to the new arrays before the old ones are
-      // freed (a later allocation may reuse a freed address)
-      auto remap = [&](HM& r) {
-        if (r.dense && r.dense == h.dense) r = b;
-      };
-      for (HM& r : D) remap(r);
-      for (Level& lev : levels) {
-        for (HM& r : lev.L) remap(r);
-        for (HM& r : lev.U) remap(r);
-      }
-      cudaFree(h.dense); cudaFree(h.U); cudaFree(h.V);
-      h = b;
+      b.slot = -2 - q;   // not a slot of the T arena
+      to[q] = b;
+      live_b.push_back(b);
+    }
+    auto remap = [&](HM& r) {
+      if (r.slot >= 0) r = to.at(r.slot);
+    };
+    for (HM& r : D) remap(r);
+    for (Level& lev : levels) {
+      for (HM& r : lev.L) remap(r);
+      for (HM& r : lev.U) remap(r);
     }
   }
   void release() {
-    for (HM& h : heap) { cudaFree(h.dense); cudaFree(h.U); cudaFree(h.V); cudaFree(h.rank); }
-    heap.clear();
+    pool.release();
+    pool_b.release();
     for (void* p : owned) cudaFree(p);
     owned.clear();
     for (auto& kv : plans) {
       cudaFree(kv.second->d_groups); cudaFree(kv.second->d_items); cudaFree(kv.second->d_targets);
+      cudaFree(kv.second->d_stack);
     }
     plans.clear();
     for (auto& kv : merged_plans) {
       cudaFree(kv.second->d_groups); cudaFree(kv.second->d_items); cudaFree(kv.second->d_targets);
+      cudaFree(kv.second->d_stack);
     }
     merged_plans.clear();
     if (scratch) cudaFree(scratch);
@@ -292,6 +422,9 @@ class Engine : public EngineBase {
     for (Pend& pd : pend) { cudaEventDestroy(pd.a); cudaEventDestroy(pd.b); }
     for (cudaEvent_t e : evfree) cudaEventDestroy(e);
     pend.clear(); evfree.clear();
+    if (ev0) cudaEventDestroy(ev0);
+    if (ev1) cudaEventDestroy(ev1);
+    ev0 = ev1 = nullptr;
   }
 
   // ------------------------------------------------------------ plans
@@ -312,16 +445,24 @@ class Engine : public EngineBase {
     return ref;
   }
 
+  // the counting pass records the largest scratch any launch needs, which is
+  // then allocated once; a one-shot setup grows it on demand
   void ensure_scratch(size_t bytes, size_t ranks, cudaStream_t st) {
+    if (dry) {
+      scratch_need = std::max(scratch_need, bytes);
+      scratch_rank_need = std::max(scratch_rank_need, ranks);
+      return;
+    }
+    if (bytes <= scratch_bytes && ranks <= scratch_rank_cnt) return;
+    if (counted) throw AcrError{S_OOM, "setup scratch larger than its counted need"};
+    ACR_CUDA(cudaStreamSynchronize(st));
     if (bytes > scratch_bytes) {
-      ACR_CUDA(cudaStreamSynchronize(st));
       if (scratch) cudaFree(scratch);
       scratch = nullptr;
       scratch = dmalloc(bytes);
       scratch_bytes = bytes;
     }
     if (ranks > scratch_rank_cnt) {
-      ACR_CUDA(cudaStreamSynchronize(st));
       if (scratch_ranks) cudaFree(scratch_ranks);
       scratch_ranks = nullptr;
       scratch_ranks = (int*)dmalloc(ranks * sizeof(int));
@@ -334,6 +475,10 @@ class Engine : public EngineBase {
     pl.d_groups = dmalloc(std::max<size_t>(pl.groups.size(), 1) * sizeof(GGroup));
     pl.d_items = dmalloc(std::max<size_t>(pl.items.size(), 1) * sizeof(GItem));
     pl.d_targets = dmalloc(std::max<size_t>(pl.targets.size(), 1) * sizeof(TInfo));
+    pl.d_stack = dmalloc(std::max<size_t>(pl.stack.size(), 1) * sizeof(StackDim));
+    if (!pl.stack.empty())
+      ACR_CUDA(cudaMemcpy(pl.d_stack, pl.stack.data(), pl.stack.size() * sizeof(StackDim),
+                          cudaMemcpyHostToDevice));
     if (!pl.groups.empty())
       ACR_CUDA(cudaMemcpy(pl.d_groups, pl.groups.data(), pl.groups.size() * sizeof(GGroup),
                           cudaMemcpyHostToDevice));
@@ -432,6 +577,8 @@ class Engine : public EngineBase {
     size_t per_plane = std::max<size_t>((size_t)pl.scratch * sizeof(T), 256);
     int Pc = (int)std::max<size_t>(1, std::min<size_t>(P, scratch_budget / per_plane));
     ensure_scratch(per_plane * Pc, (size_t)std::max(pl.scratch_ranks, 1) * Pc, st);
+    char* scr_base = dry ? fake_base() : (char*)scratch;
+    int* scr_rank_base = dry ? (int*)fake_base() : scratch_ranks;
     std::vector<void*> tab((3 * nr + 1) * (size_t)Pc);
     std::vector<void*> rtab((nr + 1) * (size_t)Pc);
     for (int c0 = 0; c0 < P; c0 += Pc) {
@@ -445,20 +592,17 @@ class Engine : public EngineBase {
           rtab[r * pc + p] = h.rank;
         }
       for (int p = 0; p < pc; ++p) {
-        tab[(3 * nr) * pc + p] = (char*)scratch + (size_t)p * per_plane;
-        rtab[nr * pc + p] = scratch_ranks + (size_t)p * std::max(pl.scratch_ranks, 1);
+        tab[(3 * nr) * pc + p] = scr_base + (size_t)p * per_plane;
+        rtab[nr * pc + p] = scr_rank_base + (size_t)p * std::max(pl.scratch_ranks, 1);
       }
       T* const* d_tab = (T* const*)ring.push(tab.data(), sizeof(void*) * (3 * nr + 1) * pc, st);
       int* const* d_rtab = (int* const*)ring.push(rtab.data(), sizeof(void*) * (nr + 1) * pc, st);
       for (const Stage& sg : pl.stages) {
         if (sg.kind == ST_GEMM)
-          timed(0, [&] { launch_ggemm<T>(pl, sg.beg, sg.end, d_tab, (const int* const*)d_rtab, pc,
-                                         d_coefs, st, sg.tag >= 0 ? fl(5 + sg.tag) : fl(0),
-                                         sg.tag); },
-                sg.tag);
+          timed(0, [&] { gemm_stage(pl, sg, d_tab, (const int* const*)d_rtab, pc, st); }, sg.tag);
         else if (sg.kind == ST_PCHOL || sg.kind == ST_PCHOL + 16)
           timed(1, [&] { launch_pchol<T>(pl, sg.beg, sg.end, sg.kind == ST_PCHOL, tau_orth(), d_tab,
-                                         d_rtab, pc, st, fl(1)); });
+                                         d_rtab, pc, st, d_sketch_stat, fl(1)); });
         else if (sg.kind == ST_EIG)
           timed(2, [&] { launch_eig<T>(pl, sg.beg, sg.end, eps, kc, c_role, d_tab, d_rtab, pc,
                                        d_err, st, fl(2)); });
@@ -466,10 +610,20 @@ class Engine : public EngineBase {
     }
   }
 
+  // One GEMM stage of a plan (grouped small GEMMs on the CUDA cores; float
+  // Grams with compensated accumulation and FP64 results).
+  void gemm_stage(const Plan& pl, const Stage& sg, T* const* d_tab, const int* const* d_rtab,
+                  int pc, cudaStream_t st) {
+    double* f = sg.tag >= 0 ? fl(5 + sg.tag) : fl(0);
+    launch_ggemm<T>(pl, sg.beg, sg.end, d_tab, d_rtab, pc, d_coefs, st, f, sg.tag);
+  }
+
   double tau_orth() const {
     // range-finder truncation: three orders below eps, never below the
-    // relative noise floor of a Gram matrix in the storage precision
-    const double floor_ = sizeof(T) == 8 ? 1e-7 : 1e-3;
+    // relative noise floor of the sketch in the storage precision (the
+    // Grams are FP64-accurate in every form: 1e-7 for FP64 data, 1e-6 for
+    // float data, whose own rounding is ~6e-8)
+    const double floor_ = sizeof(T) == 8 ? 1e-7 : 1e-6;
     return std::max(1e-3 * eps, floor_);
   }
 
@@ -510,24 +664,13 @@ class Engine : public EngineBase {
     std::vector<std::vector<HM>> roles(2);
     for (int i : planes) {
       roles[0].push_back(D[i]);
-      roles[1].push_back(alloc_hm());
+      roles[1].push_back(alloc_hm(st));
     }
     std::vector<void*> xd(P);
     for (int p = 0; p < P; ++p) xd[p] = roles[0][p].dense;
-    void* d_xdense = dmalloc(sizeof(void*) * P);
-    ACR_CUDA(cudaMemcpy(d_xdense, xd.data(), sizeof(void*) * P, cudaMemcpyHostToDevice));
+    void* d_xdense = ring.push(xd.data(), sizeof(void*) * P, st);
     hinv(0, roles, d_xdense, P, st);
-    ACR_CUDA(cudaStreamSynchronize(st));
-    cudaFree(d_xdense);
-    for (HM& h : roles[1]) free_hm(h);
-  }
-
-  void check_err(cudaStream_t st) {
-    ACR_CUDA(cudaStreamSynchronize(st));
-    int h = 0;
-    ACR_CUDA(cudaMemcpy(&h, d_err, sizeof(int), cudaMemcpyDeviceToHost));
-    if (h & ERR_PIVOT) throw AcrError{S_BREAKDOWN, "zero pivot in a dense leaf inverse"};
-    if (h & ERR_RANKCAP) throw AcrError{S_RANK_CAP, "truncated rank above the rank cap"};
+    for (HM& h : roles[1]) free_hm(h);   // reusable by later launches (stream order)
   }
 
   template <typename V>
@@ -538,8 +681,15 @@ class Engine : public EngineBase {
     owned.push_back(p);
     return (void**)p;
   }
+  // a pointer table of the setup, through the ring (capturable)
+  template <typename V>
+  void** ring_tables(const std::vector<V>& host, cudaStream_t st) {
+    return (void**)ring.push(host.data(), std::max<size_t>(host.size() * sizeof(V), 16), st);
+  }
 
   void build_apply_program();
+  void build_program(Program& pg, int inst, bool count_bytes);
+  void run_program(const Program& pg, bool trans, int nr, cudaStream_t st);
   void run_steps(const std::vector<ApplyStep>& steps, int nr, cudaStream_t st);
   static constexpr int RB = 8;       // right-hand sides per apply pass (multi-RHS apply)
   int64_t tvs = 0;                   // doubles of projection scratch per right-hand side
@@ -547,17 +697,25 @@ class Engine : public EngineBase {
 };
 
 template <typename T>
-void Engine<T>::setup(const double* coef, cudaStream_t st) {
+void Engine<T>::setup_multi(const double* const* coefs, cudaStream_t st, bool one_shot) {
+  prepare(coefs, st, !one_shot);
+  execute_timed(st);
+  finish(st, one_shot);
+}
+
+template <typename T>
+void Engine<T>::prepare(const double* const* coefs, cudaStream_t st, bool count_pass) {
   auto h0 = std::chrono::steady_clock::now();
   cur_st = st;
+  coef_in.assign(coefs, coefs + count);
   S.build(n, eta, leaf);
   if (!S.balanced || S.lsz > 64 || S.lsz < 1)
     throw AcrError{S_UNSUPPORTED, "cluster tree is not balanced with leaves of at most 64 points"};
   pp.kc = kc;
   pp.oversample = 8;
   pp.cholqr2 = true;
+  pp.gram_scale = (int)(sizeof(double) / sizeof(T));
   mvp.build(S);
-  ring.init(size_t(64) << 20);
   {
     size_t fr = 0, tot = 0;
     ACR_CUDA(cudaMemGetInfo(&fr, &tot));
@@ -594,7 +752,7 @@ void Engine<T>::setup(const double* coef, cudaStream_t st) {
   }
   if (maxcpl > kc)
     throw AcrError{S_RANK_CAP, "plane couplings inside an admissible block exceed the rank cap"};
-  const bool has_cpl = !cpl.empty();
+  has_cpl = !cpl.empty();
   sd.perm = (const int*)upload(S.perm, owned);
   sd.dinfo = (const int*)upload(dinfo, owned);
   sd.linfo = (const int*)upload(linfo, owned);
@@ -631,11 +789,12 @@ void Engine<T>::setup(const double* coef, cudaStream_t st) {
   mvd.segt_ptr = (const int32_t*)upload(mvp.segt_ptr, owned);
   mvd.nseg = mvp.seg_ptr.back();
   mvd.nsegt = mvp.segt_ptr.back();
-  std::vector<double> coefs{1.0, -1.0};
-  d_coefs = (double*)upload(coefs, owned);
+  std::vector<double> coefs_pm{1.0, -1.0};
+  d_coefs = (double*)upload(coefs_pm, owned);
   d_err = (int*)dmalloc(sizeof(int));
   owned.push_back(d_err);
-  ACR_CUDA(cudaMemset(d_err, 0, sizeof(int)));
+  d_sketch_stat = (unsigned long long*)dmalloc(2 * sizeof(unsigned long long));
+  owned.push_back(d_sketch_stat);
   if (profiling) {
     d_fl = (double*)dmalloc(21 * sizeof(double));
     owned.push_back(d_fl);
@@ -644,75 +803,139 @@ void Engine<T>::setup(const double* coef, cudaStream_t st) {
   std::vector<int> allp(n);
   for (int k = 0; k < n; ++k) allp[k] = k;
   d_planes_all = (int*)upload(allp, owned);
-  auto h1 = std::chrono::steady_clock::now();
+  Ld = (double*)dmalloc(sizeof(double) * N * count);
+  Ud = (double*)dmalloc(sizeof(double) * N * count);
+  owned.push_back(Ld); owned.push_back(Ud);
+  ACR_CUDA(cudaEventCreate(&ev0));
+  ACR_CUDA(cudaEventCreate(&ev1));
 
-  cudaEvent_t e0, e1;
-  ACR_CUDA(cudaEventCreate(&e0));
-  ACR_CUDA(cudaEventCreate(&e1));
-  ACR_CUDA(cudaEventRecord(e0, st));
+  // counting pass: the same host sequence with no device work sizes the
+  // H-matrix arena(s), the setup scratch and the table ring
+  const size_t dn = (size_t)S.dleaf.size() * S.lsz * S.lsz;
+  const size_t un = (size_t)S.sumM * kc, vn = (size_t)S.sumN * kc;
+  const size_t rb = std::max<size_t>(S.lleaf.size(), 1) * sizeof(int);
+  pool.layout(std::max<size_t>(dn, 1) * sizeof(T), std::max<size_t>(un, 1) * sizeof(T),
+              std::max<size_t>(vn, 1) * sizeof(T), rb);
+  pool_b.layout(std::max<size_t>(dn, 1) * 2, std::max<size_t>(un, 1) * 2,
+                std::max<size_t>(vn, 1) * 2, rb);
+  counted = count_pass;
+  if (!count_pass) {
+    // one-shot: plans are built as the real pass first needs them (host
+    // work overlapping the device's), memory grows on demand
+    ring.init(size_t(64) << 20);
+  } else {
+    // counting pass: the same host sequence with no device work sizes the
+    // H-matrix slots, the setup scratch and the table ring exactly
+    dry = true;
+    ring.counting = true;
+    ring.off = 0;
+    scratch_need = scratch_rank_need = 0;
+    execute(st);
+    dry = false;
+    ring.counting = false;
+    const size_t ring_need = ring.off;
+    pool.reserve(pool.hw);
+    pool.fixed = true;
+    if (bf16) {
+      pool_b.reserve(pool_b.hw);
+      pool_b.fixed = true;
+    }
+    scratch = dmalloc(std::max<size_t>(scratch_need, 256));
+    scratch_bytes = std::max<size_t>(scratch_need, 256);
+    scratch_ranks = (int*)dmalloc(std::max<size_t>(scratch_rank_need, 1) * sizeof(int));
+    scratch_rank_cnt = std::max<size_t>(scratch_rank_need, 1);
+    ring.init(ring_need);
+    ring.fixed = true;
+  }
+  info.structure_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - h0).count();
+}
+
+template <typename T>
+void Engine<T>::execute(cudaStream_t st) {
+  cur_st = st;
+  pool.restart();
+  ring.off = 0;
+  D.assign((size_t)count * n, HM());
+  levels.clear();
+  if (!dry) {
+    ACR_CUDA(cudaMemsetAsync(d_err, 0, sizeof(int), st));
+    ACR_CUDA(cudaMemsetAsync(d_sketch_stat, 0, 2 * sizeof(unsigned long long), st));
+  }
+  const int NP = count * n;   // plane slots
 
   // a3: plane blocks in H-format
-  D.resize(n);
-  for (int k = 0; k < n; ++k) D[k] = alloc_hm();
-  {
+  for (int k = 0; k < NP; ++k) D[k] = alloc_hm(st);
+  for (int i = 0; i < count; ++i) {
     std::vector<void*> td(n), tu(n), tv(n), tr(n);
-    for (int k = 0; k < n; ++k) { td[k] = D[k].dense; tu[k] = D[k].U; tv[k] = D[k].V; tr[k] = D[k].rank; }
-    void** a = put_tables(td); void** b = put_tables(tu); void** c = put_tables(tv);
-    void** d = put_tables(tr);
+    for (int k = 0; k < n; ++k) {
+      const HM& h = D[i * n + k];
+      td[k] = h.dense; tu[k] = h.U; tv[k] = h.V; tr[k] = h.rank;
+    }
+    void** a = ring_tables(td, st); void** b = ring_tables(tu, st);
+    void** c = ring_tables(tv, st); void** d = ring_tables(tr, st);
+    const double* coef = coef_in[i];
     timed(4, [&] { launch_plane_to_h<T>(sd, coef, n, d_planes_all, n, (T* const*)a, (T* const*)b,
                                         (T* const*)c, (int* const*)d, kc, st); });
-    if (has_cpl) {
-      OpDesc op;
-      op.c_node = 0; op.c_role = 0; op.alpha = 0; op.nroles = 1;
-      std::vector<std::vector<HM>> roles{D};
-      run_op(op, roles, n, st);
+    if (!dry) {
+      launch_permute(coef + 5 * N, Ld + (int64_t)i * N, sd.perm, n2, n, true, st);
+      launch_permute(coef + 6 * N, Ud + (int64_t)i * N, sd.perm, n2, n, true, st);
     }
   }
-  Ld = (double*)dmalloc(sizeof(double) * N);
-  Ud = (double*)dmalloc(sizeof(double) * N);
-  owned.push_back(Ld); owned.push_back(Ud);
-  launch_permute(coef + 5 * N, Ld, sd.perm, n2, n, true, st);
-  launch_permute(coef + 6 * N, Ud, sd.perm, n2, n, true, st);
+  if (has_cpl) {
+    OpDesc op;
+    op.c_node = 0; op.c_role = 0; op.alpha = 0; op.nroles = 1;
+    std::vector<std::vector<HM>> roles{D};
+    run_op(op, roles, NP, st);
+  }
 
-  std::vector<HM> curL(n), curU(n);   // couplings of the current level (r >= 1)
+  std::vector<HM> curL(NP), curU(NP);   // couplings of the current level (r >= 1)
   int s = 1, r = 0;
   while (s < n) {
     Level lev;
     lev.s = s;
-    for (int k = s; k < n; k += 2 * s) lev.red.push_back(k);
-    for (int k = 0; k < n; k += 2 * s) lev.black.push_back(k);
+    for (int i = 0; i < count; ++i) {
+      for (int k = s; k < n; k += 2 * s) lev.red.push_back(i * n + k);
+      for (int k = 0; k < n; k += 2 * s) lev.black.push_back(i * n + k);
+    }
     lev.L = curL;
     lev.U = curU;
     // a4: H-inverse of the red planes, in place
-    auto lvl_t0 = std::chrono::steady_clock::now();
-    char rname[16];
-    snprintf(rname, sizeof(rname), "inv%d", r);
-    nvtxRangePushA(rname);   // trace ranges: invN / updN per CR level
+    if (!dry) {
+      char rname[16];
+      snprintf(rname, sizeof(rname), "inv%d", r);
+      nvtxRangePushA(rname);   // trace ranges: invN / updN per CR level
+    }
+    cudaEvent_t li0 = nullptr, li1 = nullptr, lu1 = nullptr;
+    if (profiling && !dry && r < 16) {
+      li0 = ev(); li1 = ev(); lu1 = ev();
+      ACR_CUDA(cudaEventRecord(li0, st));
+    }
     hinv_batch(lev.red, st);
-    check_err(st);
-    nvtxRangePop();
-    snprintf(rname, sizeof(rname), "upd%d", r);
-    nvtxRangePushA(rname);
-    auto lvl_t1 = std::chrono::steady_clock::now();
-    if (profiling && r < 16) prof.inv_ms[r] = std::chrono::duration<double, std::milli>(lvl_t1 - lvl_t0).count();
+    if (!dry) {
+      nvtxRangePop();
+      char rname[16];
+      snprintf(rname, sizeof(rname), "upd%d", r);
+      nvtxRangePushA(rname);
+    }
+    if (li1) ACR_CUDA(cudaEventRecord(li1, st));
     // a5-a7: Schur updates of the black planes
     const int PB = (int)lev.black.size();
-    std::vector<HM> newL(n), newU(n);
+    std::vector<HM> newL(NP), newU(NP);
     if (r == 0) {
       std::vector<HM> Ta(PB), Tb(PB), nL(PB), nU(PB), Xa(PB), Xb(PB), Dj(PB);
       std::vector<const double*> rowA(PB), colA(PB), rowB(PB), colB(PB), colLA(PB), colUB(PB);
       for (int q = 0; q < PB; ++q) {
         const int j = lev.black[q], a = j - s, b = j + s;
         Dj[q] = D[j];
-        if (a >= 0) {
-          Xa[q] = D[a]; Ta[q] = alloc_hm(); nL[q] = alloc_hm();
+        if (has_lo(j, s)) {
+          Xa[q] = D[a]; Ta[q] = alloc_hm(st); nL[q] = alloc_hm(st);
           rowA[q] = Ld + (int64_t)j * n2; colA[q] = Ud + (int64_t)a * n2;
           colLA[q] = Ld + (int64_t)a * n2;
         }
-        if (b < n) {
-          Xb[q] = D[b]; Tb[q] = alloc_hm();
+        if (has_hi(j, s)) {
+          Xb[q] = D[b]; Tb[q] = alloc_hm(st);
           rowB[q] = Ud + (int64_t)j * n2; colB[q] = Ld + (int64_t)b * n2;
-          if (b + s < n) { nU[q] = alloc_hm(); colUB[q] = Ud + (int64_t)b * n2; }
+          if (has_hi(b, s)) { nU[q] = alloc_hm(st); colUB[q] = Ud + (int64_t)b * n2; }
         }
       }
       auto scale = [&](std::vector<HM>& out, std::vector<HM>& x, std::vector<const double*>& rs,
@@ -725,9 +948,10 @@ void Engine<T>::setup(const double* coef, cudaStream_t st) {
           xd[q] = x[q].dense; xu[q] = x[q].U; xv[q] = x[q].V; xr[q] = x[q].rank;
         }
         std::vector<const void*> rr(rs.begin(), rs.end()), cc(cs.begin(), cs.end());
-        void** t[10] = {put_tables(od), put_tables(ou), put_tables(ov), put_tables(orr),
-                        put_tables(xd), put_tables(xu), put_tables(xv), put_tables(xr),
-                        put_tables(rr), put_tables(cc)};
+        void** t[10] = {ring_tables(od, st), ring_tables(ou, st), ring_tables(ov, st),
+                        ring_tables(orr, st), ring_tables(xd, st), ring_tables(xu, st),
+                        ring_tables(xv, st), ring_tables(xr, st), ring_tables(rr, st),
+                        ring_tables(cc, st)};
         timed(4, [&] {
           launch_hscale<T>(sd, (T* const*)t[0], (T* const*)t[1], (T* const*)t[2], (int* const*)t[3],
                            (T* const*)t[4], (T* const*)t[5], (T* const*)t[6],
@@ -745,10 +969,9 @@ void Engine<T>::setup(const double* coef, cudaStream_t st) {
       op.adds.push_back(OpDesc::Add{2, 1});
       std::vector<std::vector<HM>> roles{Dj, Ta, Tb};
       run_op(op, roles, PB, st);
-      ACR_CUDA(cudaStreamSynchronize(st));
       for (int q = 0; q < PB; ++q) {
-        if (Ta[q].dense) free_hm(Ta[q]);
-        if (Tb[q].dense) free_hm(Tb[q]);
+        free_hm(Ta[q]);
+        free_hm(Tb[q]);
         newL[lev.black[q]] = nL[q];
         newU[lev.black[q]] = nU[q];
       }
@@ -760,13 +983,13 @@ void Engine<T>::setup(const double* coef, cudaStream_t st) {
         Dj[q] = D[j];
         Lj[q] = curL[j];
         Uj[q] = curU[j];
-        if (a >= 0 && curL[j].dense) {
-          Xa[q] = D[a]; Ta[q] = alloc_hm(); Ua[q] = curU[a]; La[q] = curL[a];
-          if (La[q].dense) nL[q] = alloc_hm();
+        if (has_lo(j, s) && curL[j].dense) {
+          Xa[q] = D[a]; Ta[q] = alloc_hm(st); Ua[q] = curU[a]; La[q] = curL[a];
+          if (La[q].dense) nL[q] = alloc_hm(st);
         }
-        if (b < n && curU[j].dense) {
-          Xb[q] = D[b]; Tb[q] = alloc_hm(); Lb[q] = curL[b]; Ub[q] = curU[b];
-          if (Ub[q].dense) nU[q] = alloc_hm();
+        if (has_hi(j, s) && curU[j].dense) {
+          Xb[q] = D[b]; Tb[q] = alloc_hm(st); Lb[q] = curL[b]; Ub[q] = curU[b];
+          if (Ub[q].dense) nU[q] = alloc_hm(st);
         }
       }
       OpDesc opT;
@@ -784,36 +1007,70 @@ void Engine<T>::setup(const double* coef, cudaStream_t st) {
       opN.prods.push_back(OpDesc::Prod{0, 0, 1, 2, 1});
       run_split(opN, {nL, Ta, La}, PB, st);           // L_j' = -Ta L_a
       run_split(opN, {nU, Tb, Ub}, PB, st);           // U_j' = -Tb U_b
-      ACR_CUDA(cudaStreamSynchronize(st));
       for (int q = 0; q < PB; ++q) {
-        if (Ta[q].dense) free_hm(Ta[q]);
-        if (Tb[q].dense) free_hm(Tb[q]);
+        free_hm(Ta[q]);
+        free_hm(Tb[q]);
         newL[lev.black[q]] = nL[q];
         newU[lev.black[q]] = nU[q];
       }
     }
-    check_err(st);
-    nvtxRangePop();
-    if (profiling && r < 16)
-      prof.upd_ms[r] = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - lvl_t1).count();
+    if (!dry) nvtxRangePop();
+    if (lu1) {
+      ACR_CUDA(cudaEventRecord(lu1, st));
+      ACR_CUDA(cudaEventSynchronize(lu1));
+      float a1 = 0.f, a2 = 0.f;
+      ACR_CUDA(cudaEventElapsedTime(&a1, li0, li1));
+      ACR_CUDA(cudaEventElapsedTime(&a2, li1, lu1));
+      prof.inv_ms[r] = a1;
+      prof.upd_ms[r] = a2;
+      evfree.push_back(li0); evfree.push_back(li1); evfree.push_back(lu1);
+    }
     for (int j : lev.black) { curL[j] = newL[j]; curU[j] = newU[j]; }
     levels.push_back(std::move(lev));
     s *= 2;
     ++r;
   }
-  // a8: the last plane
+  // a8: the last plane of every instance
   {
-    auto t0 = std::chrono::steady_clock::now();
-    hinv_batch({0}, st);
-    check_err(st);
-    if (profiling && r < 16)
-      prof.inv_ms[r] = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    std::vector<int> last;
+    for (int i = 0; i < count; ++i) last.push_back(i * n);
+    cudaEvent_t l0 = nullptr, l1 = nullptr;
+    if (profiling && !dry && r < 16) {
+      l0 = ev(); l1 = ev();
+      ACR_CUDA(cudaEventRecord(l0, st));
+    }
+    hinv_batch(last, st);
+    if (l1) {
+      ACR_CUDA(cudaEventRecord(l1, st));
+      ACR_CUDA(cudaEventSynchronize(l1));
+      float a1 = 0.f;
+      ACR_CUDA(cudaEventElapsedTime(&a1, l0, l1));
+      prof.inv_ms[r] = a1;
+      evfree.push_back(l0); evfree.push_back(l1);
+    }
   }
   if (bf16) convert_bf16(st);
-  ACR_CUDA(cudaEventRecord(e1, st));
-  ACR_CUDA(cudaEventSynchronize(e1));
+}
+
+template <typename T>
+void Engine<T>::check_err(cudaStream_t st) {
+  ACR_CUDA(cudaStreamSynchronize(st));
+  int h = 0;
+  ACR_CUDA(cudaMemcpy(&h, d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (h & ERR_PIVOT) throw AcrError{S_BREAKDOWN, "zero pivot in a dense leaf inverse"};
+  if (h & ERR_GROWTH)
+    throw AcrError{S_BREAKDOWN,
+                   "pivot growth of a dense leaf inverse above the storage precision's bound "
+                   "(numerically singular leaf)"};
+  if (h & ERR_RANKCAP) throw AcrError{S_RANK_CAP, "truncated rank above the rank cap"};
+  if (h & ERR_TIMEOUT) throw AcrError{S_TIMEOUT, "a bounded device wait ran out"};
+}
+
+template <typename T>
+void Engine<T>::finish(cudaStream_t st, bool one_shot) {
+  check_err(st);
   float ms = 0;
-  ACR_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+  ACR_CUDA(cudaEventElapsedTime(&ms, ev0, ev1));
   if (profiling) {
     flush_prof();
     double h[21];
@@ -825,18 +1082,25 @@ void Engine<T>::setup(const double* coef, cudaStream_t st) {
       prof.gemm.flops += h[5 + t];
     }
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
   info.setup_ms = ms;
-  info.structure_ms = std::chrono::duration<double, std::milli>(h1 - h0).count();
   info.levels = (int)levels.size();
   info.n_dense_leaves = sd.nd;
   info.n_lowrank_leaves = sd.nl;
-  // the scratch arena is only needed by the setup
-  if (scratch) { cudaFree(scratch); scratch = nullptr; scratch_bytes = 0; }
-  if (scratch_ranks) { cudaFree(scratch_ranks); scratch_ranks = nullptr; scratch_rank_cnt = 0; }
+  {
+    unsigned long long ss[2] = {0, 0};
+    ACR_CUDA(cudaMemcpy(ss, d_sketch_stat, sizeof(ss), cudaMemcpyDeviceToHost));
+    info.lr_truncations = (int64_t)ss[0];
+    info.sketch_overflows = (int64_t)ss[1];
+  }
+  if (one_shot) {
+    // the scratch arena is only needed by the setup; in the BF16 form the
+    // FP32 arena holds no stored factor any more
+    if (scratch) { cudaFree(scratch); scratch = nullptr; scratch_bytes = 0; }
+    if (scratch_ranks) { cudaFree(scratch_ranks); scratch_ranks = nullptr; scratch_rank_cnt = 0; }
+    if (bf16) pool.release();
+  }
   collect_info();
-  build_apply_program();
+  if (!Fv) build_apply_program();
 }
 
 template <typename T>
@@ -865,38 +1129,60 @@ void Engine<T>::collect_info() {
   };
   for (const Level& lev : levels) {
     for (int i : lev.red) account(D[i]);
-    for (int k = 0; k < n; k += lev.s) { account(lev.L[k]); account(lev.U[k]); }
+    for (int in = 0; in < count; ++in)
+      for (int k = 0; k < n; k += lev.s) { account(lev.L[in * n + k]); account(lev.U[in * n + k]); }
   }
-  account(D[0]);
+  for (int in = 0; in < count; ++in) account(D[in * n]);
   info.max_rank = mx;
   info.avg_rank = cnt ? (double)sumr / cnt : 0.0;
-  info.factor_bytes = bytes + 2 * N * (int64_t)sizeof(double);
+  info.factor_bytes = bytes + 2 * N * count * (int64_t)sizeof(double);
   int64_t per = ((int64_t)S.dleaf.size() * S.lsz * S.lsz + (S.sumM + S.sumN) * kc) *
                 (int64_t)store_bytes();
-  info.factor_capacity_bytes = per * (int64_t)heap.size() + 2 * N * (int64_t)sizeof(double);
+  info.factor_capacity_bytes =
+      per * (int64_t)seen.size() + 2 * N * count * (int64_t)sizeof(double);
 }
 
 template <typename T>
 void Engine<T>::build_apply_program() {
-  // work vectors for up to RB right-hand sides, N doubles apart; the step
-  // tables hold the pointers of the first one
-  Fv = (double*)dmalloc(sizeof(double) * N * RB); owned.push_back(Fv);
-  Gv = (double*)dmalloc(sizeof(double) * N * RB); owned.push_back(Gv);
-  Uv = (double*)dmalloc(sizeof(double) * N * RB); owned.push_back(Uv);
-  Tv = (double*)dmalloc(sizeof(double) * N * RB); owned.push_back(Tv);
+  // work vectors: for one problem up to RB right-hand sides N doubles apart,
+  // for a batch one right-hand side per instance (vs = count N); the step
+  // tables hold the pointers of the first right-hand side
+  const int rb = count == 1 ? RB : 1;
+  Fv = (double*)dmalloc(sizeof(double) * vs * rb); owned.push_back(Fv);
+  Gv = (double*)dmalloc(sizeof(double) * vs * rb); owned.push_back(Gv);
+  Uv = (double*)dmalloc(sizeof(double) * vs * rb); owned.push_back(Uv);
+  Tv = (double*)dmalloc(sizeof(double) * vs * rb); owned.push_back(Tv);
   maxP = 1;
   for (const Level& lev : levels) maxP = std::max<int>(maxP, (int)std::max(lev.red.size(), lev.black.size()));
   tvs = (int64_t)maxP * std::max({mvd.nseg, mvd.nsegt, 1}) * kc;
-  tvscr = (double*)dmalloc(sizeof(double) * (size_t)tvs * RB);
+  tvscr = (double*)dmalloc(sizeof(double) * (size_t)tvs * rb);
   owned.push_back(tvscr);
-  auto vec = [&](double* base, int k) -> double* { return (k >= 0 && k < n) ? base + (int64_t)k * n2 : nullptr; };
+  build_program(prog_all, -1, true);
+  prog_inst.clear();
+  if (count > 1) {
+    prog_inst.resize(count);
+    for (int i = 0; i < count; ++i) build_program(prog_inst[i], i, false);
+  }
+}
+
+// The substitution as a list of batched steps over the plane slots of
+// instance `inst` (-1: all instances).
+template <typename T>
+void Engine<T>::build_program(Program& pg, int inst, bool count_bytes) {
+  auto vec = [&](double* base, int slot) -> double* { return base + (int64_t)slot * n2; };
+  auto sel = [&](const std::vector<int>& slots) {
+    std::vector<int> o;
+    for (int q : slots)
+      if (inst < 0 || inst_of(q) == inst) o.push_back(q);
+    return o;
+  };
   // hmatvec tables: dense, U, V, rank, x, y (6 * P pointers)
   int64_t abytes = 0, aflops = 0;
-  bool count = true;   // count the plain (non-transposed) program only
+  bool cnt = count_bytes;   // count the plain (non-transposed) program only
   auto mv_step = [&](const std::vector<HM>& H, const std::vector<double*>& x,
                      const std::vector<double*>& y, double alpha, double beta, bool trans) {
     const int P = (int)H.size();
-    if (count)
+    if (cnt)
       for (int p = 0; p < P; ++p) {
         if (!y[p]) continue;
         abytes += (int64_t)n2 * 8 * (beta != 0.0 ? 2 : 1);
@@ -917,7 +1203,7 @@ void Engine<T>::build_apply_program() {
                        const std::vector<double*>& x, const std::vector<const double*>& b,
                        const std::vector<double*>& z, double sgn) {
     const int P = (int)y.size();
-    if (count)
+    if (cnt)
       for (int p = 0; p < P; ++p) {
         if (!y[p]) continue;
         abytes += (int64_t)n2 * 8 * 2;
@@ -932,33 +1218,38 @@ void Engine<T>::build_apply_program() {
   };
   auto copy_step = [&](const std::vector<double*>& dst, const std::vector<double*>& src) {
     const int P = (int)dst.size();
-    if (count)
+    if (cnt)
       for (int p = 0; p < P; ++p) abytes += (int64_t)n2 * 8 * (src[p] ? 2 : 1);
     std::vector<void*> t(2 * P);
     for (int p = 0; p < P; ++p) { t[p] = dst[p]; t[P + p] = src[p]; }
     return ApplyStep{2, P, false, 0.0, 0.0, 0.0, put_tables(t)};
   };
+  std::vector<int> last;
+  for (int i = 0; i < count; ++i)
+    if (inst < 0 || i == inst) last.push_back(i * n);
+  pg = Program();
   for (int pass = 0; pass < 2; ++pass) {
     const bool tr = pass == 1;
-    count = !tr;
-    auto& fw = tr ? fwdT_steps : fwd_steps;
-    auto& bw = tr ? bwdT_steps : bwd_steps;
+    cnt = count_bytes && !tr;
+    auto& fw = tr ? pg.fwdT : pg.fwd;
+    auto& bw = tr ? pg.bwdT : pg.bwd;
     for (size_t r = 0; r < levels.size(); ++r) {
       const Level& lev = levels[r];
       const int s = lev.s;
+      const std::vector<int> red = sel(lev.red), black = sel(lev.black);
       // g_i = X_i f_i  (transposed: X_i^T f_i)
       std::vector<HM> X;
       std::vector<double*> xs, ys;
-      for (int i : lev.red) { X.push_back(D[i]); xs.push_back(vec(Fv, i)); ys.push_back(vec(Gv, i)); }
+      for (int i : red) { X.push_back(D[i]); xs.push_back(vec(Fv, i)); ys.push_back(vec(Gv, i)); }
       fw.push_back(mv_step(X, xs, ys, 1.0, 0.0, tr));
       // black: f_j -= Lc_j g_{j-s} + Uc_j g_{j+s}
       // couplings: L_j, U_j (plain); U_{j-s}^T, L_{j+s}^T (transposed)
       if (r == 0) {
         std::vector<double*> y, x1, x2;
         std::vector<const double*> a, b;
-        for (int j : lev.black) {
+        for (int j : black) {
           y.push_back(vec(Fv, j));
-          const bool ha = j - s >= 0, hb = j + s < n;
+          const bool ha = has_lo(j, s), hb = has_hi(j, s);
           if (!tr) {
             a.push_back(ha ? Ld + (int64_t)j * n2 : nullptr);
             b.push_back(hb ? Ud + (int64_t)j * n2 : nullptr);
@@ -973,9 +1264,9 @@ void Engine<T>::build_apply_program() {
       } else {
         std::vector<HM> H1, H2;
         std::vector<double*> y, x1, x2;
-        for (int j : lev.black) {
+        for (int j : black) {
           y.push_back(vec(Fv, j));
-          const bool ha = j - s >= 0, hb = j + s < n;
+          const bool ha = has_lo(j, s), hb = has_hi(j, s);
           if (!tr) {
             H1.push_back(ha ? lev.L[j] : HM());
             H2.push_back(hb ? lev.U[j] : HM());
@@ -991,45 +1282,50 @@ void Engine<T>::build_apply_program() {
       }
     }
     // last plane: u_0 = X_0 f_0
-    fw.push_back(mv_step(std::vector<HM>{D[0]}, std::vector<double*>{vec(Fv, 0)},
-                         std::vector<double*>{vec(Uv, 0)}, 1.0, 0.0, tr));
+    {
+      std::vector<HM> X0;
+      std::vector<double*> xs, us;
+      for (int q : last) { X0.push_back(D[q]); xs.push_back(vec(Fv, q)); us.push_back(vec(Uv, q)); }
+      fw.push_back(mv_step(X0, xs, us, 1.0, 0.0, tr));
+    }
     // backward (stored in reverse level order)
     for (int r = (int)levels.size() - 1; r >= 0; --r) {
       const Level& lev = levels[r];
       const int s = lev.s;
+      const std::vector<int> red = sel(lev.red);
       std::vector<double*> tmp, x1, x2, us, gs;
       std::vector<HM> X;
-      for (int i : lev.red) {
+      for (int i : red) {
         tmp.push_back(vec(Tv, i));
         x1.push_back(vec(Uv, i - s));
-        x2.push_back(i + s < n ? vec(Uv, i + s) : nullptr);
+        x2.push_back(has_hi(i, s) ? vec(Uv, i + s) : nullptr);
         us.push_back(vec(Uv, i));
         gs.push_back(vec(Gv, i));
         X.push_back(D[i]);
       }
-      std::vector<double*> none(lev.red.size(), nullptr);
+      std::vector<double*> none(red.size(), nullptr);
       bw.push_back(copy_step(tmp, none));   // tmp = 0
       if (r == 0) {
         std::vector<const double*> a, b;
-        for (int i : lev.red) {
+        for (int i : red) {
           if (!tr) {
             a.push_back(Ld + (int64_t)i * n2);
-            b.push_back(i + s < n ? Ud + (int64_t)i * n2 : nullptr);
+            b.push_back(has_hi(i, s) ? Ud + (int64_t)i * n2 : nullptr);
           } else {
             a.push_back(Ud + (int64_t)(i - s) * n2);
-            b.push_back(i + s < n ? Ld + (int64_t)(i + s) * n2 : nullptr);
+            b.push_back(has_hi(i, s) ? Ld + (int64_t)(i + s) * n2 : nullptr);
           }
         }
         bw.push_back(diag_step(tmp, a, x1, b, x2, 1.0));
       } else {
         std::vector<HM> H1, H2;
-        for (int i : lev.red) {
+        for (int i : red) {
           if (!tr) {
             H1.push_back(lev.L[i]);
-            H2.push_back(i + s < n ? lev.U[i] : HM());
+            H2.push_back(has_hi(i, s) ? lev.U[i] : HM());
           } else {
             H1.push_back(lev.U[i - s]);
-            H2.push_back(i + s < n ? lev.L[i + s] : HM());
+            H2.push_back(has_hi(i, s) ? lev.L[i + s] : HM());
           }
         }
         bw.push_back(mv_step(H1, x1, tmp, 1.0, 1.0, tr));
@@ -1039,51 +1335,110 @@ void Engine<T>::build_apply_program() {
       bw.push_back(mv_step(X, tmp, us, -1.0, 1.0, tr));  // u_i -= X_i tmp
     }
   }
-  // the two permutations between natural and cluster order
-  info.apply_bytes = abytes + 4 * N * 8;
-  info.apply_flops = aflops;
+  if (count_bytes) {
+    // the two permutations between natural and cluster order
+    info.apply_bytes = abytes + 4 * N * count * 8;
+    info.apply_flops = aflops;
+  }
 }
 
 template <typename T>
 void Engine<T>::run_steps(const std::vector<ApplyStep>& steps, int nr, cudaStream_t st) {
   for (const ApplyStep& s : steps) {
     const int P = s.P;
+    if (P <= 0) continue;
     void** t = s.tabs;
     if (s.kind == 0 && bf16) {
       using B = __nv_bfloat16;
       launch_hmatvec<B>(mvd, (B* const*)t, (B* const*)(t + P), (B* const*)(t + 2 * P),
                         (const int* const*)(t + 3 * P), (const double* const*)(t + 4 * P),
-                        (double* const*)(t + 5 * P), s.alpha, s.beta, s.trans, tvscr, P, nr, N,
+                        (double* const*)(t + 5 * P), s.alpha, s.beta, s.trans, tvscr, P, nr, vs,
                         st);
     } else if (s.kind == 0) {
       launch_hmatvec<T>(mvd, (T* const*)t, (T* const*)(t + P), (T* const*)(t + 2 * P),
                         (const int* const*)(t + 3 * P), (const double* const*)(t + 4 * P),
-                        (double* const*)(t + 5 * P), s.alpha, s.beta, s.trans, tvscr, P, nr, N,
+                        (double* const*)(t + 5 * P), s.alpha, s.beta, s.trans, tvscr, P, nr, vs,
                         st);
     } else if (s.kind == 1) {
       launch_diag_update((double* const*)t, (const double* const*)(t + P),
                          (const double* const*)(t + 2 * P), (const double* const*)(t + 3 * P),
-                         (const double* const*)(t + 4 * P), n2, P, s.sgn, nr, N, st);
+                         (const double* const*)(t + 4 * P), n2, P, s.sgn, nr, vs, st);
     } else {
-      launch_copy_planes((double* const*)t, (const double* const*)(t + P), n2, P, nr, N, st);
+      launch_copy_planes((double* const*)t, (const double* const*)(t + P), n2, P, nr, vs, st);
     }
   }
 }
 
 template <typename T>
+void Engine<T>::run_program(const Program& pg, bool trans, int nr, cudaStream_t st) {
+  run_steps(trans ? pg.fwdT : pg.fwd, nr, st);
+  run_steps(trans ? pg.bwdT : pg.bwd, nr, st);
+}
+
+template <typename T>
 void Engine<T>::apply(const double* r, double* z, bool trans, cudaStream_t st, int nrhs) {
+  if (count > 1) {
+    // a batch: one right-hand side per instance, instances back to back
+    if (nrhs != 1) throw AcrError{S_INVALID, "a batch applies one right-hand side per instance"};
+    launch_permute(r, Fv, sd.perm, n2, n * count, true, st);
+    run_program(prog_all, trans, 1, st);
+    launch_permute(Uv, z, sd.perm, n2, n * count, false, st);
+    return;
+  }
   // groups of 8, 4, 2, 1 right-hand sides; each group streams the factors once
   for (int k = 0; k < nrhs;) {
     int R = RB;
     while (R > nrhs - k) R >>= 1;
     launch_permute(r + (int64_t)k * N, Fv, sd.perm, n2, n * R, true, st);
-    run_steps(trans ? fwdT_steps : fwd_steps, R, st);
-    run_steps(trans ? bwdT_steps : bwd_steps, R, st);
+    run_program(prog_all, trans, R, st);
     launch_permute(Uv, z + (int64_t)k * N, sd.perm, n2, n * R, false, st);
     k += R;
   }
 }
 
+template <typename T>
+void Engine<T>::apply_gather(const double* const* r, double* const* z, cudaStream_t st) {
+  for (int i = 0; i < count; ++i)
+    launch_permute(r[i], Fv + (int64_t)i * N, sd.perm, n2, n, true, st);
+  run_program(prog_all, false, 1, st);
+  for (int i = 0; i < count; ++i)
+    launch_permute(Uv + (int64_t)i * N, z[i], sd.perm, n2, n, false, st);
+}
+
+template <typename T>
+void Engine<T>::apply_instance(int i, const double* r, double* z, bool trans, cudaStream_t st) {
+  if (i < 0 || i >= count) throw AcrError{S_INVALID, "no such instance"};
+  if (count == 1) {
+    apply(r, z, trans, st, 1);
+    return;
+  }
+  launch_permute(r, Fv + (int64_t)i * N, sd.perm, n2, n, true, st);
+  run_program(prog_inst[i], trans, 1, st);
+  launch_permute(Uv + (int64_t)i * N, z, sd.perm, n2, n, false, st);
+}
+
+
+// One instance of a batched engine, seen as a single preconditioner (for the
+// Krylov drivers).
+template <typename T>
+class InstanceView : public EngineBase {
+ public:
+  InstanceView(Engine<T>* e, int i) : eng(e), inst(i) {
+    n = e->n;
+    N = e->N;
+  }
+  void setup(const double*, cudaStream_t) override {
+    throw AcrError{S_INVALID, "an instance view is not set up by itself"};
+  }
+  void apply(const double* r, double* z, bool trans, cudaStream_t st, int nrhs = 1) override {
+    for (int k = 0; k < nrhs; ++k)
+      eng->apply_instance(inst, r + (int64_t)k * N, z + (int64_t)k * N, trans, st);
+  }
+
+ private:
+  Engine<T>* eng;
+  int inst;
+};
 
 // ------------------------------------------------------------ Krylov drivers
 namespace {
@@ -1114,6 +1469,7 @@ struct Krylov {
     partial = dbuf(64 * 600);
     dres = dbuf(64);
     dcoef = dbuf(64);
+    count_allocs(1);
     ACR_CUDA(cudaMallocHost(&hpin, 128 * sizeof(double)));
   }
   void A(const double* x, double* y) {
@@ -1482,6 +1838,40 @@ struct acr_handle {
   int precision = 0;
 };
 
+// A batch: problems grouped by size; one engine per size runs all of its
+// instances in shared launches, each engine on its own stream branch.
+struct acr_batch {
+  struct Group {
+    int n = 0;
+    std::vector<int> members;                 // batch indices, in batch order
+    std::vector<const double*> coefs;
+    acr::EngineBase* e = nullptr;             // Engine<double> or Engine<float>
+    cudaStream_t side = nullptr;              // branch stream of this group
+    cudaEvent_t done = nullptr;
+  };
+  int count = 0;
+  int precision = 0;
+  std::vector<int> n;                         // per instance
+  std::vector<int> group_of, slot_of;         // per instance
+  std::vector<int64_t> off;                   // per instance: offset in batch vectors
+  std::vector<Group> groups;
+  std::vector<acr::EngineBase*> views;        // per instance
+  cudaEvent_t fork = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  ~acr_batch() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    for (acr::EngineBase* v : views) delete v;
+    for (Group& g : groups) {
+      delete g.e;
+      if (g.side) cudaStreamDestroy(g.side);
+      if (g.done) cudaEventDestroy(g.done);
+    }
+    if (fork) cudaEventDestroy(fork);
+  }
+};
+
 namespace {
 
 acr_status to_status(int s) { return (acr_status)s; }
@@ -1751,6 +2141,203 @@ acr_status acr_structure_query(int32_t n, double eta, int32_t leaf, int64_t* cou
 }
 
 int64_t acr_launch_count(void) { return acr::g_launches.load(); }
+
+int64_t acr_alloc_count(void) { return acr::g_allocs.load(); }
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- batches
+namespace {
+
+template <typename F>
+void with_engine(int precision, acr::EngineBase* e, F&& f) {
+  if (precision == ACR_FP64) f(static_cast<acr::Engine<double>*>(e));
+  else f(static_cast<acr::Engine<float>*>(e));
+}
+
+// fork the group branches off `stream`, run fn(group) on each, join
+template <typename F>
+void on_branches(acr_batch* b, cudaStream_t stream, F&& fn) {
+  ACR_CUDA(cudaEventRecord(b->fork, stream));
+  for (acr_batch::Group& g : b->groups) {
+    ACR_CUDA(cudaStreamWaitEvent(g.side, b->fork, 0));
+    fn(g);
+    ACR_CUDA(cudaEventRecord(g.done, g.side));
+  }
+  for (acr_batch::Group& g : b->groups) ACR_CUDA(cudaStreamWaitEvent(stream, g.done, 0));
+}
+
+void batch_refactor(acr_batch* b, cudaStream_t stream) {
+  on_branches(b, stream, [&](acr_batch::Group& g) {
+    with_engine(b->precision, g.e, [&](auto* e) { e->execute_timed(g.side); });
+  });
+}
+
+void batch_apply(acr_batch* b, const double* r, double* z, cudaStream_t stream) {
+  on_branches(b, stream, [&](acr_batch::Group& g) {
+    with_engine(b->precision, g.e, [&](auto* e) {
+      bool contiguous = true;
+      for (size_t k = 1; k < g.members.size(); ++k)
+        contiguous &= g.members[k] == g.members[k - 1] + 1;
+      if (contiguous) {
+        const int64_t o = b->off[g.members[0]];
+        e->apply(r + o, z + o, false, g.side, 1);
+      } else {
+        std::vector<const double*> rs;
+        std::vector<double*> zs;
+        for (int m : g.members) {
+          rs.push_back(r + b->off[m]);
+          zs.push_back(z + b->off[m]);
+        }
+        e->apply_gather(rs.data(), zs.data(), g.side);
+      }
+    });
+  });
+}
+
+}  // namespace
+
+extern "C" {
+
+acr_status acr_batch_create(int32_t count, const int32_t* n, const double* const* coefs,
+                            const acr_options* opt, cudaStream_t stream, acr_batch** out) {
+  if (out) *out = nullptr;
+  if (count < 1 || count > 4096 || !n || !coefs || !opt || !out) return ACR_ERR_INVALID_ARG;
+  for (int i = 0; i < count; ++i)
+    if (n[i] < 1 || n[i] > 1024 || !coefs[i]) return ACR_ERR_INVALID_ARG;
+  if (!(opt->eps > 0.0 && opt->eps < 1.0) || !(opt->eta > 0.0) || opt->leaf < 1 ||
+      (opt->precision != ACR_FP64 && opt->precision != ACR_FP32 &&
+       opt->precision != ACR_BF16) || opt->rank_cap < 0 || opt->rank_cap > 48)
+    return ACR_ERR_INVALID_ARG;
+  const int kc = opt->rank_cap == 0 ? 32 : opt->rank_cap;
+  acr_batch* b = new acr_batch();
+  b->count = count;
+  b->precision = opt->precision;
+  acr_status s = guarded([&] {
+    int64_t o = 0;
+    for (int i = 0; i < count; ++i) {
+      b->n.push_back(n[i]);
+      b->off.push_back(o);
+      o += (int64_t)n[i] * n[i] * n[i];
+      int g = -1;
+      for (size_t k = 0; k < b->groups.size(); ++k)
+        if (b->groups[k].n == n[i]) g = (int)k;
+      if (g < 0) {
+        b->groups.emplace_back();
+        b->groups.back().n = n[i];
+        g = (int)b->groups.size() - 1;
+      }
+      b->group_of.push_back(g);
+      b->slot_of.push_back((int)b->groups[g].members.size());
+      b->groups[g].members.push_back(i);
+      b->groups[g].coefs.push_back(coefs[i]);
+    }
+    ACR_CUDA(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming));
+    const int flags = opt->flags & ~ACR_FLAG_PROFILE;
+    for (acr_batch::Group& g : b->groups) {
+      ACR_CUDA(cudaStreamCreateWithFlags(&g.side, cudaStreamNonBlocking));
+      ACR_CUDA(cudaEventCreateWithFlags(&g.done, cudaEventDisableTiming));
+      const int cnt = (int)g.members.size();
+      if (opt->precision == ACR_FP64)
+        g.e = new acr::Engine<double>(g.n, opt->eps, opt->eta, opt->leaf, kc, flags, false, cnt);
+      else
+        g.e = new acr::Engine<float>(g.n, opt->eps, opt->eta, opt->leaf, kc, flags,
+                                     opt->precision == ACR_BF16, cnt);
+      with_engine(b->precision, g.e, [&](auto* e) { e->prepare(g.coefs.data(), g.side, true); });
+    }
+    batch_refactor(b, stream);
+    for (acr_batch::Group& g : b->groups)
+      with_engine(b->precision, g.e, [&](auto* e) { e->finish(g.side, false); });
+    for (int i = 0; i < count; ++i) {
+      acr_batch::Group& g = b->groups[b->group_of[i]];
+      if (b->precision == ACR_FP64)
+        b->views.push_back(new acr::InstanceView<double>(
+            static_cast<acr::Engine<double>*>(g.e), b->slot_of[i]));
+      else
+        b->views.push_back(new acr::InstanceView<float>(
+            static_cast<acr::Engine<float>*>(g.e), b->slot_of[i]));
+    }
+    return 0;
+  });
+  if (s != ACR_OK) {
+    delete b;
+    return s;
+  }
+  *out = b;
+  return ACR_OK;
+}
+
+acr_status acr_batch_refactor(acr_batch* b, cudaStream_t stream) {
+  if (!b) return ACR_ERR_INVALID_ARG;
+  return guarded([&] {
+    batch_refactor(b, stream);
+    return 0;
+  });
+}
+
+acr_status acr_batch_status(acr_batch* b, cudaStream_t stream) {
+  if (!b) return ACR_ERR_INVALID_ARG;
+  return guarded([&] {
+    ACR_CUDA(cudaStreamSynchronize(stream));
+    for (acr_batch::Group& g : b->groups)
+      with_engine(b->precision, g.e, [&](auto* e) { e->check_err(g.side); });
+    return 0;
+  });
+}
+
+acr_status acr_batch_apply(acr_batch* b, const double* r, double* z, cudaStream_t stream) {
+  if (!b || !r || !z) return ACR_ERR_INVALID_ARG;
+  return guarded([&] {
+    batch_apply(b, r, z, stream);
+    return 0;
+  });
+}
+
+acr_status acr_batch_capture(acr_batch* b, const double* r, double* z, cudaStream_t stream) {
+  if (!b || !r || !z) return ACR_ERR_INVALID_ARG;
+  if (stream == 0) return ACR_ERR_INVALID_ARG;   // the legacy stream cannot be captured
+  return guarded([&] {
+    if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
+    if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
+    ACR_CUDA(cudaStreamBeginCapture(stream, cudaStreamCaptureModeRelaxed));
+    try {
+      batch_refactor(b, stream);
+      batch_apply(b, r, z, stream);
+    } catch (...) {
+      cudaGraph_t g = nullptr;
+      cudaStreamEndCapture(stream, &g);
+      if (g) cudaGraphDestroy(g);
+      throw;
+    }
+    ACR_CUDA(cudaStreamEndCapture(stream, &b->graph));
+    ACR_CUDA(cudaGraphInstantiate(&b->exec, b->graph, 0));
+    return 0;
+  });
+}
+
+acr_status acr_batch_replay(acr_batch* b, cudaStream_t stream) {
+  if (!b || !b->exec) return ACR_ERR_INVALID_ARG;
+  return guarded([&] {
+    ACR_CUDA(cudaGraphLaunch(b->exec, stream));
+    return 0;
+  });
+}
+
+acr_status acr_batch_krylov_solve(acr_batch* b, int32_t i, const double* coef, int32_t method,
+                                  int32_t restart, double rtol, int32_t maxit, const double* f,
+                                  double* u, acr_solve_info* info, cudaStream_t stream) {
+  if (!b || i < 0 || i >= b->count) return ACR_ERR_INVALID_ARG;
+  acr_grid g{b->n[i], b->n[i], b->n[i]};
+  return krylov_common(b->views[i], &g, coef, method, restart, rtol, maxit, f, u, info, stream);
+}
+
+acr_status acr_batch_get_info(const acr_batch* b, int32_t i, acr_setup_info* info) {
+  if (!b || !info || i < 0 || i >= b->count) return ACR_ERR_INVALID_ARG;
+  *info = b->groups[b->group_of[i]].e->info;
+  return ACR_OK;
+}
+
+void acr_batch_destroy(acr_batch* b) { delete b; }
 
 void acr_destroy(acr_handle* h) {
   if (!h) return;

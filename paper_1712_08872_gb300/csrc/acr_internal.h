@@ -17,9 +17,11 @@ enum Status {
 
 // Process-wide count of kernel launches made by the library.
 void count_launches(int64_t k);
+// Process-wide count of device and pinned-host allocations made by the library.
+void count_allocs(int64_t k);
 
 // Device-side error word bits (written by kernels, read by the host).
-enum : int { ERR_PIVOT = 1, ERR_RANKCAP = 2 };
+enum : int { ERR_PIVOT = 1, ERR_RANKCAP = 2, ERR_GROWTH = 4, ERR_TIMEOUT = 8 };
 
 struct CudaError {
   cudaError_t e;
@@ -46,11 +48,13 @@ void launch_ggemm(const Plan& pl, int gbeg, int gend, T* const* d_tab, const int
                   int P, const double* d_coefs, cudaStream_t st, double* d_flops = nullptr,
                   int tag = -1);
 
-// Pivoted-Cholesky orthonormalisation cores (FP64) of plan targets.
+// Pivoted-Cholesky orthonormalisation cores (FP64) of plan targets.  The
+// truncating pass counts targets and stacked-rank overflows of the sketch
+// into d_sketch_stat[0..1] (may be null).
 template <typename T>
 void launch_pchol(const Plan& pl, int tbeg, int tend, bool truncate, double tau,
                   T* const* d_tab, int* const* d_rtab, int P, cudaStream_t st,
-                  double* d_flops = nullptr);
+                  unsigned long long* d_sketch_stat, double* d_flops = nullptr);
 
 // Jacobi eigen cores (FP64) of plan targets; writes the kept ranks into
 // the rank buffer of role c_role and raises ERR_RANKCAP above kc.

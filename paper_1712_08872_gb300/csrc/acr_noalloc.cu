@@ -13,14 +13,14 @@
 //
 // The array is file-scope, so every GPU that loads the library holds its
 // kNoallocBytes until the process exits.  In host code its name is only a
-// host-side stand-in: the device address is obtained once per device with
-// cudaGetSymbolAddress and passed to the kernels.
+// host-side stand-in: the device address is obtained with
+// cudaGetSymbolAddress (in the calling thread's current device context, on
+// every call) and passed to the kernels.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <chrono>
 #include <cmath>
-#include <mutex>
 
 #include "acr.h"
 #include "acr_internal.h"
@@ -32,25 +32,15 @@ constexpr int kPartialPerVec = 600;                           // >= partial sums
 constexpr size_t kHead = 64 * kPartialPerVec + 64;            // partials + results (doubles)
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
 
-constexpr int kMaxDevices = 64;
-void* g_scratch_addr[kMaxDevices] = {nullptr};
-std::mutex g_scratch_mu;
-
-// Device address of the static array on the current device (set-up on the
-// first call per device).
+// Device address of the static array in the current device's context.  It
+// is looked up on every call (no allocation once the module is loaded): a
+// cached address would go stale if the context were torn down and created
+// again, and a kernel given a stale address would write to unowned memory.
 cudaError_t scratch_address(void** out) {
-  int dev = -1;
-  cudaError_t e = cudaGetDevice(&dev);
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lk(g_scratch_mu);
-  if (!g_scratch_addr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess) return e;
-    g_scratch_addr[dev] = p;
-  }
-  *out = g_scratch_addr[dev];
+  *out = p;
   return cudaSuccess;
 }
 

@@ -393,14 +393,22 @@ struct Builder {
       lt.bt = alloc((int64_t)n * p);
       for (LItem& li : lt.items) li.sp_off = alloc((int64_t)li.cap * p);
       TInfo& ti = lt.ti;
-      ti.g_off = alloc((int64_t)p * p);
+      ti.g_off = alloc((int64_t)pp.gram_scale * p * p);
       ti.t_off = alloc((int64_t)p * p);
-      ti.h_off = alloc((int64_t)p * p);
+      ti.h_off = alloc((int64_t)pp.gram_scale * p * p);
       ti.w_off = alloc((int64_t)p * p);
       ti.p = p; ti.m = m; ti.n = n;
       ti.r_ri = alloc_rank();
       ti.c_leaf = c.leaf;
       ti.seed = 0;
+      ti.sk_beg = (int)P.stack.size();
+      for (const LItem& li : lt.items) {
+        if (li.dense)
+          P.stack.push_back(StackDim{lsz, -1, 0, li.g0, li.g1});
+        else
+          P.stack.push_back(StackDim{li.k.st, li.k.rb, li.k.ri, li.xbuf, li.zbuf});
+      }
+      ti.sk_end = (int)P.stack.size();
       P.targets.push_back(ti);
     }
     for (size_t i = 0; i < lts.size(); ++i) P.targets[i].seed = (int)(1000003u * (uint32_t)(lts[i].node + 1));
@@ -591,9 +599,12 @@ void merge_plans(const std::vector<const Plan*>& ps, Plan& out) {
     toff[i] = (int)out.targets.size();
     out.scratch += ps[i]->scratch;
     out.scratch_ranks += ps[i]->scratch_ranks;
+    const int sk0 = (int)out.stack.size();
+    out.stack.insert(out.stack.end(), ps[i]->stack.begin(), ps[i]->stack.end());
     for (TInfo ti : ps[i]->targets) {
       ti.g_off += soff[i]; ti.t_off += soff[i]; ti.h_off += soff[i]; ti.w_off += soff[i];
       ti.r_ri += roff[i];
+      ti.sk_beg += sk0; ti.sk_end += sk0;
       out.targets.push_back(ti);
     }
     out.n_lr_targets += ps[i]->n_lr_targets;

@@ -65,11 +65,20 @@ struct GGroup {
 
 // one low-rank target of phase 2 (core kernels)
 struct TInfo {
-  int64_t g_off, t_off, h_off, w_off;  // scratch offsets (p x p each, ld p)
+  int64_t g_off, t_off, h_off, w_off;  // scratch offsets (p x p each, ld p; the Grams
+                                       // at g_off, h_off are FP64)
   int32_t p, m, n;
   int32_t r_ri;        // scratch rank slot receiving the orthonormal-basis size
   int32_t c_leaf;      // low-rank leaf index of C (rank output)
   int32_t seed;
+  int32_t sk_beg, sk_end;  // the summed terms' inner dimensions: Plan::stack entries
+};
+
+// One summed term of a low-rank target, for the stacked-rank count: its
+// inner dimension (constant st or rank[ri] of rank buffer rb) and the two
+// operand buffers that must be present for the term to exist (-1: none).
+struct StackDim {
+  int32_t st, rb, ri, g0, g1;
 };
 
 enum StageKind { ST_GEMM = 0, ST_PCHOL = 1, ST_EIG = 2 };
@@ -114,6 +123,7 @@ struct Plan {
   std::vector<GGroup> groups;
   std::vector<GItem> items;
   std::vector<TInfo> targets;
+  std::vector<StackDim> stack;
   std::vector<Stage> stages;
   int64_t scratch = 0;        // real scratch elements per plane
   int32_t scratch_ranks = 0;  // int scratch entries per plane
@@ -124,12 +134,14 @@ struct Plan {
   void* d_groups = nullptr;
   void* d_items = nullptr;
   void* d_targets = nullptr;
+  void* d_stack = nullptr;
 };
 
 struct PlanParams {
   int kc;        // rank capacity of stored low-rank blocks
   int oversample;
   bool cholqr2;  // second orthonormalisation pass (single-precision forms)
+  int gram_scale = 1;   // storage elements per Gram entry: Grams are FP64 (2 for float)
 };
 
 // Build the plan of one formatted operation.

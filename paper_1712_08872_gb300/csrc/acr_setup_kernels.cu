@@ -590,22 +590,150 @@ __global__ void __launch_bounds__(NT, sizeof(Acc) == 4 ? 4 : 1) k_gdot_warp(cons
   if (flops && lane == 0 && fl > 0) atomicAdd(flops, (double)fl);
 }
 
+// Gram matrices C = Y^T Y of float columns (the range finder's sketch and
+// basis Grams and the core Gram) with FP64 results.  The rank decisions that
+// follow resolve singular values only down to sqrt(relative Gram error)
+// times the largest one, so a float-accumulated Gram (error ~1e-7) stops at
+// ~3e-4; here every product is exact (a*b split into its rounded value and
+// FMA remainder) and the sums are compensated (TwoSum per lane, float-float
+// state), then the lanes' results are combined in double: the relative
+// error is ~1e-14 of sum |y_i||y_j|, so the Grams resolve singular values
+// down to the float data's own noise (~1e-7).  Upper-triangle 4 x 4 tiles
+// per warp (the result is mirrored), lanes striding the contraction.
+__device__ __forceinline__ void ff_fma(float& s, float& c, float a, float b) {
+  const float p = a * b;
+  const float e = fmaf(a, b, -p);      // a*b = p + e exactly
+  const float t = s + p;               // TwoSum(s, p)
+  const float bp = t - s;
+  c += ((s - (t - bp)) + (p - bp)) + e;
+  s = t;
+}
+
+// One CTA per Gram: the columns of Y pass through shared memory in chunks of
+// 64 rows; thread (tile, slice) owns a 4 x 4 tile of the upper triangle and
+// the rows slice, slice + S, ... of every chunk; the float-float partials
+// are combined in double, slices summed in a fixed order.
+constexpr int GRAM_KCH = 64;
+
+__global__ void __launch_bounds__(NT) k_gram_ff(const GGroup* __restrict__ groups,
+                                                const GItem* __restrict__ items,
+                                                float* const* __restrict__ tab,
+                                                const int* const* __restrict__ rtab, int P,
+                                                int gbase, double* __restrict__ flops) {
+  const int p = blockIdx.y;
+  const GGroup G = groups[gbase + blockIdx.x];
+  float* Cf = tab[G.cbuf * P + p];
+  if (!Cf) return;
+  const int m = dimv(G.m_st, G.m_rb, G.m_ri, rtab, P, p);
+  if (m <= 0 || m > 64 || G.ie <= G.ib) return;
+  double* C = reinterpret_cast<double*>(Cf + G.coff);
+  const GItem I = items[G.ib];
+  const float* Y = tab[I.abuf * P + p];
+  if (!Y) return;
+  Y += I.aoff;
+  const int k = dimv(I.k_st, I.k_rb, I.k_ri, rtab, P, p);
+  const int ld = I.lda;
+  // ys[column][row of the chunk] during the sweep; then the per-thread tile
+  // results red[thread][16] in the same storage
+  __shared__ __align__(16) double raw[NT * 16];
+  double (*red)[16] = reinterpret_cast<double (*)[16]>(raw);
+  const int TM = (m + 3) >> 2, ntile = TM * (TM + 1) / 2;
+  // rows per chunk: the staged columns (4 TM of them) fill the buffer
+  const int kch = TM <= 4 ? 4 * GRAM_KCH : (TM <= 8 ? 2 * GRAM_KCH : GRAM_KCH);
+  float* ysb = reinterpret_cast<float*>(raw);   // ys(col, row) = ysb[col * (kch + 1) + row]
+  static_assert(64 * (GRAM_KCH + 1) * sizeof(float) <= NT * 16 * sizeof(double), "staging fits");
+  static_assert(32 * (2 * GRAM_KCH + 1) * sizeof(float) <= NT * 16 * sizeof(double), "staging fits");
+  static_assert(16 * (4 * GRAM_KCH + 1) * sizeof(float) <= NT * 16 * sizeof(double), "staging fits");
+  const int S = NT / ntile >= 1 ? NT / ntile : 1;   // ntile <= 136 < NT
+  const int tid = threadIdx.x;
+  const int tile0 = tid / S, slice = tid - tile0 * S;
+  const bool active = tile0 < ntile;
+  int ti = 0, tile = active ? tile0 : 0;
+  while (tile >= TM - ti) { tile -= TM - ti; ++ti; }   // upper triangle: tj >= ti
+  const int i0 = 4 * ti, j0 = 4 * (ti + tile);
+  if (flops && tid == 0 && k > 0) atomicAdd(flops, 2.0 * m * m * k);
+  float s[4][4], c[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) { s[a][b] = 0.f; c[a][b] = 0.f; }
+  const int mt = 4 * TM;   // columns the tiles read (>= m: the rest read as 0)
+  const int ysld = kch + 1;
+  for (int e = m * kch + tid; e < mt * kch; e += NT) ysb[(e / kch) * ysld + e % kch] = 0.f;
+  for (int l0 = 0; l0 < k; l0 += kch) {
+    const int kk = min(kch, k - l0);
+    __syncthreads();
+    for (int e = tid; e < m * kch; e += NT) {
+      const int col = e / kch, l = e - col * kch;
+      ysb[col * ysld + l] = l < kk ? Y[(l0 + l) + (int64_t)col * ld] : 0.f;
+    }
+    __syncthreads();
+    if (active)
+      for (int l = slice; l < kk; l += S) {
+        float av[4], bv[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          av[a] = ysb[(i0 + a) * ysld + l];
+          bv[a] = ysb[(j0 + a) * ysld + l];
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) ff_fma(s[a][b], c[a][b], av[a], bv[b]);
+      }
+  }
+  __syncthreads();   // every thread is done with ys
+#pragma unroll
+  for (int e = 0; e < 16; ++e)
+    red[tid][e] = active ? (double)s[e & 3][e >> 2] + (double)c[e & 3][e >> 2] : 0.0;
+  __syncthreads();
+  for (int e = tid; e < ntile * 16; e += NT) {
+    const int t = e >> 4, q = e & 15;
+    double v = 0.0;
+    for (int sl = 0; sl < S; ++sl) v += red[t * S + sl][q];
+    int tt = t, a = 0;
+    while (tt >= TM - a) { tt -= TM - a; ++a; }
+    const int i = 4 * a + (q & 3), j = 4 * (a + tt) + (q >> 2);
+    if (i < m && j < m) {
+      C[i + (int64_t)j * G.ldc] = v;
+      C[j + (int64_t)i * G.ldc] = v;
+    }
+  }
+}
+
 // ---------------------------------------------------------------- cores
 constexpr int CMAX = 64;   // largest sketch / core dimension
 
 // Pivoted Cholesky of G (pd x pd): G = P L L^T P^T, stop when the largest
 // remaining diagonal <= tau^2 * max diag(G) (truncating pass).  Writes
 // T (p x r, ld p) with Q = Y T orthonormal, and r.
+//
+// The truncating pass also counts the target (sketch_stat[0]) and, when the
+// stacked rank of its summed terms exceeds the sketch width p, the range
+// finder's inexact case (sketch_stat[1]).
 template <typename T>
 __global__ void __launch_bounds__(NT) k_pchol(const TInfo* __restrict__ tis, int tbase, bool truncate,
                                               double tau, T* const* __restrict__ tab,
                                               int* const* __restrict__ rtab, int P, int scr_buf,
-                                              int scr_rbuf, double* __restrict__ flops) {
+                                              int scr_rbuf, const StackDim* __restrict__ stack,
+                                              unsigned long long* __restrict__ sketch_stat,
+                                              double* __restrict__ flops) {
   const int p = blockIdx.y;
   const TInfo ti = tis[tbase + blockIdx.x];
   T* scr = tab[scr_buf * P + p];
   int* rs = rtab[scr_rbuf * P + p];
   if (!scr || !rs) return;
+  if (truncate && sketch_stat && threadIdx.x == 0) {
+    int64_t stacked = 0;
+    for (int e = ti.sk_beg; e < ti.sk_end; ++e) {
+      const StackDim sd = stack[e];
+      if (sd.g0 >= 0 && !tab[sd.g0 * P + p]) continue;
+      if (sd.g1 >= 0 && !tab[sd.g1 * P + p]) continue;
+      stacked += dimv(sd.st, sd.rb, sd.ri, rtab, P, p);
+    }
+    atomicAdd(sketch_stat, 1ull);
+    if (stacked > ti.p) atomicAdd(sketch_stat + 1, 1ull);
+  }
   const int ld = ti.p;
   const int pd = truncate ? ti.p : rs[ti.r_ri];
   extern __shared__ double dsm[];
@@ -615,7 +743,7 @@ __global__ void __launch_bounds__(NT) k_pchol(const TInfo* __restrict__ tis, int
   __shared__ double colbuf[CMAX];
   __shared__ int piv[CMAX];
   __shared__ double sv[NT];
-  const T* G = scr + ti.g_off;
+  const double* G = reinterpret_cast<const double*>(scr + ti.g_off);   // FP64 Gram
   T* Tm = scr + ti.t_off;
   for (int e = threadIdx.x; e < pd * pd; e += NT) {
     int i = e % pd, j = e / pd;
@@ -752,7 +880,7 @@ __global__ void __launch_bounds__(NT) k_eig(const TInfo* __restrict__ tis, int t
   __shared__ int order[CMAX];
   __shared__ double lam[CMAX];
   __shared__ int kkeep;
-  const T* H = scr + ti.h_off;
+  const double* H = reinterpret_cast<const double*>(scr + ti.h_off);   // FP64 Gram
   T* W = scr + ti.w_off;
   for (int e = threadIdx.x; e < r * r; e += NT) {
     int i = e % r, j = e / r;
@@ -889,6 +1017,28 @@ __global__ void __launch_bounds__(NT) k_eig(const TInfo* __restrict__ tis, int t
   }
 }
 
+// Largest |a| over the block (every thread passes its own candidate).
+__device__ __forceinline__ double block_absmax(double v, double* red8) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if ((threadIdx.x & 31) == 0) red8[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double r = red8[0];
+  for (int w = 1; w < NT / 32; ++w) r = fmax(r, red8[w]);
+  __syncthreads();
+  return r;
+}
+
+// Breakdown bound on the growth max|A| * max|A^-1| of a dense leaf inverse
+// (a lower bound on the condition number over n^2).  The leaf is read from
+// its storage precision, whose rounding u perturbs it by ~u relatively, so
+// the inverse keeps about -log10(growth * u) correct digits: the bound is
+// 1e10 for FP64 storage (6 digits kept) and 1e6 for float storage (about
+// one digit).  This is how an indefinite plane (Sec. 8) whose leaf nearly
+// meets an eigenvalue is caught, not only an exactly zero pivot.
+template <typename T>
+__host__ __device__ constexpr double leaf_growth_max() { return sizeof(T) == 8 ? 1e10 : 1e6; }
+
 // In-place Gauss-Jordan inverse with partial pivoting, FP64, n <= 64.
 // Per elimination step warp 0 finds the pivot with shuffles, takes the one
 // reciprocal of the step and publishes the scaled pivot row, the displaced
@@ -910,11 +1060,17 @@ __global__ void __launch_bounds__(NT) k_leaf_inv(T* const* __restrict__ dense, i
   __shared__ int cmap[CMAX];
   __shared__ int s_q, s_bad;
   __shared__ double s_pinv;
+  __shared__ double red8[NT / 32];
   const int ti = threadIdx.x & 63, tj = threadIdx.x >> 6;
+  double amax = 0.0;
   for (int j = tj; j < n; j += 4)
-    if (ti < n) A[ti][j] = (double)Ap[ti + (int64_t)j * n];
+    if (ti < n) {
+      A[ti][j] = (double)Ap[ti + (int64_t)j * n];
+      amax = fmax(amax, fabs(A[ti][j]));
+    }
   if (threadIdx.x == 0) s_bad = 0;
   __syncthreads();
+  amax = block_absmax(amax, red8);
   for (int k = 0; k < n; ++k) {
     if (threadIdx.x < 32) {
       const int lane = threadIdx.x;
@@ -962,6 +1118,18 @@ __global__ void __launch_bounds__(NT) k_leaf_inv(T* const* __restrict__ dense, i
   }
   if (s_bad) {
     if (threadIdx.x == 0) atomicOr(err, ERR_PIVOT);
+    return;
+  }
+  // pivot growth of the computed inverse (a NaN or Inf entry fails too)
+  double xmax = 0.0;
+  for (int j = tj; j < n; j += 4)
+    if (ti < n) {
+      const double v = fabs(A[ti][j]);
+      xmax = (v <= 1.7976931348623157e308) ? fmax(xmax, v) : INFINITY;   // NaN, Inf -> Inf
+    }
+  xmax = block_absmax(xmax, red8);
+  if (!(amax * xmax <= leaf_growth_max<T>())) {
+    if (threadIdx.x == 0) atomicOr(err, ERR_GROWTH);
     return;
   }
   if (threadIdx.x == 0) {
@@ -1102,7 +1270,9 @@ void launch_ggemm(const Plan& pl, int gbeg, int gend, T* const* d_tab, const int
     // warp per group for the inner products, and for the small-output
     // sketch / projection stages where the multiply type is float (the FP64
     // instance of the warp kernel holds ~200 registers: one CTA per SM)
-    if (tag == TAG_M || (sizeof(T) == 4 && (tag == TAG_S || tag == TAG_P))) {
+    if (sizeof(T) == 4 && (tag == TAG_G || tag == TAG_G2 || tag == TAG_H)) {
+      k_gram_ff<<<grid, NT, 0, st>>>(gr, it, (float* const*)d_tab, d_rtab, P, gbeg + g0, d_fl);
+    } else if (tag == TAG_M || (sizeof(T) == 4 && (tag == TAG_S || tag == TAG_P))) {
       const int cnt = std::min(maxg, ng - g0);
       dim3 gw((cnt + NT / 32 - 1) / (NT / 32), P);
       k_gdot_warp<T, Acc><<<gw, NT, 0, st>>>(gr, it, d_tab, d_rtab, P, gbeg + g0, gbeg + g0 + cnt,
@@ -1117,7 +1287,8 @@ void launch_ggemm(const Plan& pl, int gbeg, int gend, T* const* d_tab, const int
 
 template <typename T>
 void launch_pchol(const Plan& pl, int tbeg, int tend, bool truncate, double tau, T* const* d_tab,
-                  int* const* d_rtab, int P, cudaStream_t st, double* d_fl) {
+                  int* const* d_rtab, int P, cudaStream_t st, unsigned long long* d_sketch_stat,
+                  double* d_fl) {
   int nt = tend - tbeg;
   if (nt <= 0 || P <= 0) return;
   const size_t smem = 2 * CMAX * (CMAX + 1) * sizeof(double);
@@ -1125,7 +1296,8 @@ void launch_pchol(const Plan& pl, int tbeg, int tend, bool truncate, double tau,
   for (int t0 = 0; t0 < nt; t0 += 65535) {
     dim3 grid(std::min(65535, nt - t0), P);
     k_pchol<T><<<grid, NT, smem, st>>>((const TInfo*)pl.d_targets, tbeg + t0, truncate, tau, d_tab,
-                                    d_rtab, P, 3 * pl.nroles, pl.nroles, d_fl);
+                                    d_rtab, P, 3 * pl.nroles, pl.nroles,
+                                    (const StackDim*)pl.d_stack, d_sketch_stat, d_fl);
     ACR_LAUNCHED(1);
   }
 }
@@ -1188,7 +1360,7 @@ void launch_plane_to_h(const StructDev& sd, const double* coef, int n, const int
   template void launch_ggemm<T>(const Plan&, int, int, T* const*, const int* const*, int,        \
                                 const double*, cudaStream_t, double*, int);                      \
   template void launch_pchol<T>(const Plan&, int, int, bool, double, T* const*, int* const*, int, \
-                                cudaStream_t, double*);                                          \
+                                cudaStream_t, unsigned long long*, double*);                     \
   template void launch_eig<T>(const Plan&, int, int, double, int, int, T* const*, int* const*,   \
                               int, int*, cudaStream_t, double*);                                 \
   template void launch_leaf_inv<T>(T* const*, int64_t, int, int, int*, cudaStream_t, double*);   \

@@ -24,3 +24,17 @@ def pytest_collection_modifyitems(config, items):
     for item in items:
         if "gpu" in item.keywords:
             item.add_marker(skip)
+
+
+@pytest.fixture(scope="session")
+def parity_log():
+    """Record measured parity figures: appends one JSON object per call to
+    the file named by ACR_PARITY_LOG (nothing when it is unset)."""
+    import json
+    path = os.environ.get("ACR_PARITY_LOG")
+
+    def log(**rec):
+        if path:
+            with open(path, "a") as fh:
+                fh.write(json.dumps(rec, default=float) + "\n")
+    return log

@@ -36,10 +36,15 @@ def test_noalloc_cg_matches_allocating_entry_point():
         f = uniform_rhs(n, 40 + call)
         fd = torch.tensor(f, dtype=torch.float64, device=dev)
         u_ref = torch.zeros_like(fd)
+        a0 = acr.acr_alloc_count()
         info_ref, s_ref = acr.acr_krylov_solve_plain(n, coef, acr.ACR_PCG, 0, rtol, 2000, fd, u_ref)
+        a1 = acr.acr_alloc_count()
         u = torch.zeros_like(fd)
         info, s = acr.acr_krylov_solve_plain_noalloc(n, coef, rtol, 2000, fd, u)
         torch.cuda.synchronize()
+        # the allocating entry point allocates; the new one makes no
+        # allocation of the library's (device or pinned host)
+        assert a1 > a0 and acr.acr_alloc_count() == a1
         assert s == 0 and s_ref == 0
         assert info.iterations == info_ref.iterations
         uh, ur = u.cpu().numpy(), u_ref.cpu().numpy()
