@@ -263,9 +263,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="acr", choices=["acr", "reference"])
     ap.add_argument("--n", type=int, default=128)
-    ap.add_argument("--fp64-steps", type=int, default=1)
-    ap.add_argument("--e2e-steps", type=int, default=1)
-    ap.add_argument("--bf16-steps", type=int, default=1)
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--bf16-steps", type=int, default=3)
+    ap.add_argument("--no-config1", action="store_true",
+                    help="skip the n=64 high-contrast boxes comparison of the three forms")
+    ap.add_argument("--no-mixed-batch", action="store_true",
+                    help="skip the 12-instance mixed batch under a captured graph")
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the multi-right-hand-side measurements")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -351,6 +355,7 @@ def main():
     # FP64 plain form on the same GPU
     fp64 = None
     if args.fp64_steps > 0:
+        step(acr.ACR_FP64)                       # warm-up
         ms64, inf64, _ = timed(acr.ACR_FP64, args.fp64_steps)
         fp64 = {"s": ms64 / 1000.0, "iterations": inf64[-1][0].iterations,
                 "setup_ms": inf64[-1][1].setup_ms, "max_rank": inf64[-1][1].max_rank,
@@ -359,6 +364,7 @@ def main():
     # BF16-stored factors (setup as FP32, factors rounded to bfloat16)
     bf16 = None
     if args.bf16_steps > 0:
+        step(acr.ACR_BF16)                       # warm-up
         msb, infb, _ = timed(acr.ACR_BF16, args.bf16_steps)
         bf16 = {"s": msb / 1000.0, "iterations": infb[-1][0].iterations,
                 "rel_residual": infb[-1][0].rel_residual, "setup_ms": infb[-1][1].setup_ms,
@@ -374,8 +380,9 @@ def main():
         barrier()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(args.e2e_steps):
+        for it in range(args.e2e_steps + 1):     # the first pass is a warm-up
+            if it == 1:
+                e0.record(stream)
             bd = beta_h.to(dev, non_blocking=True)
             fd = f_h.to(dev, non_blocking=True)
             cf = torch.empty(7 * N, dtype=torch.float64, device=dev)
@@ -506,11 +513,110 @@ def main():
                                "one_at_a_time_solve_s": e2.elapsed_time(e3) / 1000.0,
                                "one_at_a_time_max_iterations": its_seq}}
 
+    # config 1: high-contrast boxes at n = 64, the three forms, PCG to 1e-8
+    config1 = None
+    if not args.no_config1:
+        cs, kap, fb = workload("poisson_boxes_n64")
+        nb = cs["n"]
+        cb = torch.empty(7 * nb ** 3, dtype=torch.float64, device=dev)
+        acr.acr_stencil_poisson(nb, torch.tensor(kap, dtype=torch.float64, device=dev), cb)
+        fbd = torch.tensor(fb, dtype=torch.float64, device=dev)
+        config1 = {"workload": "poisson_boxes_n64 (40 boxes kappa 1e4, eps 1e-2, leaf 64, "
+                               "PCG to 1e-8, maxit 1000)"}
+        for name, prec in (("fp64", acr.ACR_FP64), ("fp32", acr.ACR_FP32), ("bf16", acr.ACR_BF16)):
+            res = None
+            for rep in range(2):                 # warm-up, then the timed run
+                barrier()
+                ea, eb, ec = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+                ea.record(stream)
+                hb = acr.acr_setup(nb, cb, cs["eps"], 2.0, cs["leaf"], prec, args.rank_cap, stream)
+                eb.record(stream)
+                ub = torch.zeros(nb ** 3, dtype=torch.float64, device=dev)
+                ib, sb = acr.acr_krylov_solve(hb, cb, acr.ACR_PCG, 0, cs["rtol"], 1000, fbd, ub,
+                                              stream, check=False)
+                ec.record(stream)
+                torch.cuda.synchronize()
+                acr.acr_destroy(hb)
+                res = {"s": ea.elapsed_time(ec) / 1000.0, "setup_s": ea.elapsed_time(eb) / 1000.0,
+                       "solve_s": eb.elapsed_time(ec) / 1000.0, "iterations": ib.iterations,
+                       "converged": bool(ib.converged), "rel_residual": ib.rel_residual}
+            config1[name] = res
+
+    # config 3 (second half): 12 kappa-Poisson instances at n in {32, 48, 64}
+    # in one batch; the setup + apply of all 12 captured in a CUDA graph
+    mixed = None
+    if not args.no_mixed_batch:
+        from inputs import gaussian_field_kappa, uniform_rhs
+        ns = [32, 48, 64] * 4
+        cfs = []
+        for i, nn in enumerate(ns):
+            c = torch.empty(7 * nn ** 3, dtype=torch.float64, device=dev)
+            acr.acr_stencil_poisson(nn, torch.tensor(gaussian_field_kappa(nn, 40 + i),
+                                                     dtype=torch.float64, device=dev), c)
+            cfs.append(c)
+        rb = torch.tensor(np.concatenate([uniform_rhs(nn, 100 + i) for i, nn in enumerate(ns)]),
+                          dtype=torch.float64, device=dev)
+        zb = torch.empty_like(rb)
+        gs = torch.cuda.Stream(device=dev)
+        barrier()
+        t0 = time.perf_counter()
+        bt = acr.acr_batch_create(ns, cfs, 1e-2, 2.0, 64, acr.ACR_FP32, args.rank_cap, gs)
+        create_s = time.perf_counter() - t0
+        acr.acr_batch_capture(bt, rb, zb, gs)
+        acr.acr_batch_replay(bt, gs)             # warm-up
+        acr.acr_batch_status(bt, gs)
+        ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 3
+        ea.record(gs)
+        for _ in range(reps):
+            acr.acr_batch_replay(bt, gs)
+        eb.record(gs)
+        acr.acr_batch_status(bt, gs)
+        graph_ms = ea.elapsed_time(eb) / reps
+        acr.acr_batch_destroy(bt)
+        # the same 12 problems as separate handles (setup + one apply each)
+        barrier()
+        ea.record(stream)
+        o = 0
+        for i, nn in enumerate(ns):
+            hs_ = acr.acr_setup(nn, cfs[i], 1e-2, 2.0, 64, acr.ACR_FP32, args.rank_cap, stream)
+            acr.acr_apply(hs_, rb[o:o + nn ** 3], zb[o:o + nn ** 3], 1, stream)
+            acr.acr_destroy(hs_)
+            o += nn ** 3
+        eb.record(stream)
+        torch.cuda.synchronize()
+        mixed = {"workload": "12 kappa-Poisson instances (Gaussian field, seeds 40-51), "
+                             "n = 32, 48, 64 x 4, FP32, eps 1e-2, leaf 64",
+                 "create_s": create_s, "graph_setup_apply_s": graph_ms / 1000.0,
+                 "separate_handles_setup_apply_s": ea.elapsed_time(eb) / 1000.0}
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         dt, it = oracle_sample()
+        # the GPU on the very same sample (n = 32 instance of the recipe),
+        # measured in this run: the like-for-like comparison
+        sp, sb_, sf = workload("codi_n128", n=32)
+        c32 = torch.empty(7 * 32 ** 3, dtype=torch.float64, device=dev)
+        acr.acr_stencil_codi(32, torch.tensor(sb_.ravel(), dtype=torch.float64, device=dev), c32)
+        f32d = torch.tensor(sf, dtype=torch.float64, device=dev)
+        gpu32 = []
+        for rep in range(4):
+            barrier()
+            ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ea.record(stream)
+            h32 = acr.acr_setup(32, c32, eps, eta, leaf, acr.ACR_FP32, args.rank_cap, stream)
+            u32 = torch.zeros(32 ** 3, dtype=torch.float64, device=dev)
+            acr.acr_krylov_solve(h32, c32, acr.ACR_GMRES, restart, rtol, 1000, f32d, u32, stream)
+            acr.acr_destroy(h32)
+            eb.record(stream)
+            torch.cuda.synchronize()
+            if rep > 0:
+                gpu32.append(ea.elapsed_time(eb) / 1000.0)
+        g32 = statistics.median(gpu32)
         cpu = {"value": dt * oracle_scale(), "unit": "s", "cores": cpu_cores(), "kind": "oracle",
-               "sample": SAMPLE_DESC, "sample_seconds": dt}
+               "sample": SAMPLE_DESC, "sample_seconds": dt,
+               "same_sample": {"n": 32, "oracle_s": dt, "gpu_fp32_s": g32,
+                               "oracle_over_gpu": dt / g32}}
 
     value = seconds_per_solve(ms, world)
     line = {"metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": args.steps,
@@ -528,7 +634,7 @@ def main():
             "speedup_vs_fp64": (fp64["s"] / (ms / 1000.0)) if fp64 else None,
             "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks,
             "roofline": roof, "apply_roofline": apply_roof, "batching": batch,
-            "cpu_baseline": cpu}
+            "config1_boxes_n64": config1, "mixed_batch": mixed, "cpu_baseline": cpu}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
