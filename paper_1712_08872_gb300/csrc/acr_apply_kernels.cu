@@ -352,6 +352,70 @@ __global__ void k_to_bf16(const float* __restrict__ in, __nv_bfloat16* __restric
     out[e] = __float2bfloat16_rn(in[e]);
 }
 
+// Projections for a group of 32 right-hand sides: warp w takes (leaf,
+// column) pairs w, w + 8, ...; lane rr owns right-hand side rr and sums the
+// 64 products of the column with its x chunk (factor entries are broadcast
+// loads, the x chunk is staged as xs[row][rr]); two 32-product float partial
+// sums per output, combined in FP64.
+template <typename T>
+__global__ void __launch_bounds__(256) k_lr_proj32(MatvecDev mv, T* const* __restrict__ U,
+                                                   T* const* __restrict__ V,
+                                                   const int* const* __restrict__ rank,
+                                                   const double* const* __restrict__ x,
+                                                   double* tv, bool trans, int64_t vs) {
+  constexpr int R = 32;
+  __shared__ float xs[64][R + 1];
+  __shared__ int64_t s_off[MAXQ];
+  __shared__ int s_ld[MAXQ], s_seg[MAXQ], s_cum[MAXQ + 1];
+  const int c = blockIdx.x, p = blockIdx.y;
+  const T* Fb = trans ? U[p] : V[p];
+  const double* xp = x[p];
+  if (!Fb || !xp) return;
+  const int lsz = mv.lsz, kc = mv.kc;
+  const int* ptr = trans ? mv.l_ptr : mv.lt_ptr;
+  const int* lf = trans ? mv.l_leaf : mv.lt_leaf;
+  const int* lo = trans ? mv.l_rowoff : mv.lt_coloff;
+  const int* sptr = trans ? mv.segt_ptr : mv.seg_ptr;
+  const int nseg = trans ? mv.nsegt : mv.nseg;
+  const int q0 = ptr[c], nq = min(ptr[c + 1] - q0, MAXQ);
+  for (int e = threadIdx.x; e < R * lsz; e += 256) {
+    const int rr = e / lsz, i = e - rr * lsz;
+    xs[i][rr] = (float)xp[rr * vs + (int64_t)c * lsz + i];
+  }
+  for (int q = threadIdx.x; q < nq; q += 256) {
+    const int l = lf[q0 + q];
+    s_cum[q + 1] = rank[p][l];
+    s_ld[q] = trans ? mv.lr_m[l] : mv.lr_n[l];
+    s_off[q] = (trans ? mv.lr_row0[l] : mv.lr_col0[l]) * kc + lo[q0 + q];
+    s_seg[q] = sptr[l] + lo[q0 + q] / lsz;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    s_cum[0] = 0;
+    for (int q = 0; q < nq; ++q) s_cum[q + 1] += s_cum[q];
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, rr = threadIdx.x & 31;
+  const int total = s_cum[nq];
+  for (int t = warp; t < total; t += 8) {
+    int lo_q = 0, hi_q = nq;   // the q with s_cum[q] <= t < s_cum[q + 1]
+    while (hi_q - lo_q > 1) {
+      const int mid = (lo_q + hi_q) >> 1;
+      if (s_cum[mid] <= t) lo_q = mid; else hi_q = mid;
+    }
+    const int q = lo_q, j = t - s_cum[q];
+    const T* col = Fb + s_off[q] + (int64_t)j * s_ld[q];
+    float a0 = 0.f, a1 = 0.f;
+    const int h = lsz >> 1;
+    for (int i = 0; i < h; ++i) {
+      a0 += (float)ld(col[i]) * xs[i][rr];
+      a1 += (float)ld(col[i + h]) * xs[i + h][rr];
+    }
+    for (int i = 2 * h; i < lsz; ++i) a1 += (float)ld(col[i]) * xs[i][rr];
+    tv[(((int64_t)p * nseg + s_seg[q]) * kc + j) * R + rr] = (double)a0 + (double)a1;
+  }
+}
+
 }  // namespace
 
 void launch_to_bf16(const float* in, void* out, int64_t count, cudaStream_t st) {
@@ -406,6 +470,24 @@ void launch_hmatvec(const MatvecDev& mv, T* const* dense, T* const* U, T* const*
     default: throw CudaError{cudaErrorInvalidValue, "right-hand-side group must be 1, 2, 4 or 8"};
   }
 }
+
+template <typename T>
+void launch_lr_proj(const MatvecDev& mv, T* const* U, T* const* V, const int* const* rank,
+                    const double* const* x, double* tv, bool trans, int P, int nr, int64_t vs,
+                    cudaStream_t st) {
+  if (P <= 0 || mv.nl <= 0) return;
+  if (nr != 32) throw CudaError{cudaErrorInvalidValue, "projection group of 32 expected"};
+  k_lr_proj32<T><<<dim3(mv.nchunks, P), 256, 0, st>>>(mv, U, V, rank, x, tv, trans, vs);
+  ACR_LAUNCHED(1);
+}
+
+template void launch_lr_proj<float>(const MatvecDev&, float* const*, float* const*,
+                                    const int* const*, const double* const*, double*, bool, int,
+                                    int, int64_t, cudaStream_t);
+template void launch_lr_proj<__nv_bfloat16>(const MatvecDev&, __nv_bfloat16* const*,
+                                            __nv_bfloat16* const*, const int* const*,
+                                            const double* const*, double*, bool, int, int, int64_t,
+                                            cudaStream_t);
 
 void launch_permute(const double* in, double* out, const int* perm, int n2, int nplanes,
                     bool to_cluster, cudaStream_t st) {

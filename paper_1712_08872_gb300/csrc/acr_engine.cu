@@ -282,6 +282,13 @@ class Engine : public EngineBase {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   // apply work
   double *Fv = nullptr, *Gv = nullptr, *Uv = nullptr, *Tv = nullptr, *tvscr = nullptr;
+  // 32 right-hand sides per pass on the tensor cores (allocated on first use)
+  double *Fw = nullptr, *Gw = nullptr, *Uw = nullptr, *Tw = nullptr, *tvw = nullptr;
+  static constexpr int RW = 32;
+  bool wide_ok() const {
+    return !std::is_same<T, double>::value && S.lsz == 64 && mvd.max_l <= 256 && count == 1;
+  }
+  void ensure_wide();
   struct ApplyStep {
     int kind;                        // 0 hmatvec, 1 diag update, 2 copy
     int P;
@@ -292,6 +299,7 @@ class Engine : public EngineBase {
   struct Program { std::vector<ApplyStep> fwd, bwd, fwdT, bwdT; };
   Program prog_all;                  // every instance at once
   std::vector<Program> prog_inst;    // one instance (count > 1)
+  Program prog_wide;                 // 32 right-hand sides, tensor cores
   int maxP = 1;
   std::map<const void*, int64_t> hm_used;   // stored entries an apply reads per H-matrix
 
@@ -688,9 +696,10 @@ class Engine : public EngineBase {
   }
 
   void build_apply_program();
-  void build_program(Program& pg, int inst, bool count_bytes);
-  void run_program(const Program& pg, bool trans, int nr, cudaStream_t st);
-  void run_steps(const std::vector<ApplyStep>& steps, int nr, cudaStream_t st);
+  void build_program(Program& pg, int inst, bool count_bytes, double* F, double* G, double* Uu,
+                     double* Tt);
+  void run_program(const Program& pg, bool trans, int nr, cudaStream_t st, double* tv);
+  void run_steps(const std::vector<ApplyStep>& steps, int nr, cudaStream_t st, double* tv);
   static constexpr int RB = 8;       // right-hand sides per apply pass (multi-RHS apply)
   int64_t tvs = 0;                   // doubles of projection scratch per right-hand side
   void collect_info();
@@ -1157,18 +1166,30 @@ void Engine<T>::build_apply_program() {
   tvs = (int64_t)maxP * std::max({mvd.nseg, mvd.nsegt, 1}) * kc;
   tvscr = (double*)dmalloc(sizeof(double) * (size_t)tvs * rb);
   owned.push_back(tvscr);
-  build_program(prog_all, -1, true);
+  build_program(prog_all, -1, true, Fv, Gv, Uv, Tv);
   prog_inst.clear();
   if (count > 1) {
     prog_inst.resize(count);
-    for (int i = 0; i < count; ++i) build_program(prog_inst[i], i, false);
+    for (int i = 0; i < count; ++i) build_program(prog_inst[i], i, false, Fv, Gv, Uv, Tv);
   }
+}
+
+template <typename T>
+void Engine<T>::ensure_wide() {
+  if (Fw) return;
+  Fw = (double*)dmalloc(sizeof(double) * N * RW); owned.push_back(Fw);
+  Gw = (double*)dmalloc(sizeof(double) * N * RW); owned.push_back(Gw);
+  Uw = (double*)dmalloc(sizeof(double) * N * RW); owned.push_back(Uw);
+  Tw = (double*)dmalloc(sizeof(double) * N * RW); owned.push_back(Tw);
+  tvw = (double*)dmalloc(sizeof(double) * (size_t)tvs * RW); owned.push_back(tvw);
+  build_program(prog_wide, -1, false, Fw, Gw, Uw, Tw);
 }
 
 // The substitution as a list of batched steps over the plane slots of
 // instance `inst` (-1: all instances).
 template <typename T>
-void Engine<T>::build_program(Program& pg, int inst, bool count_bytes) {
+void Engine<T>::build_program(Program& pg, int inst, bool count_bytes, double* Fv, double* Gv,
+                              double* Uv, double* Tv) {
   auto vec = [&](double* base, int slot) -> double* { return base + (int64_t)slot * n2; };
   auto sel = [&](const std::vector<int>& slots) {
     std::vector<int> o;
@@ -1343,11 +1364,30 @@ void Engine<T>::build_program(Program& pg, int inst, bool count_bytes) {
 }
 
 template <typename T>
-void Engine<T>::run_steps(const std::vector<ApplyStep>& steps, int nr, cudaStream_t st) {
+void Engine<T>::run_steps(const std::vector<ApplyStep>& steps, int nr, cudaStream_t st,
+                          double* tvscr) {
   for (const ApplyStep& s : steps) {
     const int P = s.P;
     if (P <= 0) continue;
     void** t = s.tabs;
+    if constexpr (!std::is_same<T, double>::value) {
+      if (s.kind == 0 && nr == RW) {
+        // 32 right-hand sides: the H-matrix x matrix product on the tensor cores
+        if (bf16) {
+          using B = __nv_bfloat16;
+          launch_hmatvec_tc<B>(mvd, (B* const*)t, (B* const*)(t + P), (B* const*)(t + 2 * P),
+                               (const int* const*)(t + 3 * P), (const double* const*)(t + 4 * P),
+                               (double* const*)(t + 5 * P), s.alpha, s.beta, s.trans, tvscr, P,
+                               vs, d_err, st);
+        } else {
+          launch_hmatvec_tc<T>(mvd, (T* const*)t, (T* const*)(t + P), (T* const*)(t + 2 * P),
+                               (const int* const*)(t + 3 * P), (const double* const*)(t + 4 * P),
+                               (double* const*)(t + 5 * P), s.alpha, s.beta, s.trans, tvscr, P,
+                               vs, d_err, st);
+        }
+        continue;
+      }
+    }
     if (s.kind == 0 && bf16) {
       using B = __nv_bfloat16;
       launch_hmatvec<B>(mvd, (B* const*)t, (B* const*)(t + P), (B* const*)(t + 2 * P),
@@ -1370,9 +1410,9 @@ void Engine<T>::run_steps(const std::vector<ApplyStep>& steps, int nr, cudaStrea
 }
 
 template <typename T>
-void Engine<T>::run_program(const Program& pg, bool trans, int nr, cudaStream_t st) {
-  run_steps(trans ? pg.fwdT : pg.fwd, nr, st);
-  run_steps(trans ? pg.bwdT : pg.bwd, nr, st);
+void Engine<T>::run_program(const Program& pg, bool trans, int nr, cudaStream_t st, double* tv) {
+  run_steps(trans ? pg.fwdT : pg.fwd, nr, st, tv);
+  run_steps(trans ? pg.bwdT : pg.bwd, nr, st, tv);
 }
 
 template <typename T>
@@ -1381,16 +1421,26 @@ void Engine<T>::apply(const double* r, double* z, bool trans, cudaStream_t st, i
     // a batch: one right-hand side per instance, instances back to back
     if (nrhs != 1) throw AcrError{S_INVALID, "a batch applies one right-hand side per instance"};
     launch_permute(r, Fv, sd.perm, n2, n * count, true, st);
-    run_program(prog_all, trans, 1, st);
+    run_program(prog_all, trans, 1, st, tvscr);
     launch_permute(Uv, z, sd.perm, n2, n * count, false, st);
     return;
   }
-  // groups of 8, 4, 2, 1 right-hand sides; each group streams the factors once
+  // groups of 32 right-hand sides on the tensor cores (float and bfloat16
+  // factors, 64-point leaves), then groups of 8, 4, 2, 1 on the CUDA cores;
+  // each group streams the factors once
   for (int k = 0; k < nrhs;) {
+    if (nrhs - k >= RW && wide_ok()) {
+      ensure_wide();
+      launch_permute(r + (int64_t)k * N, Fw, sd.perm, n2, n * RW, true, st);
+      run_program(prog_wide, trans, RW, st, tvw);
+      launch_permute(Uw, z + (int64_t)k * N, sd.perm, n2, n * RW, false, st);
+      k += RW;
+      continue;
+    }
     int R = RB;
     while (R > nrhs - k) R >>= 1;
     launch_permute(r + (int64_t)k * N, Fv, sd.perm, n2, n * R, true, st);
-    run_program(prog_all, trans, R, st);
+    run_program(prog_all, trans, R, st, tvscr);
     launch_permute(Uv, z + (int64_t)k * N, sd.perm, n2, n * R, false, st);
     k += R;
   }
@@ -1400,7 +1450,7 @@ template <typename T>
 void Engine<T>::apply_gather(const double* const* r, double* const* z, cudaStream_t st) {
   for (int i = 0; i < count; ++i)
     launch_permute(r[i], Fv + (int64_t)i * N, sd.perm, n2, n, true, st);
-  run_program(prog_all, false, 1, st);
+  run_program(prog_all, false, 1, st, tvscr);
   for (int i = 0; i < count; ++i)
     launch_permute(Uv + (int64_t)i * N, z[i], sd.perm, n2, n, false, st);
 }
@@ -1413,7 +1463,7 @@ void Engine<T>::apply_instance(int i, const double* r, double* z, bool trans, cu
     return;
   }
   launch_permute(r, Fv + (int64_t)i * N, sd.perm, n2, n, true, st);
-  run_program(prog_inst[i], trans, 1, st);
+  run_program(prog_inst[i], trans, 1, st, tvscr);
   launch_permute(Uv + (int64_t)i * N, z, sd.perm, n2, n, false, st);
 }
 

@@ -120,6 +120,23 @@ void launch_hmatvec(const MatvecDev& mv, T* const* dense, T* const* U, T* const*
                     double alpha, double beta, bool trans, double* tv, int P, int nr,
                     int64_t vs, cudaStream_t st);
 
+// low-rank projections of the apply for a group of nr = 32 right-hand sides
+// (tv layout as launch_hmatvec's)
+template <typename T>
+void launch_lr_proj(const MatvecDev& mv, T* const* U, T* const* V, const int* const* rank,
+                    const double* const* x, double* tv, bool trans, int P, int nr, int64_t vs,
+                    cudaStream_t st);
+
+// The batched H-matrix-vector product for exactly 32 right-hand sides on the
+// tcgen05 tensor cores (float or bfloat16 factors, 64-point leaves): the
+// projections, then the row chunks as H-matrix x matrix products.  A bounded
+// wait that runs out sets ERR_TIMEOUT in d_err.
+template <typename T>
+void launch_hmatvec_tc(const MatvecDev& mv, T* const* dense, T* const* U, T* const* V,
+                       const int* const* rank, const double* const* x, double* const* y,
+                       double alpha, double beta, bool trans, double* tv, int P, int64_t vs,
+                       int* d_err, cudaStream_t st);
+
 // out[e] = bfloat16(in[e]) (round to nearest even), e < count; out is __nv_bfloat16*
 void launch_to_bf16(const float* in, void* out, int64_t count, cudaStream_t st);
 void launch_permute(const double* in, double* out, const int* perm, int n2, int nplanes,

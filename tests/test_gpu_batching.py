@@ -8,6 +8,8 @@
   confirms each residual) and agree with one-at-a-time solves to within
   10 cond(A) rtol.
 """
+import functools
+
 import numpy as np
 import pytest
 import scipy.sparse.linalg as sla
@@ -141,3 +143,56 @@ def test_autotune_leaf_picks_the_fastest_candidate(acr):
     ok = [t for t in times[:3] if t > 0]
     assert len(ok) == 3 and times[(16, 32, 64).index(best)] == min(ok)
     assert times[3] == -1.0          # leaves above 64 points are not supported
+
+
+@functools.lru_cache(maxsize=None)
+def _codi32_oracle():
+    """The oracle's factors of the n = 32 convection-diffusion recipe at leaf 64
+    (eps 1e-2, eta 2), and those of its float32 arithmetic model."""
+    n = 32
+    st = stencil_codi(codi_beta(n), n)
+    D, Ld, Ud = plane_blocks(st, n)
+    S = Structure(n, 2.0, 64)
+    return cr_setup(D, Ld, Ud, S, 1e-2), cr_setup(D, Ld, Ud, S, 1e-2, arith=np.float32)
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+@pytest.mark.parametrize("trans", [False, True])
+def test_32_rhs_tensor_core_apply(acr, parity_log, prec, trans):
+    """33 right-hand sides at n = 32, leaf 64 (dense and low-rank leaves): the
+    first 32 go through the tcgen05 H-matrix x matrix kernel in one pass, the
+    last through the CUDA-core kernel (bitwise equal to its single apply).
+    The tensor-core vectors are the same products of the same float (or
+    bfloat16) factors, from TF32 hi/lo pieces (representation error ~2^-21)
+    accumulated over at most 64 products before a compensated float sum:
+    they agree with the single-right-hand-side applies to the FP32 parity
+    bound (1e-5), and the first one (plain apply, FP32 factors) with the
+    oracle to max(1e-5, 5x the oracle's float32-model error)."""
+    n, nr = 32, 33
+    st, coef = _codi(acr, n)
+    N = n ** 3
+    R = np.stack([uniform_rhs(n, 80 + k) for k in range(nr)])
+    h = acr.Handle(n, coef, 1e-2, 2.0, 64, prec, 24)
+    Zm = torch.empty(nr * N, dtype=torch.float64, device="cuda:0")
+    (h.apply_transpose if trans else h.apply)(T(R.ravel()), Zm, nrhs=nr)
+    Zs = torch.empty(N, dtype=torch.float64, device="cuda:0")
+    zm = Zm.cpu().numpy().reshape(nr, N)
+    worst = 0.0
+    for k in range(nr):
+        (h.apply_transpose if trans else h.apply)(T(R[k]), Zs)
+        torch.cuda.synchronize()
+        e = rel(zm[k], Zs.cpu().numpy())
+        worst = max(worst, e)
+        if k == nr - 1:
+            assert np.array_equal(zm[k], Zs.cpu().numpy())   # the CUDA-core remainder
+    h.close()
+    rec = dict(test="apply_32rhs_tc", n=n, prec=prec, trans=trans, err_vs_single=worst)
+    if prec == 1 and not trans:
+        F, F32 = _codi32_oracle()
+        zo = cr_apply(F, R[0])
+        e_or = rel(zm[0], zo)
+        tol = max(1e-5, 5 * rel(cr_apply(F32, R[0]), zo))
+        rec.update(err_vs_oracle=e_or, tol_oracle=tol)
+        assert e_or <= tol, (e_or, tol)
+    parity_log(**rec)
+    assert worst <= 1e-5, worst
