@@ -240,9 +240,9 @@ def profile_setup(args):
     p = acr.acr_get_profile(h)
     inf = acr.acr_get_setup_info(h)
     acr.acr_destroy(h)
-    print("n=%d %s setup %.1f ms, levels %d, max rank %d, factors %.3f GB"
-          % (n, "FP64" if args.fp64 else "FP32", inf.setup_ms, inf.levels, inf.max_rank,
-             inf.factor_bytes / 1e9))
+    print("n=%d %s setup %.1f ms (host issue %.1f ms), levels %d, max rank %d, factors %.3f GB"
+          % (n, "FP64" if args.fp64 else "FP32", inf.setup_ms, inf.host_issue_ms, inf.levels,
+             inf.max_rank, inf.factor_bytes / 1e9))
     for k in ("gemm", "orth", "eig", "leaf_inv", "other"):
         st = getattr(p, k)
         print("  %-9s launches %7d  %9.1f ms  %8.3f TFLOP/s"
@@ -256,6 +256,42 @@ def profile_setup(args):
     return 0
 
 
+def profile_apply(args):
+    """One setup of the benchmark recipe at --n (FP32 factors) and three
+    applies of --nrhs right-hand sides at once (32: the tensor-core path;
+    1: the single-vector path); prints the CUDA-event time per apply.  Used
+    for the ncu captures of the apply kernels."""
+    import torch
+    import paper_1712_08872_gb300 as acr
+    from inputs import workload
+    dev = torch.device("cuda", 0)
+    acr.load_library()
+    n = args.n
+    spec, beta, f = workload("codi_n128", n=n)
+    coef = torch.empty(7 * n ** 3, dtype=torch.float64, device=dev)
+    acr.acr_stencil_codi(n, torch.tensor(beta.ravel(), dtype=torch.float64, device=dev), coef)
+    stream = torch.cuda.current_stream()
+    h = acr.acr_setup(n, coef, spec["eps"], 2.0, spec["leaf"], acr.ACR_FP32, args.rank_cap, stream)
+    nr = args.nrhs
+    R = torch.tensor(f, dtype=torch.float64, device=dev).repeat(nr)
+    Z = torch.empty_like(R)
+    acr.acr_apply(h, R, Z, nr, stream)
+    torch.cuda.synchronize()
+    ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ea.record(stream)
+    for _ in range(3):
+        acr.acr_apply(h, R, Z, nr, stream)
+    eb.record(stream)
+    torch.cuda.synchronize()
+    info = acr.acr_get_setup_info(h)
+    acr.acr_destroy(h)
+    ms = ea.elapsed_time(eb) / 3
+    print("n=%d %d-vector apply %.3f ms (%.4f ms per vector), factor bytes per pass %.3f GB, "
+          "%.0f GB/s" % (n, nr, ms, ms / nr, info.apply_bytes / 1e9,
+                         info.apply_bytes / (ms / 1000.0) / 1e9))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -266,6 +302,8 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--bf16-steps", type=int, default=3)
+    ap.add_argument("--no-gemm-autotune", action="store_true",
+                    help="default GEMM kernel shapes instead of the autotuned table")
     ap.add_argument("--no-config1", action="store_true",
                     help="skip the n=64 high-contrast boxes comparison of the three forms")
     ap.add_argument("--no-mixed-batch", action="store_true",
@@ -274,6 +312,11 @@ def main():
                     help="skip the multi-right-hand-side measurements")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--rank-cap", type=int, default=24)
+    ap.add_argument("--profile-apply", "--profile-apply32", dest="profile_apply",
+                    action="store_true",
+                    help="one setup at --n and three applies of --nrhs vectors, timed")
+    ap.add_argument("--nrhs", type=int, default=32,
+                    help="with --profile-apply: right-hand sides per apply (1, 8 or 32)")
     ap.add_argument("--profile-setup", action="store_true",
                     help="run one profiled setup (ACR_FLAG_PROFILE) at --n and print its "
                          "per-class, per-stage and per-level times; no benchmark line")
@@ -283,6 +326,8 @@ def main():
         return run_reference(args)
     if args.profile_setup:
         return profile_setup(args)
+    if args.profile_apply:
+        return profile_apply(args)
 
     import numpy as np
     import torch
@@ -313,8 +358,20 @@ def main():
     u = torch.zeros(N, dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream()
 
+    # GEMM kernel shapes per setup stage, tuned once on this operator (outside
+    # the timed region) for the float forms
+    tune = None
+    table = None
+    if not args.no_gemm_autotune:
+        table, ms0, ms1, ms2 = acr.acr_autotune_gemm(n, coef, eps, eta, leaf, acr.ACR_FP32,
+                                                     args.rank_cap, stream)
+        tune = {"table": table[:13], "stage_ms_shape0": [round(v, 1) for v in ms0[:13]],
+                "stage_ms_shape1": [round(v, 1) for v in ms1[:13]],
+                "stage_ms_shape2": [round(v, 1) for v in ms2[:13]]}
+
     def step(prec, flags=0):
-        h = acr.acr_setup(n, coef, eps, eta, leaf, prec, args.rank_cap, stream, flags)
+        var = table if prec != acr.ACR_FP64 else None
+        h = acr.acr_setup(n, coef, eps, eta, leaf, prec, args.rank_cap, stream, flags, var)
         u.zero_()
         info, st = acr.acr_krylov_solve(h, coef, acr.ACR_GMRES, restart, rtol, 1000, f_d, u,
                                         stream, check=False)
@@ -387,7 +444,8 @@ def main():
             fd = f_h.to(dev, non_blocking=True)
             cf = torch.empty(7 * N, dtype=torch.float64, device=dev)
             acr.acr_stencil_codi(n, bd, cf)
-            h = acr.acr_setup(n, cf, eps, eta, leaf, acr.ACR_FP32, args.rank_cap, stream)
+            h = acr.acr_setup(n, cf, eps, eta, leaf, acr.ACR_FP32, args.rank_cap, stream, 0,
+                              table)
             uu = torch.zeros(N, dtype=torch.float64, device=dev)
             acr.acr_krylov_solve(h, cf, acr.ACR_GMRES, restart, rtol, 1000, fd, uu, stream)
             acr.acr_destroy(h)
@@ -628,13 +686,16 @@ def main():
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": "inputs larger than L2 (factors tens of GB)"},
             "iterations": solve_info.iterations, "rel_residual": solve_info.rel_residual,
-            "setup_s": setup_info.setup_ms / 1000.0, "solve_s": solve_info.solve_ms / 1000.0,
+            "setup_s": setup_info.setup_ms / 1000.0,
+            "setup_host_issue_s": setup_info.host_issue_ms / 1000.0,
+            "solve_s": solve_info.solve_ms / 1000.0,
             "max_rank": setup_info.max_rank, "factor_gb": setup_info.factor_bytes / 1e9,
             "fp64_plain": fp64, "bf16_factors": bf16,
             "speedup_vs_fp64": (fp64["s"] / (ms / 1000.0)) if fp64 else None,
             "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks,
             "roofline": roof, "apply_roofline": apply_roof, "batching": batch,
-            "config1_boxes_n64": config1, "mixed_batch": mixed, "cpu_baseline": cpu}
+            "config1_boxes_n64": config1, "mixed_batch": mixed, "gemm_autotune": tune,
+            "cpu_baseline": cpu}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:

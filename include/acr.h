@@ -80,6 +80,9 @@ typedef struct {
   int32_t precision;     /* acr_precision */
   int32_t rank_cap;      /* 1..48; 0 selects the default (32) */
   int32_t flags;         /* ACR_FLAG_* bits */
+  int32_t gemm_variant[16]; /* kernel shape per setup GEMM stage (index = the stage numbering of
+                               acr_profile.stage_ms), 0, 1 or 2 (acr_autotune_gemm); all 0 is
+                               the default shape set; other values read as 0 */
 } acr_options;
 
 /* acr_options.flags: record per-kernel-class device time (CUDA events
@@ -106,6 +109,9 @@ typedef struct {
                                 terms summed into the block) exceeded the sketch width
                                 min(rank_cap + 8, 64): their range finder was a randomized
                                 approximation instead of exact */
+  double host_issue_ms;      /* host time the setup's device phase took to issue its work
+                                (launches, copies) up to its closing event; near setup_ms when
+                                the issue rate, not the device, bounds the setup */
 } acr_setup_info;
 
 /* Per-kernel-class setup statistics (ACR_FLAG_PROFILE).  flops counts the
@@ -196,6 +202,19 @@ acr_status acr_autotune_leaf(const acr_grid* grid, const double* coef, const acr
                              int32_t method, int32_t restart, double rtol, const int32_t* cand,
                              int32_t n_cand, int32_t* best_leaf, double* times_ms,
                              cudaStream_t stream);
+
+/* Autotuner of the setup's grouped-GEMM kernel shapes (the paper has no
+ * counterpart): one profiled setup of coef with opt per shape (every stage in
+ * shape 0, then every stage in shape 1, then in shape 2), then per stage the
+ * fastest.  Shape 0: one CTA per group, 4 CTAs per SM; shape 1: for float
+ * factors 3 CTAs per SM with more registers (double: half the K-chunk), and
+ * the warp- and CTA-per-group inner-product kernels swapped; shape 2 (float
+ * factors, non-inner-product stages): one warp per group.  variant_out
+ * (host, 16 int32) receives the table to put in acr_options.gemm_variant;
+ * stage_ms_out (host, 48 doubles, may be NULL) the measured stage times,
+ * shape 0, 1, then 2.  Errors: as acr_setup. */
+acr_status acr_autotune_gemm(const acr_grid* grid, const double* coef, const acr_options* opt,
+                             int32_t* variant_out, double* stage_ms_out, cudaStream_t stream);
 
 /* a9-a10, Sec. 4.1 substitution: z = M^{-1} r, M the ACR factorisation;
  * forward then backward sweep of batched H-matrix-vector products.  r, z:

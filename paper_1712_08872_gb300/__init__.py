@@ -12,7 +12,7 @@ from .acr import (  # noqa: F401
     acr_get_setup_info, acr_get_profile, acr_structure_query, ACR_FLAG_PROFILE,
     KernelStat, Profile, acr_destroy, acr_status_string, Handle, acr_launch_count, acr_alloc_count,
     acr_krylov_solve_plain_noalloc, acr_noalloc_max_unknowns, acr_krylov_solve_transpose,
-    acr_spmv_transpose, acr_kappa_gradient, acr_stencil_helmholtz, acr_autotune_leaf,
+    acr_spmv_transpose, acr_kappa_gradient, acr_stencil_helmholtz, acr_autotune_leaf, acr_autotune_gemm,
     acr_batch_create, acr_batch_refactor, acr_batch_status, acr_batch_apply, acr_batch_capture,
     acr_batch_replay, acr_batch_krylov_solve, acr_batch_get_info, acr_batch_destroy,
 )

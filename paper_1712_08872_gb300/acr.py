@@ -33,7 +33,15 @@ class Grid(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [("eps", ctypes.c_double), ("eta", ctypes.c_double), ("leaf", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("rank_cap", ctypes.c_int32),
-                ("flags", ctypes.c_int32)]
+                ("flags", ctypes.c_int32), ("gemm_variant", ctypes.c_int32 * 16)]
+
+
+def _options(eps, eta, leaf, precision, rank_cap, flags, gemm_variant=None):
+    o = Options(eps, eta, leaf, precision, rank_cap, flags)
+    if gemm_variant is not None:
+        for t, v in enumerate(gemm_variant[:16]):
+            o.gemm_variant[t] = int(v)
+    return o
 
 
 ACR_FLAG_PROFILE = 1
@@ -46,7 +54,8 @@ class SetupInfo(ctypes.Structure):
                 ("n_lowrank_leaves", ctypes.c_int32), ("setup_ms", ctypes.c_double),
                 ("structure_ms", ctypes.c_double), ("apply_bytes", ctypes.c_int64),
                 ("apply_flops", ctypes.c_int64), ("lr_truncations", ctypes.c_int64),
-                ("sketch_overflows", ctypes.c_int64)]
+                ("sketch_overflows", ctypes.c_int64),
+                ("host_issue_ms", ctypes.c_double)]
 
 
 class KernelStat(ctypes.Structure):
@@ -132,6 +141,8 @@ def load_library(path=LIB_PATH):
     lib.acr_batch_get_info.restype = ctypes.c_int
     lib.acr_batch_destroy.argtypes = [_P]
     lib.acr_batch_destroy.restype = None
+    lib.acr_autotune_gemm.argtypes = [_P, _P, ctypes.POINTER(Options), _P, _P, _P]
+    lib.acr_autotune_gemm.restype = ctypes.c_int
     lib.acr_launch_count.argtypes = []
     lib.acr_launch_count.restype = ctypes.c_int64
     lib.acr_alloc_count.argtypes = []
@@ -210,7 +221,7 @@ def acr_autotune_leaf(n, coef, eps, eta, precision, rank_cap, method, restart, r
     """Fastest leaf size among ``candidates`` by timed setup + probe solve.
     Returns (best_leaf, [ms per candidate, -1 where it failed])."""
     N = n ** 3
-    opt = Options(eps, eta, 0, precision, rank_cap, 0)
+    opt = _options(eps, eta, 0, precision, rank_cap, 0)
     cand = (ctypes.c_int32 * len(candidates))(*candidates)
     times = (ctypes.c_double * len(candidates))()
     best = ctypes.c_int32(0)
@@ -229,10 +240,25 @@ def acr_kappa_gradient(n, kappa, lam, u, grad, stream=None):
            "acr_kappa_gradient")
 
 
-def acr_setup(n, coef, eps, eta, leaf, precision=ACR_FP64, rank_cap=0, stream=None, flags=0):
+def acr_autotune_gemm(n, coef, eps, eta, leaf, precision, rank_cap, stream=None):
+    """Per-stage kernel shapes of the setup GEMMs by three profiled setups.
+    Returns (table of 16 ints for gemm_variant, stage ms shape 0, shape 1,
+    shape 2)."""
+    N = n ** 3
+    opt = _options(eps, eta, leaf, precision, rank_cap, 0)
+    var = (ctypes.c_int32 * 16)()
+    ms = (ctypes.c_double * 48)()
+    _check(load_library().acr_autotune_gemm(ctypes.byref(_grid(n)), _dev(coef, 7 * N, "coef"),
+                                             ctypes.byref(opt), var, ms, _stream(stream)),
+           "acr_autotune_gemm")
+    return list(var), list(ms[:16]), list(ms[16:32]), list(ms[32:])
+
+
+def acr_setup(n, coef, eps, eta, leaf, precision=ACR_FP64, rank_cap=0, stream=None, flags=0,
+              gemm_variant=None):
     """Returns an opaque handle (int); release it with acr_destroy."""
     N = n ** 3
-    opt = Options(eps, eta, leaf, precision, rank_cap, flags)
+    opt = _options(eps, eta, leaf, precision, rank_cap, flags, gemm_variant)
     h = _P()
     _check(load_library().acr_setup(ctypes.byref(_grid(n)), _dev(coef, 7 * N, "coef"),
                                      ctypes.byref(opt), _stream(stream), ctypes.byref(h)),
@@ -385,7 +411,7 @@ def acr_batch_create(ns, coefs, eps, eta, leaf, precision=ACR_FP32, rank_cap=0, 
     cnt = len(ns)
     nn = (ctypes.c_int32 * cnt)(*ns)
     ptrs = (_P * cnt)(*[_dev(c, 7 * n ** 3, "coef") for c, n in zip(coefs, ns)])
-    opt = Options(eps, eta, leaf, precision, rank_cap, 0)
+    opt = _options(eps, eta, leaf, precision, rank_cap, 0)
     b = _P()
     _check(load_library().acr_batch_create(cnt, nn, ptrs, ctypes.byref(opt), _stream(stream),
                                             ctypes.byref(b)), "acr_batch_create")

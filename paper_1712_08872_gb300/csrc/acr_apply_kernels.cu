@@ -300,6 +300,174 @@ __global__ void __launch_bounds__(256) k_hmv_rows(MatvecDev mv, T* const* __rest
   }
 }
 
+// 4 consecutive factor entries as floats (16-byte float or 8-byte bfloat16
+// loads; the caller guarantees the alignment)
+__device__ __forceinline__ void load4(const float* p, float (&v)[4]) {
+  const float4 q = *reinterpret_cast<const float4*>(p);
+  v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+}
+__device__ __forceinline__ void load4(const __nv_bfloat16* p, float (&v)[4]) {
+  const uint2 q = *reinterpret_cast<const uint2*>(p);
+  const __nv_bfloat162 a = *reinterpret_cast<const __nv_bfloat162*>(&q.x);
+  const __nv_bfloat162 b = *reinterpret_cast<const __nv_bfloat162*>(&q.y);
+  const float2 fa = __bfloat1622float2(a), fb = __bfloat1622float2(b);
+  v[0] = fa.x; v[1] = fa.y; v[2] = fb.x; v[3] = fb.y;
+}
+
+// The row kernel for one right-hand side, 64-point leaves, float or bfloat16
+// factors, with vector loads of 4 consecutive entries: lane group (16 lanes)
+// rl covers rows 4 rl .. 4 rl + 3 of a column, so a warp reads 2 columns of
+// a leaf per load (a low-rank leaf: one warp, all its columns at once); the
+// transposed dense product reads 4 consecutive entries of a stored column (a
+// row of D^T) per lane and reduces the 16 quads of a row with shuffles.
+// Partial sums (at most 4 dense products, or half a leaf's rank) enter
+// compensated float pairs; warps combine through shared memory in a fixed
+// order.
+template <typename T>
+__global__ void __launch_bounds__(256) k_hmv_rows_v1(MatvecDev mv, T* const* __restrict__ D,
+                                                     T* const* __restrict__ U,
+                                                     T* const* __restrict__ V,
+                                                     const int* const* __restrict__ rank,
+                                                     const double* const* __restrict__ x,
+                                                     double* const* __restrict__ y, double alpha,
+                                                     double beta, const double* __restrict__ tv,
+                                                     bool trans, int64_t vs) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float* xs = reinterpret_cast<float*>(smraw);
+  __shared__ double part[9][64];
+  const int c = blockIdx.x, p = blockIdx.y;
+  double* yp = y[p];
+  if (!yp) return;
+  const double* xp = x[p];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const bool have = D[p] != nullptr && xp != nullptr;
+  const int* dptr = trans ? mv.dt_ptr : mv.d_ptr;
+  const int* dleaf = trans ? mv.dt_leaf : mv.d_leaf;
+  const int* dcol = trans ? mv.dt_row : mv.d_col;
+  const int* lptr = trans ? mv.lt_ptr : mv.l_ptr;
+  const int* lleaf = trans ? mv.lt_leaf : mv.l_leaf;
+  const int d0 = dptr[c], nd = dptr[c + 1] - d0;
+  const int l0 = lptr[c], nlc = lptr[c + 1] - l0;
+  const int kc = mv.kc;
+  const int xstride = nd * 64;
+  float* ts = xs + xstride;
+  __shared__ int64_t s_off[MAXQ];
+  __shared__ int s_ld[MAXQ], s_k[MAXQ], s_leaf[MAXQ];
+  if (have) {
+    for (int q = tid; q < nd && q < MAXQ; q += 256) s_leaf[q] = dleaf[d0 + q];
+    for (int q = tid; q < nlc && q < MAXQ; q += 256) {
+      const int l = lleaf[l0 + q];
+      s_k[q] = rank[p][l];
+      s_ld[q] = trans ? mv.lr_n[l] : mv.lr_m[l];
+      s_off[q] = trans ? mv.lr_col0[l] * kc + mv.lt_coloff[l0 + q]
+                       : mv.lr_row0[l] * kc + mv.l_rowoff[l0 + q];
+    }
+    for (int e = tid; e < xstride; e += 256) {
+      const int q = e >> 6, j = e & 63;
+      xs[e] = (float)xp[dcol[d0 + q] + j];
+    }
+    const int* sptr = trans ? mv.segt_ptr : mv.seg_ptr;
+    const int nseg = trans ? mv.nsegt : mv.nseg;
+    for (int e = tid; e < nlc * kc; e += 256) {
+      const int q = e / kc, j = e - q * kc;
+      const int l = lleaf[l0 + q];
+      double v = 0.0;
+      if (j < rank[p][l])
+        for (int sg = sptr[l]; sg < sptr[l + 1]; ++sg) v += tv[((int64_t)p * nseg + sg) * kc + j];
+      ts[e] = (float)v;
+    }
+  }
+  __syncthreads();
+  RunSum<float> acc[4];          // rows 4 rl + v (low-rank; and dense when not transposed)
+  RunSum<float> acct[4];         // transposed dense: rows ig + 16 u
+  const int rl = tid & 15, cg = tid >> 4;
+  if (have) {
+    const T* Dp = D[p];
+    for (int q = 0; q < nd; ++q) {
+      const T* blk = Dp + (int64_t)(q < MAXQ ? s_leaf[q] : dleaf[d0 + q]) * 4096;
+      const float* xq = xs + q * 64;
+      if (!trans) {
+        float sp[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          const int j = cg + 16 * t;
+          float v4[4];
+          load4(blk + j * 64 + 4 * rl, v4);
+          const float xj = xq[j];
+#pragma unroll
+          for (int v = 0; v < 4; ++v) sp[v] += v4[v] * xj;
+        }
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[v].add(sp[v]);
+      } else {
+        const int jq = rl, ig = cg;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          float v4[4];
+          load4(blk + (ig + 16 * u) * 64 + 4 * jq, v4);
+          const float s4 = (v4[0] * xq[4 * jq] + v4[1] * xq[4 * jq + 1]) +
+                           (v4[2] * xq[4 * jq + 2] + v4[3] * xq[4 * jq + 3]);
+          acct[u].add(s4);
+        }
+      }
+    }
+    // low-rank leaves: warp w takes leaves w, w + 8, ...; its two half-warps
+    // the even and odd columns (all of a leaf's loads in flight at once)
+    const T* Fp = trans ? V[p] : U[p];
+    for (int q = warp; q < nlc; q += 8) {
+      int k, ldm;
+      int64_t off;
+      if (q < MAXQ) {
+        k = s_k[q]; ldm = s_ld[q]; off = s_off[q];
+      } else {
+        const int l = lleaf[l0 + q];
+        k = rank[p][l];
+        ldm = trans ? mv.lr_n[l] : mv.lr_m[l];
+        off = trans ? mv.lr_col0[l] * kc + mv.lt_coloff[l0 + q] : mv.lr_row0[l] * kc + mv.l_rowoff[l0 + q];
+      }
+      const T* fb = Fp + off + 4 * rl;
+      const float* tq = ts + q * kc;
+      float sp[4] = {0.f, 0.f, 0.f, 0.f};
+      for (int j = lane >> 4; j < k; j += 2) {
+        float v4[4];
+        load4(fb + (int64_t)j * ldm, v4);
+        const float t = tq[j];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) sp[v] += v4[v] * t;
+      }
+#pragma unroll
+      for (int v = 0; v < 4; ++v) acc[v].add(sp[v]);
+    }
+  }
+  // lanes l and l ^ 16 hold the same rows: combine, then one slot per warp
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    double d = acc[v].value();
+    d += __shfl_xor_sync(0xffffffffu, d, 16);
+    if (lane < 16) part[warp][4 * rl + v] = d;
+  }
+  if (trans) {
+    // transposed dense: the 16 quads of a row (16 consecutive lanes)
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      double d = acct[u].value();
+#pragma unroll
+      for (int o = 8; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+      if (rl == 0) part[8][cg + 16 * u] = d;
+    }
+  }
+  __syncthreads();
+  if (tid < 64) {
+    double sum = 0.0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) sum += part[w][tid];
+    if (trans) sum += part[8][tid];
+    double* yc = yp + (int64_t)c * 64;
+    const double old = (beta != 0.0) ? beta * yc[tid] : 0.0;
+    yc[tid] = old + (have ? alpha * sum : 0.0);
+  }
+}
+
 __global__ void k_permute(const double* __restrict__ in, double* __restrict__ out,
                           const int* __restrict__ perm, int n2, int64_t total, bool to_cluster) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
@@ -447,7 +615,23 @@ static void hmatvec_r(const MatvecDev& mv, T* const* dense, T* const* U, T* cons
     throw CudaError{cudaErrorInvalidConfiguration, "apply staging exceeds shared memory"};
   if (mv.nl > 0)
     k_lr_proj<T, R><<<dim3(mv.nchunks, P), 256, 0, st>>>(mv, U, V, rank, x, tv, trans, vs);
-  if (mv.lsz == 64)
+  bool done = false;
+  if constexpr (R == 1 && !std::is_same<T, double>::value) {
+    if (mv.lsz == 64 && mv.kc % 4 == 0) {
+      static bool attr_v1 = false;
+      if (!attr_v1) {
+        ACR_CUDA(cudaFuncSetAttribute(k_hmv_rows_v1<T>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, 180 * 1024));
+        attr_v1 = true;
+      }
+      const size_t sm1 = ((size_t)mv.max_d * 64 + (size_t)mv.max_l * mv.kc) * sizeof(float);
+      k_hmv_rows_v1<T><<<dim3(mv.nchunks, P), 256, sm1, st>>>(mv, dense, U, V, rank, x, y, alpha,
+                                                             beta, tv, trans, vs);
+      done = true;
+    }
+  }
+  if (done) {
+  } else if (mv.lsz == 64)
     k_hmv_rows<T, 64, R><<<dim3(mv.nchunks, P), 256, sm_rows, st>>>(
         mv, dense, U, V, rank, x, y, alpha, beta, tv, trans, vs);
   else

@@ -196,9 +196,11 @@ class Engine : public EngineBase {
   // count independent problems of the same size share every launch (their
   // planes are batched together; plane slot = instance * n + plane)
   Engine(int n_, double eps_, double eta_, int leaf_, int kc_, int flags_, bool bf16_ = false,
-         int count_ = 1)
+         int count_ = 1, const int32_t* variants = nullptr)
       : eps(eps_), eta(eta_), leaf(leaf_), kc(kc_), bf16(bf16_ && std::is_same<T, float>::value),
         count(count_) {
+    for (int t = 0; t < 16; ++t)
+      gemm_variant[t] = variants && variants[t] >= 0 && variants[t] <= 2 ? variants[t] : 0;
     profiling = (flags_ & ACR_FLAG_PROFILE) != 0;
     n = n_;
     n2 = n * n;
@@ -222,9 +224,12 @@ class Engine : public EngineBase {
   void execute(cudaStream_t st);
   // execute between the two events that time the setup
   void execute_timed(cudaStream_t st) {
+    const auto t0 = std::chrono::steady_clock::now();
     ACR_CUDA(cudaEventRecord(ev0, st));
     execute(st);
     ACR_CUDA(cudaEventRecord(ev1, st));
+    info.host_issue_ms =
+        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   }
   // synchronise, check the device error word, statistics, apply program
   void finish(cudaStream_t st, bool one_shot);
@@ -242,6 +247,7 @@ class Engine : public EngineBase {
   double eps, eta;
   int leaf, kc;
   bool bf16;                         // stored factors rounded to bfloat16 after the setup
+  int gemm_variant[16];              // kernel shape per GEMM stage tag
   int count = 1;
   int n2 = 0;
   int64_t vs = 0;                    // doubles between right-hand sides in the work vectors
@@ -623,7 +629,8 @@ class Engine : public EngineBase {
   void gemm_stage(const Plan& pl, const Stage& sg, T* const* d_tab, const int* const* d_rtab,
                   int pc, cudaStream_t st) {
     double* f = sg.tag >= 0 ? fl(5 + sg.tag) : fl(0);
-    launch_ggemm<T>(pl, sg.beg, sg.end, d_tab, d_rtab, pc, d_coefs, st, f, sg.tag);
+    launch_ggemm<T>(pl, sg.beg, sg.end, d_tab, d_rtab, pc, d_coefs, st, f, sg.tag,
+                    sg.tag >= 0 && sg.tag < 16 ? gemm_variant[sg.tag] : 0, d_err);
   }
 
   double tau_orth() const {
@@ -1073,6 +1080,8 @@ void Engine<T>::check_err(cudaStream_t st) {
                    "(numerically singular leaf)"};
   if (h & ERR_RANKCAP) throw AcrError{S_RANK_CAP, "truncated rank above the rank cap"};
   if (h & ERR_TIMEOUT) throw AcrError{S_TIMEOUT, "a bounded device wait ran out"};
+  if (h & ERR_SHAPE)
+    throw AcrError{S_UNSUPPORTED, "a warp-per-group GEMM stage met an output of more than 64 rows"};
 }
 
 template <typename T>
@@ -2018,10 +2027,11 @@ acr_status acr_setup(const acr_grid* grid, const double* coef, const acr_options
   h->precision = opt->precision;
   acr_status s = guarded([&] {
     if (opt->precision == ACR_FP64)
-      h->e = new acr::Engine<double>(grid->nx, opt->eps, opt->eta, opt->leaf, kc, opt->flags);
+      h->e = new acr::Engine<double>(grid->nx, opt->eps, opt->eta, opt->leaf, kc, opt->flags,
+                                     false, 1, opt->gemm_variant);
     else
       h->e = new acr::Engine<float>(grid->nx, opt->eps, opt->eta, opt->leaf, kc, opt->flags,
-                                    opt->precision == ACR_BF16);
+                                    opt->precision == ACR_BF16, 1, opt->gemm_variant);
     h->e->setup(coef, stream);
     return 0;
   });
@@ -2289,10 +2299,11 @@ acr_status acr_batch_create(int32_t count, const int32_t* n, const double* const
       ACR_CUDA(cudaEventCreateWithFlags(&g.done, cudaEventDisableTiming));
       const int cnt = (int)g.members.size();
       if (opt->precision == ACR_FP64)
-        g.e = new acr::Engine<double>(g.n, opt->eps, opt->eta, opt->leaf, kc, flags, false, cnt);
+        g.e = new acr::Engine<double>(g.n, opt->eps, opt->eta, opt->leaf, kc, flags, false, cnt,
+                                      opt->gemm_variant);
       else
         g.e = new acr::Engine<float>(g.n, opt->eps, opt->eta, opt->leaf, kc, flags,
-                                     opt->precision == ACR_BF16, cnt);
+                                     opt->precision == ACR_BF16, cnt, opt->gemm_variant);
       with_engine(b->precision, g.e, [&](auto* e) { e->prepare(g.coefs.data(), g.side, true); });
     }
     batch_refactor(b, stream);
@@ -2393,6 +2404,34 @@ void acr_destroy(acr_handle* h) {
   if (!h) return;
   delete h->e;
   delete h;
+}
+
+acr_status acr_autotune_gemm(const acr_grid* grid, const double* coef, const acr_options* opt,
+                             int32_t* variant_out, double* stage_ms_out, cudaStream_t stream) {
+  if (!grid_ok(grid) || !coef || !opt || !variant_out) return ACR_ERR_INVALID_ARG;
+  constexpr int NV = 3;
+  double ms[NV][16] = {};
+  for (int v = 0; v < NV; ++v) {
+    acr_options o = *opt;
+    o.flags |= ACR_FLAG_PROFILE;
+    for (int t = 0; t < 16; ++t) o.gemm_variant[t] = v;
+    acr_handle* h = nullptr;
+    const acr_status s = acr_setup(grid, coef, &o, stream, &h);
+    if (s != ACR_OK) return s;
+    acr_profile p{};
+    acr_get_profile(h, &p);
+    for (int t = 0; t < 16; ++t) ms[v][t] = p.stage_ms[t];
+    acr_destroy(h);
+  }
+  for (int t = 0; t < 16; ++t) {
+    int best = 0;
+    for (int v = 1; v < NV; ++v)
+      if (ms[v][t] < ms[best][t]) best = v;
+    variant_out[t] = best;
+    if (stage_ms_out)
+      for (int v = 0; v < NV; ++v) stage_ms_out[16 * v + t] = ms[v][t];
+  }
+  return ACR_OK;
 }
 
 acr_status acr_autotune_leaf(const acr_grid* grid, const double* coef, const acr_options* opt,

@@ -21,7 +21,7 @@ void count_launches(int64_t k);
 void count_allocs(int64_t k);
 
 // Device-side error word bits (written by kernels, read by the host).
-enum : int { ERR_PIVOT = 1, ERR_RANKCAP = 2, ERR_GROWTH = 4, ERR_TIMEOUT = 8 };
+enum : int { ERR_PIVOT = 1, ERR_RANKCAP = 2, ERR_GROWTH = 4, ERR_TIMEOUT = 8, ERR_SHAPE = 16 };
 
 struct CudaError {
   cudaError_t e;
@@ -42,11 +42,15 @@ struct CudaError {
   } while (0)
 
 // ------------------------------------------------------------ setup kernels
-// Grouped small GEMMs of a plan stage: one CTA per (group, plane).
+// Grouped small GEMMs of a plan stage: one CTA per (group, plane), or one
+// warp per group for inner-product stages.  variant (0 or 1, picked per
+// stage by the GEMM autotuner): 1 swaps the warp- and CTA-per-group
+// inner-product kernels and halves the staged kernel's K-chunk for more
+// CTAs per SM.
 template <typename T>
 void launch_ggemm(const Plan& pl, int gbeg, int gend, T* const* d_tab, const int* const* d_rtab,
                   int P, const double* d_coefs, cudaStream_t st, double* d_flops = nullptr,
-                  int tag = -1);
+                  int tag = -1, int variant = 0, int* d_err = nullptr);
 
 // Pivoted-Cholesky orthonormalisation cores (FP64) of plan targets.  The
 // truncating pass counts targets and stacked-rank overflows of the sketch

@@ -65,8 +65,10 @@ constexpr int STAGE_BYTES = 36864;   // shared staging of one K-chunk (A and B p
 // tiles (m, n > 32) use 4x4 register blocking over 64x64; smaller tiles
 // spread their outputs over the threads and split each chunk's K across the
 // spare threads, reducing the partial sums in shared memory at the end.
-template <typename T, typename Acc>
-__global__ void __launch_bounds__(NT, sizeof(Acc) == 4 ? 4 : 2) k_ggemm(const GGroup* __restrict__ groups,
+// SB: shared staging bytes of one K-chunk; MINB: CTAs per SM the register
+// budget is sized for (the autotuned shape: larger chunks vs more CTAs)
+template <typename T, typename Acc, int SB, int MINB>
+__global__ void __launch_bounds__(NT, MINB) k_ggemm(const GGroup* __restrict__ groups,
                                               const GItem* __restrict__ items,
                                               T* const* __restrict__ tab,
                                               const int* const* __restrict__ rtab, int P,
@@ -81,8 +83,8 @@ __global__ void __launch_bounds__(NT, sizeof(Acc) == 4 ? 4 : 2) k_ggemm(const GG
   const int n = dimv(G.n_st, G.n_rb, G.n_ri, rtab, P, p);
   if (m <= 0 || n <= 0) return;
   C += G.coff;
-  constexpr int SE = STAGE_BYTES / sizeof(Acc);
-  __shared__ __align__(16) unsigned char stage_raw[STAGE_BYTES];
+  constexpr int SE = SB / sizeof(Acc);
+  __shared__ __align__(16) unsigned char stage_raw[SB];
   __shared__ Acc red[NT];
   Acc* sm = reinterpret_cast<Acc*>(stage_raw);
   const Acc beta = G.beta >= 0 ? (Acc)coefs[G.beta] : Acc(0);
@@ -361,6 +363,160 @@ __global__ void __launch_bounds__(NT, sizeof(Acc) == 4 ? 4 : 2) k_ggemm(const GG
   if (flops && threadIdx.x == 0 && fl > 0) atomicAdd(flops, (double)fl);
 }
 
+// Warp-per-group form of k_ggemm for float operands and row panels
+// (m <= 64 output rows): one warp owns one group's m x n output, lane l
+// rows l and l + 32, NB = 8 columns at a time (more columns: further passes
+// over the items; 8 keeps the kernel at 80 registers, 3 CTAs per SM).  Per item, a K-chunk of B (times the item's coefficient) is
+// staged in the warp's own shared slice; A is read straight from global
+// memory, four K-steps of loads in flight, each lane its two rows.  No
+// block-wide barrier: a CTA's 8 warps run 8 independent groups, so the
+// many tiny groups of the factor, sketch and basis stages (64 x r outputs,
+// r of a few units, K of a few units to 64) cost a warp's worth of latency
+// each instead of a whole CTA's staging round trip.
+template <int NB>
+__device__ __forceinline__ void gwarp_panel(const GGroup& G, const GItem* __restrict__ items,
+                                            float* const* __restrict__ tab,
+                                            const int* const* __restrict__ rtab, int P, int p,
+                                            int m, int n, float* C,
+                                            const double* __restrict__ coefs, float* Bs,
+                                            long long& fl) {
+  constexpr int KCH = 32, LDB = NB + 4;
+  const int lane = threadIdx.x & 31;
+  const float beta = G.beta >= 0 ? (float)coefs[G.beta] : 0.f;
+  for (int j0 = 0; j0 < n; j0 += NB) {
+    const int nb = min(NB, n - j0);
+    float acc0[NB], acc1[NB];
+#pragma unroll
+    for (int j = 0; j < NB; ++j) { acc0[j] = 0.f; acc1[j] = 0.f; }
+    for (int it = G.ib; it < G.ie; ++it) {
+      const GItem I = items[it];
+      if (I.guard0 >= 0 && !tab[I.guard0 * P + p]) continue;
+      if (I.guard1 >= 0 && !tab[I.guard1 * P + p]) continue;
+      const float* A = nullptr;
+      const float* B = nullptr;
+      if (I.abuf >= 0) { A = tab[I.abuf * P + p]; if (!A) continue; A += I.aoff; }
+      if (I.bbuf >= 0) { B = tab[I.bbuf * P + p]; if (!B) continue; B += I.boff; }
+      const int k = dimv(I.k_st, I.k_rb, I.k_ri, rtab, P, p);
+      const int rows = dimv(I.r_st, I.r_rb, I.r_ri, rtab, P, p);
+      if (k <= 0 || rows <= 0) continue;
+      const float cf = (float)coefs[I.coef];
+      const int i0 = lane - I.row_off, i1 = lane + 32 - I.row_off;
+      const bool v0 = i0 >= 0 && i0 < rows, v1 = i1 >= 0 && i1 < rows;
+      if ((I.aflags & FL_IDENT) || (I.bflags & FL_IDENT)) {
+        // C(row_off + i, j) += cf * B(i, j)  or  cf * A(i, j)
+        fl += (long long)rows * nb;
+        const float* src = (I.aflags & FL_IDENT) ? B : A;
+        const int ld = (I.aflags & FL_IDENT) ? I.ldb : I.lda;
+#pragma unroll
+        for (int j = 0; j < NB; ++j) {
+          if (j < nb) {
+            if (v0) acc0[j] += cf * src[i0 + (int64_t)(j0 + j) * ld];
+            if (v1) acc1[j] += cf * src[i1 + (int64_t)(j0 + j) * ld];
+          }
+        }
+        continue;
+      }
+      fl += 2LL * rows * nb * k;
+      const bool at = I.aflags & FL_T, bt = I.bflags & FL_T, bo = I.bflags & FL_OMEGA;
+      // A(i, l): A[i + l lda] (plain) or A[l + i lda] (transposed)
+      const int astep = at ? 1 : I.lda;
+      const float* a0 = A + (v0 ? (at ? (int64_t)i0 * I.lda : i0) : 0);
+      const float* a1 = A + (v1 ? (at ? (int64_t)i1 * I.lda : i1) : 0);
+      for (int k0 = 0; k0 < k; k0 += KCH) {
+        const int kt = min(KCH, k - k0);
+        __syncwarp();
+        for (int e = lane; e < kt * NB; e += 32) {
+          const int kk = e / NB, j = e % NB;
+          float v = 0.f;
+          if (j < nb) {
+            const int l = k0 + kk, jj = j0 + j;
+            v = bo ? omega((uint32_t)I.seed, (uint32_t)(I.omega_row0 + l), (uint32_t)jj)
+                   : (bt ? B[jj + (int64_t)l * I.ldb] : B[l + (int64_t)jj * I.ldb]);
+          }
+          Bs[kk * LDB + j] = cf * v;
+        }
+        __syncwarp();
+        // A pointers at this chunk (offsets within a 64-row leaf panel
+        // stay far inside 32 bits: K-chunks of at most 32 columns)
+        const float* p0 = a0 + (int64_t)k0 * astep;
+        const float* p1 = a1 + (int64_t)k0 * astep;
+        int kk = 0;
+        for (; kk + 4 <= kt; kk += 4) {
+          float x0[4], x1[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            x0[u] = v0 ? p0[(kk + u) * astep] : 0.f;
+            x1[u] = v1 ? p1[(kk + u) * astep] : 0.f;
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+#pragma unroll
+            for (int q = 0; q < NB / 4; ++q) {
+              const float4 b = *reinterpret_cast<const float4*>(Bs + (kk + u) * LDB + 4 * q);
+              acc0[4 * q] += x0[u] * b.x; acc0[4 * q + 1] += x0[u] * b.y;
+              acc0[4 * q + 2] += x0[u] * b.z; acc0[4 * q + 3] += x0[u] * b.w;
+              acc1[4 * q] += x1[u] * b.x; acc1[4 * q + 1] += x1[u] * b.y;
+              acc1[4 * q + 2] += x1[u] * b.z; acc1[4 * q + 3] += x1[u] * b.w;
+            }
+          }
+        }
+        for (; kk < kt; ++kk) {
+          const float y0 = v0 ? p0[kk * astep] : 0.f;
+          const float y1 = v1 ? p1[kk * astep] : 0.f;
+#pragma unroll
+          for (int q = 0; q < NB / 4; ++q) {
+            const float4 b = *reinterpret_cast<const float4*>(Bs + kk * LDB + 4 * q);
+            acc0[4 * q] += y0 * b.x; acc0[4 * q + 1] += y0 * b.y;
+            acc0[4 * q + 2] += y0 * b.z; acc0[4 * q + 3] += y0 * b.w;
+            acc1[4 * q] += y1 * b.x; acc1[4 * q + 1] += y1 * b.y;
+            acc1[4 * q + 2] += y1 * b.z; acc1[4 * q + 3] += y1 * b.w;
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+      if (j >= nb) continue;
+      if (lane < m) {
+        float* c = C + lane + (int64_t)(j0 + j) * G.ldc;
+        *c = acc0[j] + (G.beta >= 0 ? beta * *c : 0.f);
+      }
+      if (lane + 32 < m) {
+        float* c = C + lane + 32 + (int64_t)(j0 + j) * G.ldc;
+        *c = acc1[j] + (G.beta >= 0 ? beta * *c : 0.f);
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(NT, 3) k_gwarp(const GGroup* __restrict__ groups,
+                                                 const GItem* __restrict__ items,
+                                                 float* const* __restrict__ tab,
+                                                 const int* const* __restrict__ rtab, int P,
+                                                 int gbeg, int gend,
+                                                 const double* __restrict__ coefs,
+                                                 double* __restrict__ flops, int* err) {
+  __shared__ __align__(16) float bsm[NT / 32][32 * 12];   // KCH x (NB + 4), NB = 8
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = gbeg + blockIdx.x * (NT / 32) + warp;
+  const int p = blockIdx.y;
+  if (g >= gend) return;
+  const GGroup G = groups[g];
+  float* C = tab[G.cbuf * P + p];
+  if (!C) return;
+  const int m = dimv(G.m_st, G.m_rb, G.m_ri, rtab, P, p);
+  const int n = dimv(G.n_st, G.n_rb, G.n_ri, rtab, P, p);
+  if (m <= 0 || n <= 0) return;
+  if (m > 64) {   // row panels only (the host launches this form for leaf-row stages)
+    if (lane == 0) atomicOr(err, ERR_SHAPE);
+    return;
+  }
+  C += G.coff;
+  long long fl = 0;
+  gwarp_panel<8>(G, items, tab, rtab, P, p, m, n, C, coefs, bsm[warp], fl);
+  if (flops && lane == 0 && fl > 0) atomicAdd(flops, (double)fl);
+}
+
 // Stages whose items read A transposed and B untransposed (or the sketch
 // hash), so both operands are contiguous along the contraction: U^T V,
 // Z^T Omega, X^T Q and the Grams.  Each warp owns a 4x4 output sub-tile and
@@ -596,8 +752,8 @@ __global__ void __launch_bounds__(NT, sizeof(Acc) == 4 ? 4 : 1) k_gdot_warp(cons
 // times the largest one, so a float-accumulated Gram (error ~1e-7) stops at
 // ~3e-4; here every product is exact (a*b split into its rounded value and
 // FMA remainder) and the sums are compensated (TwoSum per lane, float-float
-// state), then the lanes' results are combined in double: the relative
-// error is ~1e-14 of sum |y_i||y_j|, so the Grams resolve singular values
+// state, the lanes' results summed the same way, then rounded to double):
+// the relative error is ~1e-13 of sum |y_i||y_j|, so the Grams resolve singular values
 // down to the float data's own noise (~1e-7).  Upper-triangle 4 x 4 tiles
 // per warp (the result is mirrored), lanes striding the contraction.
 __device__ __forceinline__ void ff_fma(float& s, float& c, float a, float b) {
@@ -611,8 +767,8 @@ __device__ __forceinline__ void ff_fma(float& s, float& c, float a, float b) {
 
 // One CTA per Gram: the columns of Y pass through shared memory in chunks of
 // 64 rows; thread (tile, slice) owns a 4 x 4 tile of the upper triangle and
-// the rows slice, slice + S, ... of every chunk; the float-float partials
-// are combined in double, slices summed in a fixed order.
+// the rows slice, slice + S, ... of every chunk; the slices' float-float
+// partials are summed in float-float in a fixed order, then rounded to double.
 constexpr int GRAM_KCH = 64;
 
 __global__ void __launch_bounds__(NT) k_gram_ff(const GGroup* __restrict__ groups,
@@ -634,9 +790,8 @@ __global__ void __launch_bounds__(NT) k_gram_ff(const GGroup* __restrict__ group
   const int k = dimv(I.k_st, I.k_rb, I.k_ri, rtab, P, p);
   const int ld = I.lda;
   // ys[column][row of the chunk] during the sweep; then the per-thread tile
-  // results red[thread][16] in the same storage
+  // results (float-float pairs) in the same storage
   __shared__ __align__(16) double raw[NT * 16];
-  double (*red)[16] = reinterpret_cast<double (*)[16]>(raw);
   const int TM = (m + 3) >> 2, ntile = TM * (TM + 1) / 2;
   // rows per chunk: the staged columns (4 TM of them) fill the buffer
   const int kch = TM <= 4 ? 4 * GRAM_KCH : (TM <= 8 ? 2 * GRAM_KCH : GRAM_KCH);
@@ -683,14 +838,27 @@ __global__ void __launch_bounds__(NT) k_gram_ff(const GGroup* __restrict__ group
       }
   }
   __syncthreads();   // every thread is done with ys
+  // the slices' float-float partials, summed in float-float (TwoSum) in a
+  // fixed order; one conversion to double per output (the FP64 pipe is a
+  // small fraction of the FP32 one)
+  float (*red_s)[16] = reinterpret_cast<float (*)[16]>(raw);
+  float (*red_c)[16] = reinterpret_cast<float (*)[16]>(reinterpret_cast<float*>(raw) + NT * 16);
 #pragma unroll
-  for (int e = 0; e < 16; ++e)
-    red[tid][e] = active ? (double)s[e & 3][e >> 2] + (double)c[e & 3][e >> 2] : 0.0;
+  for (int e = 0; e < 16; ++e) {
+    red_s[tid][e] = active ? s[e & 3][e >> 2] : 0.f;
+    red_c[tid][e] = active ? c[e & 3][e >> 2] : 0.f;
+  }
   __syncthreads();
   for (int e = tid; e < ntile * 16; e += NT) {
     const int t = e >> 4, q = e & 15;
-    double v = 0.0;
-    for (int sl = 0; sl < S; ++sl) v += red[t * S + sl][q];
+    float hi = 0.f, lo = 0.f;
+    for (int sl = 0; sl < S; ++sl) {
+      const float x = red_s[t * S + sl][q];
+      const float u = hi + x, bp = u - hi;
+      lo += ((hi - (u - bp)) + (x - bp)) + red_c[t * S + sl][q];
+      hi = u;
+    }
+    const double v = (double)hi + (double)lo;
     int tt = t, a = 0;
     while (tt >= TM - a) { tt -= TM - a; ++a; }
     const int i = 4 * a + (q & 3), j = 4 * (a + tt) + (q >> 2);
@@ -712,6 +880,140 @@ constexpr int CMAX = 64;   // largest sketch / core dimension
 // stacked rank of its summed terms exceeds the sketch width p, the range
 // finder's inexact case (sketch_stat[1]).
 template <typename T>
+__device__ void count_stacked(const TInfo& ti, const StackDim* __restrict__ stack,
+                              T* const* __restrict__ tab, const int* const* __restrict__ rtab,
+                              int P, int p, unsigned long long* sketch_stat) {
+  int64_t stacked = 0;
+  for (int e = ti.sk_beg; e < ti.sk_end; ++e) {
+    const StackDim sd = stack[e];
+    if (sd.g0 >= 0 && !tab[sd.g0 * P + p]) continue;
+    if (sd.g1 >= 0 && !tab[sd.g1 * P + p]) continue;
+    stacked += dimv(sd.st, sd.rb, sd.ri, rtab, P, p);
+  }
+  atomicAdd(sketch_stat, 1ull);
+  if (stacked > ti.p) atomicAdd(sketch_stat + 1, 1ull);
+}
+
+constexpr int PCHOL_WARP_MAX = 32;   // Grams up to this size: one warp each
+constexpr int PW = 4;                // warps (targets) per CTA of k_pchol_warp
+constexpr size_t PCHOL_WARP_SMEM =
+    PW * (2 * 32 * 33 * sizeof(double) + 2 * 32 * sizeof(double) + 32 * sizeof(int));
+
+// The same pivoted Cholesky for Grams up to 32 x 32, one warp per target,
+// four targets per CTA, warp barriers only: lane i owns row i of the pivot
+// search, of each new factor column and (for the inverse) column i.
+template <typename T>
+__global__ void __launch_bounds__(32 * PW) k_pchol_warp(
+    const TInfo* __restrict__ tis, int tbase, int tend, bool truncate, double tau,
+    T* const* __restrict__ tab, int* const* __restrict__ rtab, int P, int scr_buf, int scr_rbuf,
+    const StackDim* __restrict__ stack, unsigned long long* __restrict__ sketch_stat,
+    double* __restrict__ flops) {
+  constexpr int M = PCHOL_WARP_MAX;
+  const int p = blockIdx.y;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int t = tbase + blockIdx.x * PW + warp;
+  if (t >= tend) return;
+  const TInfo ti = tis[t];
+  T* scr = tab[scr_buf * P + p];
+  int* rs = rtab[scr_rbuf * P + p];
+  if (!scr || !rs) return;
+  const int ld = ti.p;
+  const int pd = truncate ? ti.p : rs[ti.r_ri];
+  if (pd > M) return;   // k_pchol takes it
+  if (truncate && sketch_stat && lane == 0) count_stacked(ti, stack, tab, rtab, P, p, sketch_stat);
+  extern __shared__ double dsm[];
+  double* base = dsm + (size_t)warp * (2 * 32 * 33 + 2 * 32 + 16);
+  double (*L)[M + 1] = reinterpret_cast<double (*)[M + 1]>(base);
+  double (*F)[M + 1] = reinterpret_cast<double (*)[M + 1]>(base + 32 * 33);
+  double* d = base + 2 * 32 * 33;
+  double* colbuf = d + 32;
+  int* piv = reinterpret_cast<int*>(colbuf + 32);
+  const double* G = reinterpret_cast<const double*>(scr + ti.g_off);   // FP64 Gram
+  T* Tm = scr + ti.t_off;
+  for (int e = lane; e < pd * pd; e += 32) {
+    const int i = e % pd, j = e / pd;
+    L[i][j] = G[i + (int64_t)j * ld];
+  }
+  for (int e = lane; e < M * (M + 1); e += 32) (&F[0][0])[e] = 0.0;
+  __syncwarp();
+  double dm = 0.0;
+  if (lane < pd) {
+    d[lane] = L[lane][lane];
+    piv[lane] = lane;
+    dm = d[lane];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) dm = fmax(dm, __shfl_xor_sync(0xffffffffu, dm, o));
+  __syncwarp();
+  const double tol = truncate ? tau * tau * dm : 1e-30 * dm;
+  int r = 0;
+  for (int j = 0; j < pd; ++j) {
+    // largest remaining diagonal among pivoted positions j..pd-1
+    double best = -1.0;
+    int bi = -1;
+    if (lane >= j && lane < pd) { best = d[piv[lane]]; bi = lane; }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (oi >= 0 && (bi < 0 || ov > best || (ov == best && oi < bi))) { best = ov; bi = oi; }
+    }
+    if (bi < 0 || !(best > tol) || !(best > 0.0)) {
+      if (!truncate) r = pd;
+      break;
+    }
+    const int q = bi;
+    const double ljj = sqrt(best);
+    __syncwarp();
+    if (lane == 0) { const int tt = piv[j]; piv[j] = piv[q]; piv[q] = tt; }
+    __syncwarp();
+    if (lane >= j && lane < pd) {
+      const int i = lane;
+      const int src = (i == j) ? q : (i == q ? j : i);
+      double sum = L[piv[i]][piv[j]];
+      for (int l = 0; l < j; ++l) sum -= F[src][l] * F[q][l];
+      colbuf[i] = (i == j) ? ljj : sum / ljj;
+    }
+    __syncwarp();
+    if (q != j && lane < j) {
+      const double tt = F[j][lane]; F[j][lane] = F[q][lane]; F[q][lane] = tt;
+    }
+    if (lane >= j && lane < pd) {
+      F[lane][j] = colbuf[lane];
+      if (lane > j) d[piv[lane]] -= colbuf[lane] * colbuf[lane];
+    }
+    __syncwarp();
+    if (lane == 0) d[piv[j]] = 0.0;
+    __syncwarp();
+    r = j + 1;
+  }
+  __syncwarp();
+  // inverse of the r x r lower factor, column c by lane c, into L
+  if (lane < r) {
+    const int c = lane;
+    for (int i = 0; i < r; ++i) {
+      double sacc = (i == c) ? 1.0 : 0.0;
+      for (int l = c; l < i; ++l) sacc -= F[i][l] * L[l][c];
+      L[i][c] = (F[i][i] != 0.0 && i >= c) ? sacc / F[i][i] : 0.0;
+    }
+  }
+  __syncwarp();
+  for (int e = lane; e < pd * r; e += 32) {
+    const int i = e % pd, c = e / pd;
+    Tm[i + (int64_t)c * ld] = (T)0;
+  }
+  __syncwarp();
+  for (int e = lane; e < r * r; e += 32) {
+    const int j = e % r, c = e / r;
+    Tm[piv[j] + (int64_t)c * ld] = (T)(j <= c ? L[c][j] : 0.0);
+  }
+  if (lane == 0) {
+    rs[ti.r_ri] = r;
+    if (flops) atomicAdd(flops, (double)pd * r * r - 2.0 * r * r * r / 3.0 + (double)r * r * r / 3.0);
+  }
+}
+
+template <typename T>
 __global__ void __launch_bounds__(NT) k_pchol(const TInfo* __restrict__ tis, int tbase, bool truncate,
                                               double tau, T* const* __restrict__ tab,
                                               int* const* __restrict__ rtab, int P, int scr_buf,
@@ -723,19 +1025,10 @@ __global__ void __launch_bounds__(NT) k_pchol(const TInfo* __restrict__ tis, int
   T* scr = tab[scr_buf * P + p];
   int* rs = rtab[scr_rbuf * P + p];
   if (!scr || !rs) return;
-  if (truncate && sketch_stat && threadIdx.x == 0) {
-    int64_t stacked = 0;
-    for (int e = ti.sk_beg; e < ti.sk_end; ++e) {
-      const StackDim sd = stack[e];
-      if (sd.g0 >= 0 && !tab[sd.g0 * P + p]) continue;
-      if (sd.g1 >= 0 && !tab[sd.g1 * P + p]) continue;
-      stacked += dimv(sd.st, sd.rb, sd.ri, rtab, P, p);
-    }
-    atomicAdd(sketch_stat, 1ull);
-    if (stacked > ti.p) atomicAdd(sketch_stat + 1, 1ull);
-  }
   const int ld = ti.p;
   const int pd = truncate ? ti.p : rs[ti.r_ri];
+  if (pd <= PCHOL_WARP_MAX) return;   // k_pchol_warp's cores
+  if (truncate && sketch_stat && threadIdx.x == 0) count_stacked(ti, stack, tab, rtab, P, p, sketch_stat);
   extern __shared__ double dsm[];
   double (*L)[CMAX + 1] = reinterpret_cast<double (*)[CMAX + 1]>(dsm);
   double (*F)[CMAX + 1] = reinterpret_cast<double (*)[CMAX + 1]>(dsm + CMAX * (CMAX + 1));
@@ -853,7 +1146,159 @@ __global__ void __launch_bounds__(NT) k_pchol(const TInfo* __restrict__ tis, int
   }
 }
 
-// Cyclic Jacobi (round-robin parallel order) on the r x r symmetric core H.
+constexpr int EIG_WARP_MAX = 16;   // cores up to this size: one warp each
+
+// The same cyclic Jacobi for small cores (1 < r <= 16), one warp per target,
+// eight targets per CTA: the rotations of a round are computed and applied
+// by the warp's lanes with warp barriers only (same rotation sequence and
+// stopping rule as k_eig).
+template <typename T>
+__global__ void __launch_bounds__(NT) k_eig_warp(const TInfo* __restrict__ tis, int tbase,
+                                                 int tend, double eps, int kc, int c_rbuf,
+                                                 T* const* __restrict__ tab,
+                                                 int* const* __restrict__ rtab, int P,
+                                                 int scr_buf, int scr_rbuf, int* err,
+                                                 double* __restrict__ flops) {
+  constexpr int M = EIG_WARP_MAX;
+  const int p = blockIdx.y;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int t = tbase + blockIdx.x * (NT / 32) + warp;
+  __shared__ double As[NT / 32][M][M + 1], Vs[NT / 32][M][M + 1];
+  __shared__ double css[NT / 32][M / 2], sns[NT / 32][M / 2], lams[NT / 32][M];
+  __shared__ int pps[NT / 32][M / 2], qqs[NT / 32][M / 2], ords[NT / 32][M];
+  if (t >= tend) return;
+  const TInfo ti = tis[t];
+  T* scr = tab[scr_buf * P + p];
+  int* rs = rtab[scr_rbuf * P + p];
+  int* crank = rtab[c_rbuf * P + p];
+  if (!scr || !rs || !crank) return;
+  const int r = rs[ti.r_ri];
+  if (r <= 0 || r > M) return;   // r == 0: k_eig writes the zero rank
+  const int ld = ti.p;
+  double (*A)[M + 1] = As[warp];
+  double (*V)[M + 1] = Vs[warp];
+  double* cs = css[warp];
+  double* sn = sns[warp];
+  int* pp = pps[warp];
+  int* qq = qqs[warp];
+  const double* H = reinterpret_cast<const double*>(scr + ti.h_off);
+  T* W = scr + ti.w_off;
+  for (int e = lane; e < r * r; e += 32) {
+    const int i = e % r, j = e / r;
+    A[i][j] = 0.5 * (H[i + (int64_t)j * ld] + H[j + (int64_t)i * ld]);
+    V[i][j] = (i == j) ? 1.0 : 0.0;
+  }
+  __syncwarp();
+  const int nn = (r + 1) & ~1;
+  const int npair = nn / 2;
+  int sweeps_done = 0;
+  const double conv = sizeof(T) == 8 ? 1e-30 : 1e-16;
+  for (int sweep = 0; sweep < 40; ++sweep) {
+    double off = 0, tot = 0;
+    for (int e = lane; e < r * r; e += 32) {
+      const int i = e % r, j = e / r;
+      const double v = A[i][j] * A[i][j];
+      tot += v;
+      if (i != j) off += v;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      off += __shfl_xor_sync(0xffffffffu, off, o);
+      tot += __shfl_xor_sync(0xffffffffu, tot, o);
+    }
+    if (off <= conv * tot || r == 1) break;
+    ++sweeps_done;
+    for (int round = 0; round < nn - 1; ++round) {
+      if (lane < npair) {
+        const int k = lane;
+        const int pa = k, pb = nn - 1 - k;
+        const int a = (pa == 0) ? 0 : 1 + ((pa - 1 + round) % (nn - 1));
+        const int b = 1 + ((pb - 1 + round) % (nn - 1));
+        const int lo = a < b ? a : b, hi = a < b ? b : a;
+        pp[k] = lo; qq[k] = hi;
+        double c = 1.0, sv = 0.0;
+        if (hi < r) {
+          const double apq = A[lo][hi];
+          if (apq != 0.0) {
+            const double tau_ = (A[hi][hi] - A[lo][lo]) / (2.0 * apq);
+            const double tt = (tau_ >= 0 ? 1.0 : -1.0) / (fabs(tau_) + sqrt(1.0 + tau_ * tau_));
+            c = rsqrt(1.0 + tt * tt);
+            sv = tt * c;
+          }
+        }
+        cs[k] = c; sn[k] = sv;
+      }
+      __syncwarp();
+      const int nblk = npair * npair;
+      for (int e = lane; e < nblk + npair * r; e += 32) {
+        if (e < nblk) {
+          const int k1 = e / npair, k2 = e - k1 * npair;
+          const int a1 = pp[k1], b1 = qq[k1], a2 = pp[k2], b2 = qq[k2];
+          const bool h1 = b1 < r, h2 = b2 < r;
+          const double c1 = cs[k1], s1 = sn[k1], c2 = cs[k2], s2 = sn[k2];
+          const double x00 = A[a1][a2];
+          const double x01 = h2 ? A[a1][b2] : 0.0;
+          const double x10 = h1 ? A[b1][a2] : 0.0;
+          const double x11 = (h1 && h2) ? A[b1][b2] : 0.0;
+          const double y00 = c2 * x00 - s2 * x01, y01 = s2 * x00 + c2 * x01;
+          const double y10 = c2 * x10 - s2 * x11, y11 = s2 * x10 + c2 * x11;
+          A[a1][a2] = c1 * y00 - s1 * y10;
+          if (h2) A[a1][b2] = c1 * y01 - s1 * y11;
+          if (h1) A[b1][a2] = s1 * y00 + c1 * y10;
+          if (h1 && h2) A[b1][b2] = s1 * y01 + c1 * y11;
+        } else {
+          const int f = e - nblk;
+          const int k = f / r, iv = f - k * r;
+          const int a = pp[k], b = qq[k];
+          if (b < r) {
+            const double c = cs[k], sv = sn[k];
+            const double vx = V[iv][a], vy = V[iv][b];
+            V[iv][a] = c * vx - sv * vy;
+            V[iv][b] = sv * vx + c * vy;
+          }
+        }
+      }
+      __syncwarp();
+    }
+  }
+  double* lam = lams[warp];
+  int* order = ords[warp];
+  if (lane < r) lam[lane] = A[lane][lane];
+  __syncwarp();
+  if (lane < r) {
+    int pos = 0;
+    for (int j = 0; j < r; ++j)
+      if (lam[j] > lam[lane] || (lam[j] == lam[lane] && j < lane)) ++pos;
+    order[pos] = lane;
+  }
+  __syncwarp();
+  int k = 0;
+  if (lane == 0) {
+    const double l1 = lam[order[0]];
+    if (l1 > 0.0) {
+      const double s1 = sqrt(l1);
+      for (int j = 0; j < r; ++j) {
+        const double lj = lam[order[j]];
+        if (lj > 0.0 && sqrt(lj) > eps * s1) ++k;
+        else break;
+      }
+    }
+    if (k > kc) {
+      atomicOr(err, ERR_RANKCAP);
+      k = kc;
+    }
+    crank[ti.c_leaf] = k;
+    if (flops) atomicAdd(flops, 9.0 * r * r * r * sweeps_done);
+  }
+  k = __shfl_sync(0xffffffffu, k, 0);
+  for (int e = lane; e < r * k; e += 32) {
+    const int i = e % r, j = e / r;
+    W[i + (int64_t)j * ld] = (T)V[i][order[j]];
+  }
+}
+
+// Cyclic Jacobi (round-robin parallel order) on the r x r symmetric core H
+// (cores with r > 16; k_eig_warp takes the smaller ones).
 template <typename T>
 __global__ void __launch_bounds__(NT) k_eig(const TInfo* __restrict__ tis, int tbase, double eps,
                                             int kc, int c_rbuf, T* const* __restrict__ tab,
@@ -871,6 +1316,7 @@ __global__ void __launch_bounds__(NT) k_eig(const TInfo* __restrict__ tis, int t
     if (threadIdx.x == 0) crank[ti.c_leaf] = 0;
     return;
   }
+  if (r <= EIG_WARP_MAX) return;   // k_eig_warp's cores
   extern __shared__ double dsm[];
   double (*A)[CMAX + 1] = reinterpret_cast<double (*)[CMAX + 1]>(dsm);
   double (*V)[CMAX + 1] = reinterpret_cast<double (*)[CMAX + 1]>(dsm + CMAX * (CMAX + 1));
@@ -1047,14 +1493,9 @@ __host__ __device__ constexpr double leaf_growth_max() { return sizeof(T) == 8 ?
 // and columns t / 64 + 4 m.  The interchanges become one column permutation
 // of the result, applied when it is stored.
 template <typename T>
-__global__ void __launch_bounds__(NT) k_leaf_inv(T* const* __restrict__ dense, int64_t off, int n,
-                                                 int* err, double* __restrict__ flops) {
+__device__ void leaf_inv_fp64(T* __restrict__ Ap, int n, double (*A)[CMAX + 1], int* err,
+                              double* __restrict__ flops) {
   static_assert(NT == 256 && CMAX == 64, "thread mapping assumes 256 threads and 64 x 64 leaves");
-  const int p = blockIdx.x;
-  T* Ap = dense[p];
-  if (!Ap) return;
-  Ap += off;
-  __shared__ double A[CMAX][CMAX + 1];
   __shared__ double rowk[CMAX], colk[CMAX], krow[CMAX];
   __shared__ int piv[CMAX];
   __shared__ int cmap[CMAX];
@@ -1147,6 +1588,200 @@ __global__ void __launch_bounds__(NT) k_leaf_inv(T* const* __restrict__ dense, i
   for (int j = tj; j < n; j += 4)
     if (ti < n) Ap[ti + (int64_t)cmap[j] * n] = (T)A[ti][j];
   if (flops && threadIdx.x == 0) atomicAdd(flops, 2.0 * n * n * n);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NT) k_leaf_inv(T* const* __restrict__ dense, int64_t off, int n,
+                                                 int* err, double* __restrict__ flops) {
+  T* Ap = dense[blockIdx.x];
+  if (!Ap) return;
+  __shared__ double A[CMAX][CMAX + 1];
+  leaf_inv_fp64<T>(Ap + off, n, A, err, flops);
+}
+
+__device__ __forceinline__ float block_absmaxf(float v, float* red8) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if ((threadIdx.x & 31) == 0) red8[threadIdx.x >> 5] = v;
+  __syncthreads();
+  float r = red8[0];
+  for (int w = 1; w < NT / 32; ++w) r = fmaxf(r, red8[w]);
+  __syncthreads();
+  return r;
+}
+
+// Leaf inverse of float storage without the FP64 pipe (a small fraction of
+// the FP32 one on this part): Gauss-Jordan with partial pivoting in float
+// gives X0 with relative error ~ cond * 6e-8; mixed-precision iterative
+// refinement X <- X + X R, R = I - A X, with the residual formed from exact
+// products and compensated sums (float-float, the Gram kernels' ff_fma),
+// then contracts the error by ~ |R| per step until the correction is below
+// two units in the last place of the largest entry: the result is the
+// inverse to float rounding, as the FP64 elimination rounded to float gives.
+// When it cannot get there (a float pivot of zero, a non-finite entry, a
+// first residual above 1/(2n), no convergence in three steps) the leaf is
+// inverted by the FP64 elimination instead (the shared buffers reused), so
+// the pivot and growth diagnostics are those of the FP64 form.
+constexpr int LEAF_F_SMEM = 3 * CMAX * (CMAX + 1) * (int)sizeof(float);
+
+__global__ void __launch_bounds__(NT) k_leaf_inv_f(float* const* __restrict__ dense, int64_t off,
+                                                   int n, int* err, double* __restrict__ flops) {
+  static_assert(NT == 256 && CMAX == 64, "thread mapping assumes 256 threads and 64 x 64 leaves");
+  static_assert(2 * CMAX * (CMAX + 1) * sizeof(float) >= CMAX * (CMAX + 1) * sizeof(double),
+                "the FP64 fallback fits the X and R buffers");
+  float* Ap = dense[blockIdx.x];
+  if (!Ap) return;
+  Ap += off;
+  extern __shared__ __align__(16) float lsm[];
+  float (*A0)[CMAX + 1] = reinterpret_cast<float (*)[CMAX + 1]>(lsm);
+  float (*X)[CMAX + 1] = reinterpret_cast<float (*)[CMAX + 1]>(lsm + CMAX * (CMAX + 1));
+  float (*R)[CMAX + 1] = reinterpret_cast<float (*)[CMAX + 1]>(lsm + 2 * CMAX * (CMAX + 1));
+  __shared__ float rowk[CMAX], colk[CMAX], krow[CMAX];
+  __shared__ int piv[CMAX];
+  __shared__ int cmap[CMAX];
+  __shared__ int s_q, s_bad;
+  __shared__ float s_pinv;
+  __shared__ float red8[NT / 32];
+  const int ti = threadIdx.x & 63, tj = threadIdx.x >> 6;
+  float amax = 0.f;
+  for (int j = tj; j < n; j += 4)
+    if (ti < n) {
+      const float v = Ap[ti + (int64_t)j * n];
+      A0[ti][j] = v;
+      X[ti][j] = v;
+      amax = fmaxf(amax, fabsf(v));
+    }
+  if (threadIdx.x == 0) s_bad = 0;
+  __syncthreads();
+  amax = block_absmaxf(amax, red8);
+  // 1. Gauss-Jordan in float (the FP64 elimination's steps)
+  for (int k = 0; k < n; ++k) {
+    if (threadIdx.x < 32) {
+      const int lane = threadIdx.x;
+      float best = -1.f;
+      int q = -1;
+      for (int i = k + lane; i < n; i += 32) {
+        const float v = fabsf(X[i][k]);
+        if (v > best) { best = v; q = i; }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const float ov = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, q, o);
+        if (oi >= 0 && (q < 0 || ov > best || (ov == best && oi < q))) { best = ov; q = oi; }
+      }
+      if (q < 0 || !(best > 0.f)) {
+        if (lane == 0) s_bad = 1;
+      } else {
+        const float pinv = 1.f / X[q][k];
+        for (int j = lane; j < n; j += 32) {
+          rowk[j] = (j == k) ? pinv : X[q][j] * pinv;
+          krow[j] = X[k][j];
+          colk[j] = (j == k) ? 0.f : (j == q ? X[k][k] : X[j][k]);
+        }
+        if (lane == 0) { s_q = q; s_pinv = pinv; piv[k] = q; }
+      }
+    }
+    __syncthreads();
+    if (s_bad) break;
+    const int q = s_q;
+    const float pinv = s_pinv;
+    if (ti < n) {
+      const float f = colk[ti];
+      for (int j = tj; j < n; j += 4) {
+        if (ti == k) {
+          X[ti][j] = rowk[j];
+        } else {
+          const float old = (ti == q) ? krow[j] : X[ti][j];
+          X[ti][j] = (j == k) ? -f * pinv : old - f * rowk[j];
+        }
+      }
+    }
+    __syncthreads();
+  }
+  bool fallback = s_bad != 0;
+  int steps = 0;
+  if (!fallback) {
+    if (threadIdx.x == 0) {
+      int pi_[CMAX];
+      for (int c = 0; c < n; ++c) pi_[c] = c;
+      for (int k = n - 1; k >= 0; --k) {
+        const int q = piv[k];
+        const int t = pi_[k]; pi_[k] = pi_[q]; pi_[q] = t;
+      }
+      for (int c = 0; c < n; ++c) cmap[pi_[c]] = c;
+    }
+    __syncthreads();
+    // the inverse in natural column order, into R; then the buffers trade roles
+    for (int j = tj; j < n; j += 4)
+      if (ti < n) R[ti][cmap[j]] = X[ti][j];
+    __syncthreads();
+    float (*tmp)[CMAX + 1] = X; X = R; R = tmp;
+    // 2. refinement
+    bool done = false;
+    for (int it = 0; it < 3 && !done && !fallback; ++it) {
+      ++steps;
+      // R = I - A0 X from exact products and compensated sums
+      float rmax = 0.f;
+      if (ti < n)
+        for (int j = tj; j < n; j += 4) {
+          float sh = 0.f, sl = 0.f;
+          for (int l = 0; l < n; ++l) ff_fma(sh, sl, A0[ti][l], X[l][j]);
+          const float r = ((ti == j ? 1.f : 0.f) - sh) - sl;
+          R[ti][j] = r;
+          rmax = (fabsf(r) <= 3.0e38f) ? fmaxf(rmax, fabsf(r)) : INFINITY;
+        }
+      rmax = block_absmaxf(rmax, red8);   // (its barriers also publish R)
+      if (it == 0 && !(rmax * n <= 0.5f)) { fallback = true; break; }
+      // correction D = X R; X += D
+      float d[CMAX / 4];
+      float dmax = 0.f;
+#pragma unroll
+      for (int q = 0; q < CMAX / 4; ++q) {
+        const int j = tj + 4 * q;
+        float v = 0.f;
+        if (ti < n && j < n)
+          for (int l = 0; l < n; ++l) v = fmaf(X[ti][l], R[l][j], v);
+        d[q] = v;
+        dmax = (fabsf(v) <= 3.0e38f) ? fmaxf(dmax, fabsf(v)) : INFINITY;
+      }
+      __syncthreads();   // every read of X is done
+      float xmax = 0.f;
+#pragma unroll
+      for (int q = 0; q < CMAX / 4; ++q) {
+        const int j = tj + 4 * q;
+        if (ti < n && j < n) {
+          X[ti][j] += d[q];
+          const float v = fabsf(X[ti][j]);
+          xmax = (v <= 3.0e38f) ? fmaxf(xmax, v) : INFINITY;
+        }
+      }
+      dmax = block_absmaxf(dmax, red8);
+      xmax = block_absmaxf(xmax, red8);
+      if (!(xmax <= 3.0e38f) || !(dmax <= 3.0e38f)) fallback = true;
+      else if (dmax <= 2.4e-7f * xmax) done = true;
+    }
+    if (!done) fallback = true;
+    if (!fallback) {
+      float xmax = 0.f;
+      for (int j = tj; j < n; j += 4)
+        if (ti < n) xmax = fmaxf(xmax, fabsf(X[ti][j]));
+      xmax = block_absmaxf(xmax, red8);
+      if (!((double)amax * (double)xmax <= leaf_growth_max<float>())) {
+        if (threadIdx.x == 0) atomicOr(err, ERR_GROWTH);
+        return;
+      }
+      for (int j = tj; j < n; j += 4)
+        if (ti < n) Ap[ti + (int64_t)j * n] = X[ti][j];
+      if (flops && threadIdx.x == 0) atomicAdd(flops, 2.0 * n * n * n * (1 + 2 * steps));
+      return;
+    }
+  }
+  // 3. FP64 elimination of the stored leaf (untouched so far), in the X and
+  // R buffers (contiguous: X and R may have traded roles, the pair has not)
+  __syncthreads();
+  leaf_inv_fp64<float>(Ap, n, reinterpret_cast<double (*)[CMAX + 1]>(lsm + CMAX * (CMAX + 1)),
+                       err, flops);
 }
 
 // out = sgn * diag(r) X diag(c): dense part
@@ -1258,7 +1893,8 @@ __global__ void k_plane_lr(const double* __restrict__ coef, int n, const int* __
 
 template <typename T>
 void launch_ggemm(const Plan& pl, int gbeg, int gend, T* const* d_tab, const int* const* d_rtab,
-                  int P, const double* d_coefs, cudaStream_t st, double* d_fl, int tag) {
+                  int P, const double* d_coefs, cudaStream_t st, double* d_fl, int tag,
+                  int variant, int* d_err) {
   int ng = gend - gbeg;
   if (ng <= 0 || P <= 0) return;
   using Acc = T;
@@ -1270,17 +1906,35 @@ void launch_ggemm(const Plan& pl, int gbeg, int gend, T* const* d_tab, const int
     // warp per group for the inner products, and for the small-output
     // sketch / projection stages where the multiply type is float (the FP64
     // instance of the warp kernel holds ~200 registers: one CTA per SM)
+    // variant 1 swaps the warp-per-group and CTA-per-group inner-product
+    // kernels; for float it gives the staged kernel 3 CTAs per SM and 80
+    // registers (no spills) instead of 4 CTAs and 64 registers, for double
+    // half the staging per K-step.  Variant 2 (float, non-dot stages) runs
+    // one warp per group (k_gwarp).
+    const bool warp_dot = (tag == TAG_M || (sizeof(T) == 4 && (tag == TAG_S || tag == TAG_P)));
     if (sizeof(T) == 4 && (tag == TAG_G || tag == TAG_G2 || tag == TAG_H)) {
       k_gram_ff<<<grid, NT, 0, st>>>(gr, it, (float* const*)d_tab, d_rtab, P, gbeg + g0, d_fl);
-    } else if (tag == TAG_M || (sizeof(T) == 4 && (tag == TAG_S || tag == TAG_P))) {
+    } else if (variant == 2 && sizeof(T) == 4 && d_err && !tag_is_dot(tag)) {
+      const int cnt = std::min(maxg, ng - g0);
+      dim3 gw((cnt + NT / 32 - 1) / (NT / 32), P);
+      k_gwarp<<<gw, NT, 0, st>>>(gr, it, (float* const*)d_tab, d_rtab, P, gbeg + g0,
+                                 gbeg + g0 + cnt, d_coefs, d_fl, d_err);
+    } else if (tag_is_dot(tag) && (warp_dot != (variant == 1))) {
       const int cnt = std::min(maxg, ng - g0);
       dim3 gw((cnt + NT / 32 - 1) / (NT / 32), P);
       k_gdot_warp<T, Acc><<<gw, NT, 0, st>>>(gr, it, d_tab, d_rtab, P, gbeg + g0, gbeg + g0 + cnt,
                                              d_coefs, d_fl);
     } else if (tag_is_dot(tag))
       k_gdot<T, Acc><<<grid, NT, 0, st>>>(gr, it, d_tab, d_rtab, P, gbeg + g0, d_coefs, d_fl);
+    else if (variant == 1 && sizeof(Acc) == 4)
+      k_ggemm<T, Acc, STAGE_BYTES, 3>
+          <<<grid, NT, 0, st>>>(gr, it, d_tab, d_rtab, P, gbeg + g0, d_coefs, d_fl);
+    else if (variant == 1)
+      k_ggemm<T, Acc, STAGE_BYTES / 2, 2>
+          <<<grid, NT, 0, st>>>(gr, it, d_tab, d_rtab, P, gbeg + g0, d_coefs, d_fl);
     else
-      k_ggemm<T, Acc><<<grid, NT, 0, st>>>(gr, it, d_tab, d_rtab, P, gbeg + g0, d_coefs, d_fl);
+      k_ggemm<T, Acc, STAGE_BYTES, sizeof(Acc) == 4 ? 4 : 2>
+          <<<grid, NT, 0, st>>>(gr, it, d_tab, d_rtab, P, gbeg + g0, d_coefs, d_fl);
     ACR_LAUNCHED(1);
   }
 }
@@ -1293,6 +1947,16 @@ void launch_pchol(const Plan& pl, int tbeg, int tend, bool truncate, double tau,
   if (nt <= 0 || P <= 0) return;
   const size_t smem = 2 * CMAX * (CMAX + 1) * sizeof(double);
   ACR_CUDA(cudaFuncSetAttribute(k_pchol<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  ACR_CUDA(cudaFuncSetAttribute(k_pchol_warp<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)PCHOL_WARP_SMEM));
+  for (int t0 = 0; t0 < nt; t0 += 65535 * PW) {
+    const int cnt = std::min(65535 * PW, nt - t0);
+    dim3 grid((cnt + PW - 1) / PW, P);
+    k_pchol_warp<T><<<grid, 32 * PW, PCHOL_WARP_SMEM, st>>>(
+        (const TInfo*)pl.d_targets, tbeg + t0, tbeg + t0 + cnt, truncate, tau, d_tab, d_rtab, P,
+        3 * pl.nroles, pl.nroles, (const StackDim*)pl.d_stack, d_sketch_stat, d_fl);
+    ACR_LAUNCHED(1);
+  }
   for (int t0 = 0; t0 < nt; t0 += 65535) {
     dim3 grid(std::min(65535, nt - t0), P);
     k_pchol<T><<<grid, NT, smem, st>>>((const TInfo*)pl.d_targets, tbeg + t0, truncate, tau, d_tab,
@@ -1310,6 +1974,17 @@ void launch_eig(const Plan& pl, int tbeg, int tend, double eps, int kc, int c_ro
   if (nt <= 0 || P <= 0) return;
   const size_t smem = 2 * CMAX * (CMAX + 1) * sizeof(double);
   ACR_CUDA(cudaFuncSetAttribute(k_eig<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  {
+    const int per = NT / 32;
+    for (int t0 = 0; t0 < nt; t0 += 65535 * per) {
+      const int cnt = std::min(65535 * per, nt - t0);
+      dim3 grid((cnt + per - 1) / per, P);
+      k_eig_warp<T><<<grid, NT, 0, st>>>((const TInfo*)pl.d_targets, tbeg + t0, tbeg + t0 + cnt,
+                                         eps, kc, c_role, d_tab, d_rtab, P, 3 * pl.nroles,
+                                         pl.nroles, d_err, d_fl);
+      ACR_LAUNCHED(1);
+    }
+  }
   for (int t0 = 0; t0 < nt; t0 += 65535) {
     dim3 grid(std::min(65535, nt - t0), P);
     k_eig<T><<<grid, NT, smem, st>>>((const TInfo*)pl.d_targets, tbeg + t0, eps, kc, c_role, d_tab,
@@ -1322,7 +1997,17 @@ template <typename T>
 void launch_leaf_inv(T* const* d_dense, int64_t off, int lsz, int P, int* d_err, cudaStream_t st,
                      double* d_fl) {
   if (P <= 0) return;
-  k_leaf_inv<T><<<P, NT, 0, st>>>(d_dense, off, lsz, d_err, d_fl);
+  if constexpr (std::is_same<T, float>::value) {
+    static bool attr = false;
+    if (!attr) {
+      ACR_CUDA(cudaFuncSetAttribute(k_leaf_inv_f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    LEAF_F_SMEM));
+      attr = true;
+    }
+    k_leaf_inv_f<<<P, NT, LEAF_F_SMEM, st>>>(d_dense, off, lsz, d_err, d_fl);
+  } else {
+    k_leaf_inv<T><<<P, NT, 0, st>>>(d_dense, off, lsz, d_err, d_fl);
+  }
   ACR_LAUNCHED(1);
 }
 
@@ -1358,7 +2043,7 @@ void launch_plane_to_h(const StructDev& sd, const double* coef, int n, const int
 
 #define ACR_INST(T)                                                                              \
   template void launch_ggemm<T>(const Plan&, int, int, T* const*, const int* const*, int,        \
-                                const double*, cudaStream_t, double*, int);                      \
+                                const double*, cudaStream_t, double*, int, int, int*);           \
   template void launch_pchol<T>(const Plan&, int, int, bool, double, T* const*, int* const*, int, \
                                 cudaStream_t, unsigned long long*, double*);                     \
   template void launch_eig<T>(const Plan&, int, int, double, int, int, T* const*, int* const*,   \
