@@ -137,7 +137,7 @@ def oracle_scale():
 
 
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "grouped_gemm_dram_codi_n64.md")
-GEMM_SOURCE = os.path.join(ROOT, "paper_1712_08872_gb300", "csrc", "acr_setup_kernels.cu")
+GEMM_SOURCE = os.path.join(ROOT, "paper_1712_08872_gb300", "csrc", "acr_gemm_kernels.cu")
 
 
 def gemm_traffic_per_flop():
@@ -251,6 +251,7 @@ def profile_setup(args):
         print("    %-14s %9.1f ms  %10.3f GFLOP  %8.3f TFLOP/s"
               % (nm, p.stage_ms[i], p.stage_flops[i] / 1e9,
                  p.stage_flops[i] / max(p.stage_ms[i], 1e-9) / 1e9))
+    print("  leaf inverses by the FP64 fallback: %d" % inf.leaf_fp64_fallbacks)
     print("  inversion ms per level", [round(x, 1) for x in p.inv_ms[:inf.levels + 1]])
     print("  update ms per level   ", [round(x, 1) for x in p.upd_ms[:inf.levels]])
     return 0
@@ -688,6 +689,7 @@ def main():
             "iterations": solve_info.iterations, "rel_residual": solve_info.rel_residual,
             "setup_s": setup_info.setup_ms / 1000.0,
             "setup_host_issue_s": setup_info.host_issue_ms / 1000.0,
+            "leaf_fp64_fallbacks": setup_info.leaf_fp64_fallbacks,
             "solve_s": solve_info.solve_ms / 1000.0,
             "max_rank": setup_info.max_rank, "factor_gb": setup_info.factor_bytes / 1e9,
             "fp64_plain": fp64, "bf16_factors": bf16,

@@ -109,6 +109,9 @@ typedef struct {
                                 terms summed into the block) exceeded the sketch width
                                 min(rank_cap + 8, 64): their range finder was a randomized
                                 approximation instead of exact */
+  int64_t leaf_fp64_fallbacks; /* float storage: dense leaf inverses (all planes, all levels)
+                                whose float elimination + refinement could not reach float
+                                accuracy and were done by the FP64 elimination instead */
   double host_issue_ms;      /* host time the setup's device phase took to issue its work
                                 (launches, copies) up to its closing event; near setup_ms when
                                 the issue rate, not the device, bounds the setup */

@@ -55,6 +55,7 @@ class SetupInfo(ctypes.Structure):
                 ("structure_ms", ctypes.c_double), ("apply_bytes", ctypes.c_int64),
                 ("apply_flops", ctypes.c_int64), ("lr_truncations", ctypes.c_int64),
                 ("sketch_overflows", ctypes.c_int64),
+                ("leaf_fp64_fallbacks", ctypes.c_int64),
                 ("host_issue_ms", ctypes.c_double)]
 
 

@@ -282,7 +282,8 @@ class Engine : public EngineBase {
   size_t scratch_budget = 0;
   double* d_coefs = nullptr;
   int* d_err = nullptr;
-  unsigned long long* d_sketch_stat = nullptr;   // truncated targets, stacked-rank overflows
+  unsigned long long* d_sketch_stat = nullptr;   // truncated targets, stacked-rank overflows,
+                                                 // leaf inverses by the FP64 fallback
   int* d_planes_all = nullptr;
   bool has_cpl = false;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -649,7 +650,7 @@ class Engine : public EngineBase {
     if (c.child[0] < 0) {
       int nd = S.node(t, t);
       timed(3, [&] { launch_leaf_inv<T>((T* const*)d_xdense, S.dense_off(S.bn[nd].leaf), S.lsz, P,
-                                        d_err, st, fl(3)); });
+                                        d_err, st, fl(3), d_sketch_stat + 2); });
       return;
     }
     const int t1 = c.child[0], t2 = c.child[1];
@@ -809,7 +810,7 @@ void Engine<T>::prepare(const double* const* coefs, cudaStream_t st, bool count_
   d_coefs = (double*)upload(coefs_pm, owned);
   d_err = (int*)dmalloc(sizeof(int));
   owned.push_back(d_err);
-  d_sketch_stat = (unsigned long long*)dmalloc(2 * sizeof(unsigned long long));
+  d_sketch_stat = (unsigned long long*)dmalloc(3 * sizeof(unsigned long long));
   owned.push_back(d_sketch_stat);
   if (profiling) {
     d_fl = (double*)dmalloc(21 * sizeof(double));
@@ -875,7 +876,7 @@ void Engine<T>::execute(cudaStream_t st) {
   levels.clear();
   if (!dry) {
     ACR_CUDA(cudaMemsetAsync(d_err, 0, sizeof(int), st));
-    ACR_CUDA(cudaMemsetAsync(d_sketch_stat, 0, 2 * sizeof(unsigned long long), st));
+    ACR_CUDA(cudaMemsetAsync(d_sketch_stat, 0, 3 * sizeof(unsigned long long), st));
   }
   const int NP = count * n;   // plane slots
 
@@ -1105,10 +1106,11 @@ void Engine<T>::finish(cudaStream_t st, bool one_shot) {
   info.n_dense_leaves = sd.nd;
   info.n_lowrank_leaves = sd.nl;
   {
-    unsigned long long ss[2] = {0, 0};
+    unsigned long long ss[3] = {0, 0, 0};
     ACR_CUDA(cudaMemcpy(ss, d_sketch_stat, sizeof(ss), cudaMemcpyDeviceToHost));
     info.lr_truncations = (int64_t)ss[0];
     info.sketch_overflows = (int64_t)ss[1];
+    info.leaf_fp64_fallbacks = (int64_t)ss[2];
   }
   if (one_shot) {
     // the scratch arena is only needed by the setup; in the BF16 form the

@@ -67,11 +67,14 @@ void launch_eig(const Plan& pl, int tbeg, int tend, double eps, int kc, int c_ro
                 T* const* d_tab, int* const* d_rtab, int P, int* d_err, cudaStream_t st,
                 double* d_flops = nullptr);
 
-// In-place FP64 Gauss-Jordan inverse (partial pivoting) of one dense
-// lsz x lsz leaf in each of P H-matrices (base pointers in d_dense[p]).
+// In-place Gauss-Jordan inverse (partial pivoting) of one dense lsz x lsz
+// leaf in each of P H-matrices (base pointers in d_dense[p]): FP64, or for
+// float storage float elimination with iterative refinement, counting the
+// leaves that needed the FP64 elimination instead in *d_fallbacks (may be
+// null).
 template <typename T>
 void launch_leaf_inv(T* const* d_dense, int64_t off, int lsz, int P, int* d_err, cudaStream_t st,
-                     double* d_flops = nullptr);
+                     double* d_flops = nullptr, unsigned long long* d_fallbacks = nullptr);
 
 // Device copies of the plane structure arrays.
 struct StructDev {
