@@ -235,8 +235,13 @@ def profile_setup(args):
     acr.acr_stencil_codi(n, torch.tensor(beta.ravel(), dtype=torch.float64, device=dev), coef)
     prec = acr.ACR_FP64 if args.fp64 else acr.ACR_FP32
     stream = torch.cuda.current_stream()
+    table = None
+    if args.tuned:
+        table = acr.acr_autotune_gemm(n, coef, spec["eps"], 2.0, spec["leaf"], prec,
+                                      args.rank_cap, stream)[0]
+        print("kernel shapes per stage:", table[:13])
     h = acr.acr_setup(n, coef, spec["eps"], 2.0, spec["leaf"], prec, args.rank_cap, stream,
-                      acr.ACR_FLAG_PROFILE)
+                      acr.ACR_FLAG_PROFILE, table)
     p = acr.acr_get_profile(h)
     inf = acr.acr_get_setup_info(h)
     acr.acr_destroy(h)
@@ -322,6 +327,8 @@ def main():
                     help="run one profiled setup (ACR_FLAG_PROFILE) at --n and print its "
                          "per-class, per-stage and per-level times; no benchmark line")
     ap.add_argument("--fp64", action="store_true", help="with --profile-setup: FP64 factors")
+    ap.add_argument("--tuned", action="store_true",
+                    help="with --profile-setup: GEMM kernel shapes from acr_autotune_gemm")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

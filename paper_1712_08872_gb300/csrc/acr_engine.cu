@@ -631,7 +631,7 @@ class Engine : public EngineBase {
                   int pc, cudaStream_t st) {
     double* f = sg.tag >= 0 ? fl(5 + sg.tag) : fl(0);
     launch_ggemm<T>(pl, sg.beg, sg.end, d_tab, d_rtab, pc, d_coefs, st, f, sg.tag,
-                    sg.tag >= 0 && sg.tag < 16 ? gemm_variant[sg.tag] : 0, d_err);
+                    sg.tag >= 0 && sg.tag < 16 ? gemm_variant[sg.tag] : 0, d_err, sg.nwide);
   }
 
   double tau_orth() const {

@@ -838,9 +838,17 @@ __global__ void __launch_bounds__(NT) k_gram_ff(const GGroup* __restrict__ group
 template <typename T>
 void launch_ggemm(const Plan& pl, int gbeg, int gend, T* const* d_tab, const int* const* d_rtab,
                   int P, const double* d_coefs, cudaStream_t st, double* d_fl, int tag,
-                  int variant, int* d_err) {
+                  int variant, int* d_err, int nwide) {
   int ng = gend - gbeg;
   if (ng <= 0 || P <= 0) return;
+  if (variant == 2 && nwide > 0 && sizeof(T) == 4 && !tag_is_dot(tag)) {
+    // the stage's wide groups (64-column outputs: dense products) in the
+    // staged CTA kernel, the rest one warp per group
+    const int w = std::min(nwide, ng);
+    launch_ggemm<T>(pl, gbeg, gbeg + w, d_tab, d_rtab, P, d_coefs, st, d_fl, tag, 0, d_err, 0);
+    launch_ggemm<T>(pl, gbeg + w, gend, d_tab, d_rtab, P, d_coefs, st, d_fl, tag, 2, d_err, 0);
+    return;
+  }
   using Acc = T;
   const int maxg = 65535;
   for (int g0 = 0; g0 < ng; g0 += maxg) {
@@ -884,8 +892,8 @@ void launch_ggemm(const Plan& pl, int gbeg, int gend, T* const* d_tab, const int
 }
 
 template void launch_ggemm<double>(const Plan&, int, int, double* const*, const int* const*, int,
-                                   const double*, cudaStream_t, double*, int, int, int*);
+                                   const double*, cudaStream_t, double*, int, int, int*, int);
 template void launch_ggemm<float>(const Plan&, int, int, float* const*, const int* const*, int,
-                                  const double*, cudaStream_t, double*, int, int, int*);
+                                  const double*, cudaStream_t, double*, int, int, int*, int);
 
 }  // namespace acr

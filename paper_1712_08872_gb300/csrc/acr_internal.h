@@ -50,7 +50,7 @@ struct CudaError {
 template <typename T>
 void launch_ggemm(const Plan& pl, int gbeg, int gend, T* const* d_tab, const int* const* d_rtab,
                   int P, const double* d_coefs, cudaStream_t st, double* d_flops = nullptr,
-                  int tag = -1, int variant = 0, int* d_err = nullptr);
+                  int tag = -1, int variant = 0, int* d_err = nullptr, int nwide = 0);
 
 // Pivoted-Cholesky orthonormalisation cores (FP64) of plan targets.  The
 // truncating pass counts targets and stacked-rank overflows of the sketch

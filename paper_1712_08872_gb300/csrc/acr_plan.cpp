@@ -555,6 +555,21 @@ struct Builder {
 
 }  // namespace
 
+namespace {
+// Order every GEMM stage's groups wide (static 64-column outputs) first and
+// record their count, so a launch can give the two kinds different kernels.
+// Groups of one stage write disjoint outputs: their order changes nothing.
+void order_wide_first(Plan& plan) {
+  for (Stage& sg : plan.stages) {
+    if (sg.kind != ST_GEMM) continue;
+    auto wide = [](const GGroup& g) { return g.n_rb < 0 && g.n_st >= 64; };
+    auto mid = std::stable_partition(plan.groups.begin() + sg.beg, plan.groups.begin() + sg.end,
+                                     wide);
+    sg.nwide = (int)(mid - (plan.groups.begin() + sg.beg));
+  }
+}
+}  // namespace
+
 void build_plan(const Structure& S, const OpDesc& op, const PlanParams& pp, Plan& plan) {
   plan = Plan();
   plan.nroles = op.nroles;
@@ -571,6 +586,7 @@ void build_plan(const Structure& S, const OpDesc& op, const PlanParams& pp, Plan
   plan.n_terms = (int)b.terms.size();
   b.phase1();
   b.phase2();
+  order_wide_first(plan);
 }
 
 namespace {
@@ -652,6 +668,7 @@ void merge_plans(const std::vector<const Plan*>& ps, Plan& out) {
       out.stages.push_back(Stage{kind, tb, te, -1});
     }
   }
+  order_wide_first(out);
 }
 
 void MatvecPlan::build(const Structure& S) {

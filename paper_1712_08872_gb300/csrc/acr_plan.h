@@ -105,7 +105,9 @@ inline bool tag_is_dot(int t) {
   return t == TAG_M || t == TAG_S || t == TAG_G || t == TAG_G2 || t == TAG_P || t == TAG_H;
 }
 
-struct Stage { int kind; int beg, end; int tag = -1; };
+// A GEMM stage's groups are ordered with those of a static 64-column output
+// (dense leaf products) first: nwide of them, then the narrow ones.
+struct Stage { int kind; int beg, end; int tag = -1; int nwide = 0; };
 
 // Operand roles: role r owns buffers 3r (dense), 3r+1 (U), 3r+2 (V) and
 // rank buffer r.  The scratch real buffer is 3*nroles, the scratch rank
