@@ -371,11 +371,11 @@ def main():
     tune = None
     table = None
     if not args.no_gemm_autotune:
-        table, ms0, ms1, ms2 = acr.acr_autotune_gemm(n, coef, eps, eta, leaf, acr.ACR_FP32,
-                                                     args.rank_cap, stream)
-        tune = {"table": table[:13], "stage_ms_shape0": [round(v, 1) for v in ms0[:13]],
-                "stage_ms_shape1": [round(v, 1) for v in ms1[:13]],
-                "stage_ms_shape2": [round(v, 1) for v in ms2[:13]]}
+        table, *shape_ms = acr.acr_autotune_gemm(n, coef, eps, eta, leaf, acr.ACR_FP32,
+                                                 args.rank_cap, stream)
+        tune = {"table": table[:13]}
+        for v, ms in enumerate(shape_ms):
+            tune["stage_ms_shape%d" % v] = [round(x, 1) for x in ms[:13]]
 
     def step(prec, flags=0):
         var = table if prec != acr.ACR_FP64 else None

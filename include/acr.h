@@ -81,8 +81,8 @@ typedef struct {
   int32_t rank_cap;      /* 1..48; 0 selects the default (32) */
   int32_t flags;         /* ACR_FLAG_* bits */
   int32_t gemm_variant[16]; /* kernel shape per setup GEMM stage (index = the stage numbering of
-                               acr_profile.stage_ms), 0, 1 or 2 (acr_autotune_gemm); all 0 is
-                               the default shape set; other values read as 0 */
+                               acr_profile.stage_ms), 0..3 (acr_autotune_gemm); all 0 is the
+                               default shape set; other values read as 0 */
 } acr_options;
 
 /* acr_options.flags: record per-kernel-class device time (CUDA events
@@ -208,14 +208,16 @@ acr_status acr_autotune_leaf(const acr_grid* grid, const double* coef, const acr
 
 /* Autotuner of the setup's grouped-GEMM kernel shapes (the paper has no
  * counterpart): one profiled setup of coef with opt per shape (every stage in
- * shape 0, then every stage in shape 1, then in shape 2), then per stage the
- * fastest.  Shape 0: one CTA per group, 4 CTAs per SM; shape 1: for float
- * factors 3 CTAs per SM with more registers (double: half the K-chunk), and
- * the warp- and CTA-per-group inner-product kernels swapped; shape 2 (float
- * factors, non-inner-product stages): one warp per group.  variant_out
- * (host, 16 int32) receives the table to put in acr_options.gemm_variant;
- * stage_ms_out (host, 48 doubles, may be NULL) the measured stage times,
- * shape 0, 1, then 2.  Errors: as acr_setup. */
+ * shape 0, then every stage in shape 1, 2, 3), then per stage the fastest.
+ * Shape 0: one CTA per group, 4 CTAs per SM; shape 1: for float factors 3
+ * CTAs per SM with more registers (double: half the K-chunk), and the warp-
+ * and CTA-per-group inner-product kernels swapped; shape 2 (float factors,
+ * non-inner-product stages): one warp per group, groups with 64-column
+ * outputs on the shape-0 kernel; shape 3: as 2 with those groups on the
+ * tcgen05 tensor cores (split-TF32 operands).  variant_out (host, 16 int32)
+ * receives the table to put in acr_options.gemm_variant; stage_ms_out (host,
+ * 64 doubles, may be NULL) the measured stage times, shape 0, 1, 2, then 3.
+ * Errors: as acr_setup. */
 acr_status acr_autotune_gemm(const acr_grid* grid, const double* coef, const acr_options* opt,
                              int32_t* variant_out, double* stage_ms_out, cudaStream_t stream);
 

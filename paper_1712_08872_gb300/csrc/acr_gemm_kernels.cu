@@ -841,14 +841,20 @@ void launch_ggemm(const Plan& pl, int gbeg, int gend, T* const* d_tab, const int
                   int variant, int* d_err, int nwide) {
   int ng = gend - gbeg;
   if (ng <= 0 || P <= 0) return;
-  if (variant == 2 && nwide > 0 && sizeof(T) == 4 && !tag_is_dot(tag)) {
+  if ((variant == 2 || variant == 3) && nwide > 0 && sizeof(T) == 4 && !tag_is_dot(tag)) {
     // the stage's wide groups (64-column outputs: dense products) in the
-    // staged CTA kernel, the rest one warp per group
+    // staged CTA kernel (shape 2) or on the tensor cores (shape 3), the rest
+    // one warp per group
     const int w = std::min(nwide, ng);
-    launch_ggemm<T>(pl, gbeg, gbeg + w, d_tab, d_rtab, P, d_coefs, st, d_fl, tag, 0, d_err, 0);
+    if (variant == 3 && d_err)
+      launch_ggemm_tc(pl, gbeg, gbeg + w, (float* const*)d_tab, d_rtab, P, d_coefs, st, d_fl,
+                      d_err);
+    else
+      launch_ggemm<T>(pl, gbeg, gbeg + w, d_tab, d_rtab, P, d_coefs, st, d_fl, tag, 0, d_err, 0);
     launch_ggemm<T>(pl, gbeg + w, gend, d_tab, d_rtab, P, d_coefs, st, d_fl, tag, 2, d_err, 0);
     return;
   }
+  if (variant == 3) variant = 2;   // no wide groups: shape 3 is shape 2
   using Acc = T;
   const int maxg = 65535;
   for (int g0 = 0; g0 < ng; g0 += maxg) {
@@ -862,7 +868,8 @@ void launch_ggemm(const Plan& pl, int gbeg, int gend, T* const* d_tab, const int
     // kernels; for float it gives the staged kernel 3 CTAs per SM and 80
     // registers (no spills) instead of 4 CTAs and 64 registers, for double
     // half the staging per K-step.  Variant 2 (float, non-dot stages) runs
-    // one warp per group (k_gwarp).
+    // one warp per group (k_gwarp); variant 3 as 2, with the wide groups on
+    // the tensor cores.
     const bool warp_dot = (tag == TAG_M || (sizeof(T) == 4 && (tag == TAG_S || tag == TAG_P)));
     if (sizeof(T) == 4 && (tag == TAG_G || tag == TAG_G2 || tag == TAG_H)) {
       k_gram_ff<<<grid, NT, 0, st>>>(gr, it, (float* const*)d_tab, d_rtab, P, gbeg + g0, d_fl);

@@ -52,6 +52,12 @@ void launch_ggemm(const Plan& pl, int gbeg, int gend, T* const* d_tab, const int
                   int P, const double* d_coefs, cudaStream_t st, double* d_flops = nullptr,
                   int tag = -1, int variant = 0, int* d_err = nullptr, int nwide = 0);
 
+// The wide (dense-output, up to 64 x 64) groups [gbeg, gend) of a float GEMM
+// stage on the tcgen05 tensor cores (split-TF32 operands, FP32 results).
+void launch_ggemm_tc(const Plan& pl, int gbeg, int gend, float* const* d_tab,
+                     const int* const* d_rtab, int P, const double* d_coefs, cudaStream_t st,
+                     double* d_fl, int* d_err);
+
 // Pivoted-Cholesky orthonormalisation cores (FP64) of plan targets.  The
 // truncating pass counts targets and stacked-rank overflows of the sketch
 // into d_sketch_stat[0..1] (may be null).

@@ -559,7 +559,10 @@ namespace {
 // Order every GEMM stage's groups wide (static 64-column outputs) first and
 // record their count, so a launch can give the two kinds different kernels.
 // Groups of one stage write disjoint outputs: their order changes nothing.
+// Also records the widest sketch of the plan's targets.
 void order_wide_first(Plan& plan) {
+  plan.max_p = 0;
+  for (const TInfo& ti : plan.targets) plan.max_p = std::max(plan.max_p, ti.p);
   for (Stage& sg : plan.stages) {
     if (sg.kind != ST_GEMM) continue;
     auto wide = [](const GGroup& g) { return g.n_rb < 0 && g.n_st >= 64; };

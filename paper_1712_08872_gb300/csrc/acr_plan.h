@@ -132,6 +132,7 @@ struct Plan {
   int nroles = 1;
   int n_lr_targets = 0, n_dense_targets = 0, n_terms = 0;
   int64_t flops_static = 0;   // flops of the static-size GEMM parts (per plane)
+  int32_t max_p = 0;          // widest sketch over the targets (bounds every core's size)
   // device copies (owned by the engine)
   void* d_groups = nullptr;
   void* d_items = nullptr;

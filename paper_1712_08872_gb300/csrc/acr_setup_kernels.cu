@@ -328,7 +328,11 @@ __global__ void __launch_bounds__(NT) k_eig_warp(const TInfo* __restrict__ tis, 
   int* crank = rtab[c_rbuf * P + p];
   if (!scr || !rs || !crank) return;
   const int r = rs[ti.r_ri];
-  if (r <= 0 || r > M) return;   // r == 0: k_eig writes the zero rank
+  if (r <= 0) {   // an empty basis: rank 0
+    if (lane == 0) crank[ti.c_leaf] = 0;
+    return;
+  }
+  if (r > M) return;   // k_eig's cores
   const int ld = ti.p;
   double (*A)[M + 1] = As[warp];
   double (*V)[M + 1] = Vs[warp];
@@ -467,11 +471,7 @@ __global__ void __launch_bounds__(NT) k_eig(const TInfo* __restrict__ tis, int t
   if (!scr || !rs || !crank) return;
   const int r = rs[ti.r_ri];
   const int ld = ti.p;
-  if (r <= 0) {
-    if (threadIdx.x == 0) crank[ti.c_leaf] = 0;
-    return;
-  }
-  if (r <= EIG_WARP_MAX) return;   // k_eig_warp's cores
+  if (r <= EIG_WARP_MAX) return;   // k_eig_warp's cores (and the empty bases)
   extern __shared__ double dsm[];
   double (*A)[CMAX + 1] = reinterpret_cast<double (*)[CMAX + 1]>(dsm);
   double (*V)[CMAX + 1] = reinterpret_cast<double (*)[CMAX + 1]>(dsm + CMAX * (CMAX + 1));
@@ -619,13 +619,14 @@ __global__ void __launch_bounds__(NT) k_eig(const TInfo* __restrict__ tis, int t
 }
 
 // Largest |a| over the block (every thread passes its own candidate).
+template <int TH>
 __device__ __forceinline__ double block_absmax(double v, double* red8) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
   if ((threadIdx.x & 31) == 0) red8[threadIdx.x >> 5] = v;
   __syncthreads();
   double r = red8[0];
-  for (int w = 1; w < NT / 32; ++w) r = fmax(r, red8[w]);
+  for (int w = 1; w < TH / 32; ++w) r = fmax(r, red8[w]);
   __syncthreads();
   return r;
 }
@@ -647,26 +648,28 @@ __host__ __device__ constexpr double leaf_growth_max() { return sizeof(T) == 8 ?
 // interchange folded in -- two barriers per step.  Thread t owns row t % 64
 // and columns t / 64 + 4 m.  The interchanges become one column permutation
 // of the result, applied when it is stored.
-template <typename T>
+// TH threads: thread t owns row t % 64 and columns t / 64 + (TH / 64) m.
+template <typename T, int TH>
 __device__ void leaf_inv_fp64(T* __restrict__ Ap, int n, double (*A)[CMAX + 1], int* err,
                               double* __restrict__ flops) {
-  static_assert(NT == 256 && CMAX == 64, "thread mapping assumes 256 threads and 64 x 64 leaves");
+  static_assert(TH % 64 == 0 && TH <= 1024 && CMAX == 64, "64 x 64 leaves, whole rows of threads");
+  constexpr int CS = TH / 64;
   __shared__ double rowk[CMAX], colk[CMAX], krow[CMAX];
   __shared__ int piv[CMAX];
   __shared__ int cmap[CMAX];
   __shared__ int s_q, s_bad;
   __shared__ double s_pinv;
-  __shared__ double red8[NT / 32];
+  __shared__ double red8[TH / 32];
   const int ti = threadIdx.x & 63, tj = threadIdx.x >> 6;
   double amax = 0.0;
-  for (int j = tj; j < n; j += 4)
+  for (int j = tj; j < n; j += CS)
     if (ti < n) {
       A[ti][j] = (double)Ap[ti + (int64_t)j * n];
       amax = fmax(amax, fabs(A[ti][j]));
     }
   if (threadIdx.x == 0) s_bad = 0;
   __syncthreads();
-  amax = block_absmax(amax, red8);
+  amax = block_absmax<TH>(amax, red8);
   for (int k = 0; k < n; ++k) {
     if (threadIdx.x < 32) {
       const int lane = threadIdx.x;
@@ -701,7 +704,7 @@ __device__ void leaf_inv_fp64(T* __restrict__ Ap, int n, double (*A)[CMAX + 1], 
     const double pinv = s_pinv;
     if (ti < n) {
       const double f = colk[ti];
-      for (int j = tj; j < n; j += 4) {
+      for (int j = tj; j < n; j += CS) {
         if (ti == k) {
           A[ti][j] = rowk[j];
         } else {
@@ -718,12 +721,12 @@ __device__ void leaf_inv_fp64(T* __restrict__ Ap, int n, double (*A)[CMAX + 1], 
   }
   // pivot growth of the computed inverse (a NaN or Inf entry fails too)
   double xmax = 0.0;
-  for (int j = tj; j < n; j += 4)
+  for (int j = tj; j < n; j += CS)
     if (ti < n) {
       const double v = fabs(A[ti][j]);
       xmax = (v <= 1.7976931348623157e308) ? fmax(xmax, v) : INFINITY;   // NaN, Inf -> Inf
     }
-  xmax = block_absmax(xmax, red8);
+  xmax = block_absmax<TH>(xmax, red8);
   if (!(amax * xmax <= leaf_growth_max<T>())) {
     if (threadIdx.x == 0) atomicOr(err, ERR_GROWTH);
     return;
@@ -740,7 +743,7 @@ __device__ void leaf_inv_fp64(T* __restrict__ Ap, int n, double (*A)[CMAX + 1], 
     for (int c = 0; c < n; ++c) cmap[pi_[c]] = c;
   }
   __syncthreads();
-  for (int j = tj; j < n; j += 4)
+  for (int j = tj; j < n; j += CS)
     if (ti < n) Ap[ti + (int64_t)cmap[j] * n] = (T)A[ti][j];
   if (flops && threadIdx.x == 0) atomicAdd(flops, 2.0 * n * n * n);
 }
@@ -751,16 +754,17 @@ __global__ void __launch_bounds__(NT) k_leaf_inv(T* const* __restrict__ dense, i
   T* Ap = dense[blockIdx.x];
   if (!Ap) return;
   __shared__ double A[CMAX][CMAX + 1];
-  leaf_inv_fp64<T>(Ap + off, n, A, err, flops);
+  leaf_inv_fp64<T, NT>(Ap + off, n, A, err, flops);
 }
 
+template <int TH>
 __device__ __forceinline__ float block_absmaxf(float v, float* red8) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
   if ((threadIdx.x & 31) == 0) red8[threadIdx.x >> 5] = v;
   __syncthreads();
   float r = red8[0];
-  for (int w = 1; w < NT / 32; ++w) r = fmaxf(r, red8[w]);
+  for (int w = 1; w < TH / 32; ++w) r = fmaxf(r, red8[w]);
   __syncthreads();
   return r;
 }
@@ -778,11 +782,13 @@ __device__ __forceinline__ float block_absmaxf(float v, float* red8) {
 // leaf is inverted by the FP64 elimination instead (the shared buffers
 // reused), so the pivot and growth diagnostics are those of the FP64 form.
 constexpr int LEAF_F_SMEM = 3 * CMAX * (CMAX + 1) * (int)sizeof(float);
+constexpr int LTH = 512;   // threads of the float leaf inverse: 8 entries each
 
-__global__ void __launch_bounds__(NT) k_leaf_inv_f(float* const* __restrict__ dense, int64_t off,
-                                                   int n, int* err, double* __restrict__ flops,
-                                                   unsigned long long* __restrict__ fallbacks) {
-  static_assert(NT == 256 && CMAX == 64, "thread mapping assumes 256 threads and 64 x 64 leaves");
+__global__ void __launch_bounds__(LTH) k_leaf_inv_f(float* const* __restrict__ dense, int64_t off,
+                                                    int n, int* err, double* __restrict__ flops,
+                                                    unsigned long long* __restrict__ fallbacks) {
+  constexpr int TH = LTH, CS = TH / 64;
+  static_assert(CMAX == 64, "64 x 64 leaves");
   static_assert(2 * CMAX * (CMAX + 1) * sizeof(float) >= CMAX * (CMAX + 1) * sizeof(double),
                 "the FP64 fallback fits the X and R buffers");
   float* Ap = dense[blockIdx.x];
@@ -797,10 +803,10 @@ __global__ void __launch_bounds__(NT) k_leaf_inv_f(float* const* __restrict__ de
   __shared__ int cmap[CMAX];
   __shared__ int s_q, s_bad;
   __shared__ float s_pinv;
-  __shared__ float red8[NT / 32];
+  __shared__ float red8[TH / 32];
   const int ti = threadIdx.x & 63, tj = threadIdx.x >> 6;
   float amax = 0.f;
-  for (int j = tj; j < n; j += 4)
+  for (int j = tj; j < n; j += CS)
     if (ti < n) {
       const float v = Ap[ti + (int64_t)j * n];
       A0[ti][j] = v;
@@ -809,7 +815,7 @@ __global__ void __launch_bounds__(NT) k_leaf_inv_f(float* const* __restrict__ de
     }
   if (threadIdx.x == 0) s_bad = 0;
   __syncthreads();
-  amax = block_absmaxf(amax, red8);
+  amax = block_absmaxf<TH>(amax, red8);
   // 1. Gauss-Jordan in float (the FP64 elimination's steps)
   for (int k = 0; k < n; ++k) {
     if (threadIdx.x < 32) {
@@ -844,7 +850,7 @@ __global__ void __launch_bounds__(NT) k_leaf_inv_f(float* const* __restrict__ de
     const float pinv = s_pinv;
     if (ti < n) {
       const float f = colk[ti];
-      for (int j = tj; j < n; j += 4) {
+      for (int j = tj; j < n; j += CS) {
         if (ti == k) {
           X[ti][j] = rowk[j];
         } else {
@@ -869,7 +875,7 @@ __global__ void __launch_bounds__(NT) k_leaf_inv_f(float* const* __restrict__ de
     }
     __syncthreads();
     // the inverse in natural column order, into R; then the buffers trade roles
-    for (int j = tj; j < n; j += 4)
+    for (int j = tj; j < n; j += CS)
       if (ti < n) R[ti][cmap[j]] = X[ti][j];
     __syncthreads();
     float (*tmp)[CMAX + 1] = X; X = R; R = tmp;
@@ -880,18 +886,18 @@ __global__ void __launch_bounds__(NT) k_leaf_inv_f(float* const* __restrict__ de
       ++steps;
       // R = I - A0 X from exact products and compensated sums
       if (ti < n)
-        for (int j = tj; j < n; j += 4) {
+        for (int j = tj; j < n; j += CS) {
           float sh = 0.f, sl = 0.f;
           for (int l = 0; l < n; ++l) ff_fma(sh, sl, A0[ti][l], X[l][j]);
           R[ti][j] = ((ti == j ? 1.f : 0.f) - sh) - sl;
         }
       __syncthreads();
       // correction D = X R; X += D
-      float d[CMAX / 4];
+      float d[CMAX / CS];
       float dmax = 0.f;
 #pragma unroll
-      for (int q = 0; q < CMAX / 4; ++q) {
-        const int j = tj + 4 * q;
+      for (int q = 0; q < CMAX / CS; ++q) {
+        const int j = tj + CS * q;
         float v = 0.f;
         if (ti < n && j < n)
           for (int l = 0; l < n; ++l) v = fmaf(X[ti][l], R[l][j], v);
@@ -901,16 +907,16 @@ __global__ void __launch_bounds__(NT) k_leaf_inv_f(float* const* __restrict__ de
       __syncthreads();   // every read of X is done
       float xmax = 0.f;
 #pragma unroll
-      for (int q = 0; q < CMAX / 4; ++q) {
-        const int j = tj + 4 * q;
+      for (int q = 0; q < CMAX / CS; ++q) {
+        const int j = tj + CS * q;
         if (ti < n && j < n) {
           X[ti][j] += d[q];
           const float v = fabsf(X[ti][j]);
           xmax = (v <= 3.0e38f) ? fmaxf(xmax, v) : INFINITY;
         }
       }
-      dmax = block_absmaxf(dmax, red8);
-      xmax = block_absmaxf(xmax, red8);
+      dmax = block_absmaxf<TH>(dmax, red8);
+      xmax = block_absmaxf<TH>(xmax, red8);
       if (!(xmax <= 3.0e38f) || !(dmax <= 3.0e38f)) fallback = true;   // non-finite
       else if (dmax <= 2.4e-7f * xmax) done = true;
       else if (dmax > 0.5f * dprev) fallback = true;                    // not contracting
@@ -919,14 +925,14 @@ __global__ void __launch_bounds__(NT) k_leaf_inv_f(float* const* __restrict__ de
     if (!done) fallback = true;
     if (!fallback) {
       float xmax = 0.f;
-      for (int j = tj; j < n; j += 4)
+      for (int j = tj; j < n; j += CS)
         if (ti < n) xmax = fmaxf(xmax, fabsf(X[ti][j]));
-      xmax = block_absmaxf(xmax, red8);
+      xmax = block_absmaxf<TH>(xmax, red8);
       if (!((double)amax * (double)xmax <= leaf_growth_max<float>())) {
         if (threadIdx.x == 0) atomicOr(err, ERR_GROWTH);
         return;
       }
-      for (int j = tj; j < n; j += 4)
+      for (int j = tj; j < n; j += CS)
         if (ti < n) Ap[ti + (int64_t)j * n] = X[ti][j];
       if (flops && threadIdx.x == 0) atomicAdd(flops, 2.0 * n * n * n * (1 + 2 * steps));
       return;
@@ -936,7 +942,7 @@ __global__ void __launch_bounds__(NT) k_leaf_inv_f(float* const* __restrict__ de
   // R buffers (contiguous: X and R may have traded roles, the pair has not)
   __syncthreads();
   if (fallbacks && threadIdx.x == 0) atomicAdd(fallbacks, 1ull);
-  leaf_inv_fp64<float>(Ap, n, reinterpret_cast<double (*)[CMAX + 1]>(lsm + CMAX * (CMAX + 1)),
+  leaf_inv_fp64<float, TH>(Ap, n, reinterpret_cast<double (*)[CMAX + 1]>(lsm + CMAX * (CMAX + 1)),
                        err, flops);
 }
 
@@ -1066,6 +1072,9 @@ void launch_pchol(const Plan& pl, int tbeg, int tend, bool truncate, double tau,
         3 * pl.nroles, pl.nroles, (const StackDim*)pl.d_stack, d_sketch_stat, d_fl);
     ACR_LAUNCHED(1);
   }
+  // Grams wider than a warp's (none when every sketch is at most 32 wide:
+  // the second pass's basis is never wider than its sketch)
+  if (pl.max_p <= PCHOL_WARP_MAX) return;
   for (int t0 = 0; t0 < nt; t0 += 65535) {
     dim3 grid(std::min(65535, nt - t0), P);
     k_pchol<T><<<grid, NT, smem, st>>>((const TInfo*)pl.d_targets, tbeg + t0, truncate, tau, d_tab,
@@ -1094,6 +1103,9 @@ void launch_eig(const Plan& pl, int tbeg, int tend, double eps, int kc, int c_ro
       ACR_LAUNCHED(1);
     }
   }
+  // cores wider than a warp's (none when every sketch is at most that wide:
+  // a core is never wider than its basis, nor the basis than its sketch)
+  if (pl.max_p <= EIG_WARP_MAX) return;
   for (int t0 = 0; t0 < nt; t0 += 65535) {
     dim3 grid(std::min(65535, nt - t0), P);
     k_eig<T><<<grid, NT, smem, st>>>((const TInfo*)pl.d_targets, tbeg + t0, eps, kc, c_role, d_tab,
@@ -1113,7 +1125,7 @@ void launch_leaf_inv(T* const* d_dense, int64_t off, int lsz, int P, int* d_err,
                                     LEAF_F_SMEM));
       attr = true;
     }
-    k_leaf_inv_f<<<P, NT, LEAF_F_SMEM, st>>>(d_dense, off, lsz, d_err, d_fl, d_fallbacks);
+    k_leaf_inv_f<<<P, LTH, LEAF_F_SMEM, st>>>(d_dense, off, lsz, d_err, d_fl, d_fallbacks);
   } else {
     k_leaf_inv<T><<<P, NT, 0, st>>>(d_dense, off, lsz, d_err, d_fl);
   }
