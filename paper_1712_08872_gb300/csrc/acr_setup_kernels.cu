@@ -122,12 +122,13 @@ __global__ void __launch_bounds__(32 * PW) k_pchol_warp(
     __syncwarp();
     if (lane == 0) { const int tt = piv[j]; piv[j] = piv[q]; piv[q] = tt; }
     __syncwarp();
+    const double rjj = 1.0 / ljj;   // one division per column (FP64 division is slow here)
     if (lane >= j && lane < pd) {
       const int i = lane;
       const int src = (i == j) ? q : (i == q ? j : i);
       double sum = L[piv[i]][piv[j]];
       for (int l = 0; l < j; ++l) sum -= F[src][l] * F[q][l];
-      colbuf[i] = (i == j) ? ljj : sum / ljj;
+      colbuf[i] = (i == j) ? ljj : sum * rjj;
     }
     __syncwarp();
     if (q != j && lane < j) {
@@ -143,13 +144,16 @@ __global__ void __launch_bounds__(32 * PW) k_pchol_warp(
     r = j + 1;
   }
   __syncwarp();
-  // inverse of the r x r lower factor, column c by lane c, into L
+  // inverse of the r x r lower factor, column c by lane c, into L (the
+  // diagonal's reciprocals taken once, by lane i for row i)
+  if (lane < r) d[lane] = (F[lane][lane] != 0.0) ? 1.0 / F[lane][lane] : 0.0;
+  __syncwarp();
   if (lane < r) {
     const int c = lane;
     for (int i = 0; i < r; ++i) {
       double sacc = (i == c) ? 1.0 : 0.0;
       for (int l = c; l < i; ++l) sacc -= F[i][l] * L[l][c];
-      L[i][c] = (F[i][i] != 0.0 && i >= c) ? sacc / F[i][i] : 0.0;
+      L[i][c] = (i >= c) ? sacc * d[i] : 0.0;
     }
   }
   __syncwarp();
@@ -453,6 +457,208 @@ __global__ void __launch_bounds__(NT) k_eig_warp(const TInfo* __restrict__ tis, 
   for (int e = lane; e < r * k; e += 32) {
     const int i = e % r, j = e / r;
     W[i + (int64_t)j * ld] = (T)V[i][order[j]];
+  }
+}
+
+// Float-float numbers (an unevaluated sum hi + lo of two floats, ~48
+// significant bits): the products and sums of the float form's small
+// Jacobi cores, on the FP32 pipe instead of this part's narrow FP64 pipe.
+struct FF {
+  float h, l;
+};
+__device__ __forceinline__ FF ff_of(double x) {
+  const float h = (float)x;
+  return FF{h, (float)(x - (double)h)};
+}
+__device__ __forceinline__ double ff_dbl(FF a) { return (double)a.h + (double)a.l; }
+// a * b: exact product of the high parts plus the cross terms, renormalised
+__device__ __forceinline__ FF ff_mul(FF a, FF b) {
+  const float p = a.h * b.h;
+  float e = fmaf(a.h, b.h, -p);
+  e = fmaf(a.h, b.l, e);
+  e = fmaf(a.l, b.h, e);
+  const float s = p + e;
+  return FF{s, e - (s - p)};
+}
+// a + b: TwoSum of the high parts, low parts added, renormalised
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+  const float s = a.h + b.h;
+  const float bp = s - a.h;
+  float e = (a.h - (s - bp)) + (b.h - bp);
+  e += a.l + b.l;
+  const float r = s + e;
+  return FF{r, e - (r - s)};
+}
+__device__ __forceinline__ FF ff_neg(FF a) { return FF{-a.h, -a.l}; }
+// (1 + t^2)^(-1/2) to float-float accuracy: one Newton step y + y (1 - x y^2) / 2
+// from the float estimate
+__device__ __forceinline__ FF ff_rsqrt1p(float t) {
+  const float p = t * t;
+  const FF x = ff_add(FF{1.f, 0.f}, FF{p, fmaf(t, t, -p)});
+  const float y = rsqrtf(x.h);
+  const FF xy2 = ff_mul(x, ff_mul(FF{y, 0.f}, FF{y, 0.f}));
+  const FF e = ff_add(FF{1.f, 0.f}, ff_neg(xy2));
+  return ff_add(FF{y, 0.f}, ff_mul(FF{y, 0.f}, FF{0.5f * e.h, 0.5f * e.l}));
+}
+
+// k_eig_warp for float factors: the same rotation sequence, stopping rule
+// and rank selection, with the core and the accumulated eigenvectors held
+// and rotated in float-float (~1e-14 relative, far below what the float
+// factors keep).  Each rotation's angle is taken in float (an angle off by
+// ~1e-7 leaves ~1e-7 of the entry it should zero, which later rotations
+// remove), and its cosine and sine to float-float accuracy from that angle,
+// so that every rotation is orthogonal to ~1e-14 and no FP64 operation
+// remains in the sweep.
+__global__ void __launch_bounds__(NT) k_eig_warp_ff(const TInfo* __restrict__ tis, int tbase,
+                                                    int tend, double eps, int kc, int c_rbuf,
+                                                    float* const* __restrict__ tab,
+                                                    int* const* __restrict__ rtab, int P,
+                                                    int scr_buf, int scr_rbuf, int* err,
+                                                    double* __restrict__ flops) {
+  constexpr int M = EIG_WARP_MAX;
+  const int p = blockIdx.y;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int t = tbase + blockIdx.x * (NT / 32) + warp;
+  __shared__ FF As[NT / 32][M][M + 1], Vs[NT / 32][M][M + 1];
+  __shared__ FF css[NT / 32][M / 2], sns[NT / 32][M / 2];
+  __shared__ double lams[NT / 32][M];
+  __shared__ int pps[NT / 32][M / 2], qqs[NT / 32][M / 2], ords[NT / 32][M];
+  if (t >= tend) return;
+  const TInfo ti = tis[t];
+  float* scr = tab[scr_buf * P + p];
+  int* rs = rtab[scr_rbuf * P + p];
+  int* crank = rtab[c_rbuf * P + p];
+  if (!scr || !rs || !crank) return;
+  const int r = rs[ti.r_ri];
+  if (r <= 0) {   // an empty basis: rank 0
+    if (lane == 0) crank[ti.c_leaf] = 0;
+    return;
+  }
+  if (r > M) return;   // k_eig's cores
+  const int ld = ti.p;
+  FF (*A)[M + 1] = As[warp];
+  FF (*V)[M + 1] = Vs[warp];
+  FF* cs = css[warp];
+  FF* sn = sns[warp];
+  int* pp = pps[warp];
+  int* qq = qqs[warp];
+  const double* H = reinterpret_cast<const double*>(scr + ti.h_off);
+  float* W = scr + ti.w_off;
+  for (int e = lane; e < r * r; e += 32) {
+    const int i = e % r, j = e / r;
+    A[i][j] = ff_of(0.5 * (H[i + (int64_t)j * ld] + H[j + (int64_t)i * ld]));
+    V[i][j] = FF{(i == j) ? 1.f : 0.f, 0.f};
+  }
+  __syncwarp();
+  const int nn = (r + 1) & ~1;
+  const int npair = nn / 2;
+  int sweeps_done = 0;
+  const double conv = 1e-16;
+  for (int sweep = 0; sweep < 40; ++sweep) {
+    double off = 0, tot = 0;
+    for (int e = lane; e < r * r; e += 32) {
+      const int i = e % r, j = e / r;
+      const double a = ff_dbl(A[i][j]);
+      const double v = a * a;
+      tot += v;
+      if (i != j) off += v;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      off += __shfl_xor_sync(0xffffffffu, off, o);
+      tot += __shfl_xor_sync(0xffffffffu, tot, o);
+    }
+    if (off <= conv * tot || r == 1) break;
+    ++sweeps_done;
+    for (int round = 0; round < nn - 1; ++round) {
+      if (lane < npair) {
+        const int k = lane;
+        const int pa = k, pb = nn - 1 - k;
+        const int a = (pa == 0) ? 0 : 1 + ((pa - 1 + round) % (nn - 1));
+        const int b = 1 + ((pb - 1 + round) % (nn - 1));
+        const int lo = a < b ? a : b, hi = a < b ? b : a;
+        pp[k] = lo; qq[k] = hi;
+        FF c{1.f, 0.f}, sv{0.f, 0.f};
+        if (hi < r) {
+          const float apq = A[lo][hi].h;
+          if (apq != 0.f) {
+            const float tau_ = (A[hi][hi].h - A[lo][lo].h) / (2.f * apq);
+            const float tt = (tau_ >= 0.f ? 1.f : -1.f) / (fabsf(tau_) + sqrtf(1.f + tau_ * tau_));
+            c = ff_rsqrt1p(tt);
+            sv = ff_mul(FF{tt, 0.f}, c);
+          }
+        }
+        cs[k] = c; sn[k] = sv;
+      }
+      __syncwarp();
+      const int nblk = npair * npair;
+      for (int e = lane; e < nblk + npair * r; e += 32) {
+        if (e < nblk) {
+          const int k1 = e / npair, k2 = e - k1 * npair;
+          const int a1 = pp[k1], b1 = qq[k1], a2 = pp[k2], b2 = qq[k2];
+          const bool h1 = b1 < r, h2 = b2 < r;
+          const FF c1 = cs[k1], s1 = sn[k1], c2 = cs[k2], s2 = sn[k2];
+          const FF z{0.f, 0.f};
+          const FF x00 = A[a1][a2];
+          const FF x01 = h2 ? A[a1][b2] : z;
+          const FF x10 = h1 ? A[b1][a2] : z;
+          const FF x11 = (h1 && h2) ? A[b1][b2] : z;
+          const FF y00 = ff_add(ff_mul(c2, x00), ff_neg(ff_mul(s2, x01)));
+          const FF y01 = ff_add(ff_mul(s2, x00), ff_mul(c2, x01));
+          const FF y10 = ff_add(ff_mul(c2, x10), ff_neg(ff_mul(s2, x11)));
+          const FF y11 = ff_add(ff_mul(s2, x10), ff_mul(c2, x11));
+          A[a1][a2] = ff_add(ff_mul(c1, y00), ff_neg(ff_mul(s1, y10)));
+          if (h2) A[a1][b2] = ff_add(ff_mul(c1, y01), ff_neg(ff_mul(s1, y11)));
+          if (h1) A[b1][a2] = ff_add(ff_mul(s1, y00), ff_mul(c1, y10));
+          if (h1 && h2) A[b1][b2] = ff_add(ff_mul(s1, y01), ff_mul(c1, y11));
+        } else {
+          const int f = e - nblk;
+          const int k = f / r, iv = f - k * r;
+          const int a = pp[k], b = qq[k];
+          if (b < r) {
+            const FF c = cs[k], sv = sn[k];
+            const FF vx = V[iv][a], vy = V[iv][b];
+            V[iv][a] = ff_add(ff_mul(c, vx), ff_neg(ff_mul(sv, vy)));
+            V[iv][b] = ff_add(ff_mul(sv, vx), ff_mul(c, vy));
+          }
+        }
+      }
+      __syncwarp();
+    }
+  }
+  double* lam = lams[warp];
+  int* order = ords[warp];
+  if (lane < r) lam[lane] = ff_dbl(A[lane][lane]);
+  __syncwarp();
+  if (lane < r) {
+    int pos = 0;
+    for (int j = 0; j < r; ++j)
+      if (lam[j] > lam[lane] || (lam[j] == lam[lane] && j < lane)) ++pos;
+    order[pos] = lane;
+  }
+  __syncwarp();
+  int k = 0;
+  if (lane == 0) {
+    const double l1 = lam[order[0]];
+    if (l1 > 0.0) {
+      const double s1 = sqrt(l1);
+      for (int j = 0; j < r; ++j) {
+        const double lj = lam[order[j]];
+        if (lj > 0.0 && sqrt(lj) > eps * s1) ++k;
+        else break;
+      }
+    }
+    if (k > kc) {
+      atomicOr(err, ERR_RANKCAP);
+      k = kc;
+    }
+    crank[ti.c_leaf] = k;
+    if (flops) atomicAdd(flops, 9.0 * r * r * r * sweeps_done);
+  }
+  k = __shfl_sync(0xffffffffu, k, 0);
+  for (int e = lane; e < r * k; e += 32) {
+    const int i = e % r, j = e / r;
+    W[i + (int64_t)j * ld] = (float)ff_dbl(V[i][order[j]]);
   }
 }
 
@@ -1097,9 +1303,14 @@ void launch_eig(const Plan& pl, int tbeg, int tend, double eps, int kc, int c_ro
     for (int t0 = 0; t0 < nt; t0 += 65535 * per) {
       const int cnt = std::min(65535 * per, nt - t0);
       dim3 grid((cnt + per - 1) / per, P);
-      k_eig_warp<T><<<grid, NT, 0, st>>>((const TInfo*)pl.d_targets, tbeg + t0, tbeg + t0 + cnt,
-                                         eps, kc, c_role, d_tab, d_rtab, P, 3 * pl.nroles,
-                                         pl.nroles, d_err, d_fl);
+      if constexpr (std::is_same<T, float>::value)
+        k_eig_warp_ff<<<grid, NT, 0, st>>>((const TInfo*)pl.d_targets, tbeg + t0, tbeg + t0 + cnt,
+                                           eps, kc, c_role, d_tab, d_rtab, P, 3 * pl.nroles,
+                                           pl.nroles, d_err, d_fl);
+      else
+        k_eig_warp<T><<<grid, NT, 0, st>>>((const TInfo*)pl.d_targets, tbeg + t0, tbeg + t0 + cnt,
+                                           eps, kc, c_role, d_tab, d_rtab, P, 3 * pl.nroles,
+                                           pl.nroles, d_err, d_fl);
       ACR_LAUNCHED(1);
     }
   }
