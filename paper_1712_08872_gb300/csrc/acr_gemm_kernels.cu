@@ -353,88 +353,118 @@ __device__ __forceinline__ void gwarp_panel(const GGroup& G, const GItem* __rest
     float acc0[NB], acc1[NB];
 #pragma unroll
     for (int j = 0; j < NB; ++j) { acc0[j] = 0.f; acc1[j] = 0.f; }
-    for (int it = G.ib; it < G.ie; ++it) {
-      const GItem I = items[it];
-      if (I.guard0 >= 0 && !tab[I.guard0 * P + p]) continue;
-      if (I.guard1 >= 0 && !tab[I.guard1 * P + p]) continue;
-      const float* A = nullptr;
-      const float* B = nullptr;
-      if (I.abuf >= 0) { A = tab[I.abuf * P + p]; if (!A) continue; A += I.aoff; }
-      if (I.bbuf >= 0) { B = tab[I.bbuf * P + p]; if (!B) continue; B += I.boff; }
-      const int k = dimv(I.k_st, I.k_rb, I.k_ri, rtab, P, p);
-      const int rows = dimv(I.r_st, I.r_rb, I.r_ri, rtab, P, p);
-      if (k <= 0 || rows <= 0) continue;
-      const float cf = (float)coefs[I.coef];
-      const int i0 = lane - I.row_off, i1 = lane + 32 - I.row_off;
-      const bool v0 = i0 >= 0 && i0 < rows, v1 = i1 >= 0 && i1 < rows;
-      if ((I.aflags & FL_IDENT) || (I.bflags & FL_IDENT)) {
-        // C(row_off + i, j) += cf * B(i, j)  or  cf * A(i, j)
-        fl += (long long)rows * nb;
-        const float* src = (I.aflags & FL_IDENT) ? B : A;
-        const int ld = (I.aflags & FL_IDENT) ? I.ldb : I.lda;
-#pragma unroll
-        for (int j = 0; j < NB; ++j) {
-          if (j < nb) {
-            if (v0) acc0[j] += cf * src[i0 + (int64_t)(j0 + j) * ld];
-            if (v1) acc1[j] += cf * src[i1 + (int64_t)(j0 + j) * ld];
-          }
+    for (int base = G.ib; base < G.ie; base += 32) {
+      // lane q resolves item base + q: every item's chain of dependent loads
+      // (descriptor, operand pointers, ranks, coefficient) in flight at once
+      const float* rA = nullptr;
+      const float* rB = nullptr;
+      int rk = 0, rrows = 0, rflags = 0, rr0 = 0, rlda = 0, rldb = 0, rseed = 0, rorow = 0;
+      float rcf = 0.f;
+      if (base + lane < G.ie) {
+        const GItem I = items[base + lane];
+        bool ok = !(I.guard0 >= 0 && !tab[I.guard0 * P + p]) &&
+                  !(I.guard1 >= 0 && !tab[I.guard1 * P + p]);
+        if (ok && I.abuf >= 0) { rA = tab[I.abuf * P + p]; ok = rA != nullptr; if (ok) rA += I.aoff; }
+        if (ok && I.bbuf >= 0) { rB = tab[I.bbuf * P + p]; ok = rB != nullptr; if (ok) rB += I.boff; }
+        if (ok) {
+          rk = dimv(I.k_st, I.k_rb, I.k_ri, rtab, P, p);
+          rrows = dimv(I.r_st, I.r_rb, I.r_ri, rtab, P, p);
+          rcf = (float)coefs[I.coef];
+          rflags = ((I.aflags & FL_IDENT) ? 1 : 0) | ((I.bflags & FL_IDENT) ? 2 : 0) |
+                   ((I.aflags & FL_T) ? 4 : 0) | ((I.bflags & FL_T) ? 8 : 0) |
+                   ((I.bflags & FL_OMEGA) ? 16 : 0);
+          rr0 = I.row_off; rlda = I.lda; rldb = I.ldb; rseed = I.seed; rorow = I.omega_row0;
+        } else {
+          rk = 0;
         }
-        continue;
       }
-      fl += 2LL * rows * nb * k;
-      const bool at = I.aflags & FL_T, bt = I.bflags & FL_T, bo = I.bflags & FL_OMEGA;
-      // A(i, l): A[i + l lda] (plain) or A[l + i lda] (transposed)
-      const int astep = at ? 1 : I.lda;
-      const float* a0 = A + (v0 ? (at ? (int64_t)i0 * I.lda : i0) : 0);
-      const float* a1 = A + (v1 ? (at ? (int64_t)i1 * I.lda : i1) : 0);
-      for (int k0 = 0; k0 < k; k0 += KCH) {
-        const int kt = min(KCH, k - k0);
-        __syncwarp();
-        for (int e = lane; e < kt * NB; e += 32) {
-          const int kk = e / NB, j = e % NB;
-          float v = 0.f;
-          if (j < nb) {
-            const int l = k0 + kk, jj = j0 + j;
-            v = bo ? omega((uint32_t)I.seed, (uint32_t)(I.omega_row0 + l), (uint32_t)jj)
-                   : (bt ? B[jj + (int64_t)l * I.ldb] : B[l + (int64_t)jj * I.ldb]);
-          }
-          Bs[kk * LDB + j] = cf * v;
-        }
-        __syncwarp();
-        // A pointers at this chunk (offsets within a 64-row leaf panel
-        // stay far inside 32 bits: K-chunks of at most 32 columns)
-        const float* p0 = a0 + (int64_t)k0 * astep;
-        const float* p1 = a1 + (int64_t)k0 * astep;
-        int kk = 0;
-        for (; kk + 4 <= kt; kk += 4) {
-          float x0[4], x1[4];
+      const int cnt = min(32, G.ie - base);
+      for (int q = 0; q < cnt; ++q) {
+        const int k = __shfl_sync(0xffffffffu, rk, q);
+        const int rows = __shfl_sync(0xffffffffu, rrows, q);
+        if (k <= 0 || rows <= 0) continue;
+        const float* A = reinterpret_cast<const float*>(
+            __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(rA), q));
+        const float* B = reinterpret_cast<const float*>(
+            __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(rB), q));
+        const float cf = __shfl_sync(0xffffffffu, rcf, q);
+        const int flags = __shfl_sync(0xffffffffu, rflags, q);
+        const int row_off = __shfl_sync(0xffffffffu, rr0, q);
+        const int lda = __shfl_sync(0xffffffffu, rlda, q);
+        const int ldb = __shfl_sync(0xffffffffu, rldb, q);
+        const int seed = __shfl_sync(0xffffffffu, rseed, q);
+        const int orow0 = __shfl_sync(0xffffffffu, rorow, q);
+        const int i0 = lane - row_off, i1 = lane + 32 - row_off;
+        const bool v0 = i0 >= 0 && i0 < rows, v1 = i1 >= 0 && i1 < rows;
+        if (flags & 3) {
+          // C(row_off + i, j) += cf * B(i, j)  or  cf * A(i, j)
+          fl += (long long)rows * nb;
+          const float* src = (flags & 1) ? B : A;
+          const int ld = (flags & 1) ? ldb : lda;
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            x0[u] = v0 ? p0[(kk + u) * astep] : 0.f;
-            x1[u] = v1 ? p1[(kk + u) * astep] : 0.f;
-          }
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-#pragma unroll
-            for (int q = 0; q < NB / 4; ++q) {
-              const float4 b = *reinterpret_cast<const float4*>(Bs + (kk + u) * LDB + 4 * q);
-              acc0[4 * q] += x0[u] * b.x; acc0[4 * q + 1] += x0[u] * b.y;
-              acc0[4 * q + 2] += x0[u] * b.z; acc0[4 * q + 3] += x0[u] * b.w;
-              acc1[4 * q] += x1[u] * b.x; acc1[4 * q + 1] += x1[u] * b.y;
-              acc1[4 * q + 2] += x1[u] * b.z; acc1[4 * q + 3] += x1[u] * b.w;
+          for (int j = 0; j < NB; ++j) {
+            if (j < nb) {
+              if (v0) acc0[j] += cf * src[i0 + (int64_t)(j0 + j) * ld];
+              if (v1) acc1[j] += cf * src[i1 + (int64_t)(j0 + j) * ld];
             }
           }
+          continue;
         }
-        for (; kk < kt; ++kk) {
-          const float y0 = v0 ? p0[kk * astep] : 0.f;
-          const float y1 = v1 ? p1[kk * astep] : 0.f;
+        fl += 2LL * rows * nb * k;
+        const bool at = flags & 4, bt = flags & 8, bo = flags & 16;
+        // A(i, l): A[i + l lda] (plain) or A[l + i lda] (transposed)
+        const int astep = at ? 1 : lda;
+        const float* a0 = A + (v0 ? (at ? (int64_t)i0 * lda : i0) : 0);
+        const float* a1 = A + (v1 ? (at ? (int64_t)i1 * lda : i1) : 0);
+        for (int k0 = 0; k0 < k; k0 += KCH) {
+          const int kt = min(KCH, k - k0);
+          __syncwarp();
+          for (int e = lane; e < kt * NB; e += 32) {
+            const int kk = e / NB, j = e % NB;
+            float v = 0.f;
+            if (j < nb) {
+              const int l = k0 + kk, jj = j0 + j;
+              v = bo ? omega((uint32_t)seed, (uint32_t)(orow0 + l), (uint32_t)jj)
+                     : (bt ? B[jj + (int64_t)l * ldb] : B[l + (int64_t)jj * ldb]);
+            }
+            Bs[kk * LDB + j] = cf * v;
+          }
+          __syncwarp();
+          // A pointers at this chunk (offsets within a 64-row leaf panel
+          // stay far inside 32 bits: K-chunks of at most 32 columns)
+          const float* p0 = a0 + (int64_t)k0 * astep;
+          const float* p1 = a1 + (int64_t)k0 * astep;
+          int kk = 0;
+          for (; kk + 4 <= kt; kk += 4) {
+            float x0[4], x1[4];
 #pragma unroll
-          for (int q = 0; q < NB / 4; ++q) {
-            const float4 b = *reinterpret_cast<const float4*>(Bs + kk * LDB + 4 * q);
-            acc0[4 * q] += y0 * b.x; acc0[4 * q + 1] += y0 * b.y;
-            acc0[4 * q + 2] += y0 * b.z; acc0[4 * q + 3] += y0 * b.w;
-            acc1[4 * q] += y1 * b.x; acc1[4 * q + 1] += y1 * b.y;
-            acc1[4 * q + 2] += y1 * b.z; acc1[4 * q + 3] += y1 * b.w;
+            for (int u = 0; u < 4; ++u) {
+              x0[u] = v0 ? p0[(kk + u) * astep] : 0.f;
+              x1[u] = v1 ? p1[(kk + u) * astep] : 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+#pragma unroll
+              for (int q = 0; q < NB / 4; ++q) {
+                const float4 b = *reinterpret_cast<const float4*>(Bs + (kk + u) * LDB + 4 * q);
+                acc0[4 * q] += x0[u] * b.x; acc0[4 * q + 1] += x0[u] * b.y;
+                acc0[4 * q + 2] += x0[u] * b.z; acc0[4 * q + 3] += x0[u] * b.w;
+                acc1[4 * q] += x1[u] * b.x; acc1[4 * q + 1] += x1[u] * b.y;
+                acc1[4 * q + 2] += x1[u] * b.z; acc1[4 * q + 3] += x1[u] * b.w;
+              }
+            }
+          }
+          for (; kk < kt; ++kk) {
+            const float y0 = v0 ? p0[kk * astep] : 0.f;
+            const float y1 = v1 ? p1[kk * astep] : 0.f;
+#pragma unroll
+            for (int q = 0; q < NB / 4; ++q) {
+              const float4 b = *reinterpret_cast<const float4*>(Bs + kk * LDB + 4 * q);
+              acc0[4 * q] += y0 * b.x; acc0[4 * q + 1] += y0 * b.y;
+              acc0[4 * q + 2] += y0 * b.z; acc0[4 * q + 3] += y0 * b.w;
+              acc1[4 * q] += y1 * b.x; acc1[4 * q + 1] += y1 * b.y;
+              acc1[4 * q + 2] += y1 * b.z; acc1[4 * q + 3] += y1 * b.w;
+            }
           }
         }
       }

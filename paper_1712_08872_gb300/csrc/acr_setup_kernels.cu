@@ -2,8 +2,9 @@
 // acr_gemm_kernels.cu:
 //  * k_pchol   -- FP64 pivoted Cholesky of a sketch Gram: orthonormal basis
 //                 transform of the range finder;
-//  * k_eig     -- FP64 cyclic Jacobi of the small recompression core, rank
-//                 selection sigma_i > eps * sigma_1 (Sec. 4.3 H_eps);
+//  * k_eig     -- cyclic Jacobi of the small recompression core (FP64; for
+//                 float factors float-float), rank selection
+//                 sigma_i > eps * sigma_1 (Sec. 4.3 H_eps);
 //  * k_leaf_inv-- Gauss-Jordan inverse with partial pivoting of a dense
 //                 diagonal leaf (the leaves of the recursive H-inverse): FP64,
 //                 or for float storage float elimination refined to float
@@ -305,161 +306,6 @@ __global__ void __launch_bounds__(NT) k_pchol(const TInfo* __restrict__ tis, int
   }
 }
 
-constexpr int EIG_WARP_MAX = 16;   // cores up to this size: one warp each
-
-// The same cyclic Jacobi for small cores (1 < r <= 16), one warp per target,
-// eight targets per CTA: the rotations of a round are computed and applied
-// by the warp's lanes with warp barriers only (same rotation sequence and
-// stopping rule as k_eig).
-template <typename T>
-__global__ void __launch_bounds__(NT) k_eig_warp(const TInfo* __restrict__ tis, int tbase,
-                                                 int tend, double eps, int kc, int c_rbuf,
-                                                 T* const* __restrict__ tab,
-                                                 int* const* __restrict__ rtab, int P,
-                                                 int scr_buf, int scr_rbuf, int* err,
-                                                 double* __restrict__ flops) {
-  constexpr int M = EIG_WARP_MAX;
-  const int p = blockIdx.y;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int t = tbase + blockIdx.x * (NT / 32) + warp;
-  __shared__ double As[NT / 32][M][M + 1], Vs[NT / 32][M][M + 1];
-  __shared__ double css[NT / 32][M / 2], sns[NT / 32][M / 2], lams[NT / 32][M];
-  __shared__ int pps[NT / 32][M / 2], qqs[NT / 32][M / 2], ords[NT / 32][M];
-  if (t >= tend) return;
-  const TInfo ti = tis[t];
-  T* scr = tab[scr_buf * P + p];
-  int* rs = rtab[scr_rbuf * P + p];
-  int* crank = rtab[c_rbuf * P + p];
-  if (!scr || !rs || !crank) return;
-  const int r = rs[ti.r_ri];
-  if (r <= 0) {   // an empty basis: rank 0
-    if (lane == 0) crank[ti.c_leaf] = 0;
-    return;
-  }
-  if (r > M) return;   // k_eig's cores
-  const int ld = ti.p;
-  double (*A)[M + 1] = As[warp];
-  double (*V)[M + 1] = Vs[warp];
-  double* cs = css[warp];
-  double* sn = sns[warp];
-  int* pp = pps[warp];
-  int* qq = qqs[warp];
-  const double* H = reinterpret_cast<const double*>(scr + ti.h_off);
-  T* W = scr + ti.w_off;
-  for (int e = lane; e < r * r; e += 32) {
-    const int i = e % r, j = e / r;
-    A[i][j] = 0.5 * (H[i + (int64_t)j * ld] + H[j + (int64_t)i * ld]);
-    V[i][j] = (i == j) ? 1.0 : 0.0;
-  }
-  __syncwarp();
-  const int nn = (r + 1) & ~1;
-  const int npair = nn / 2;
-  int sweeps_done = 0;
-  const double conv = sizeof(T) == 8 ? 1e-30 : 1e-16;
-  for (int sweep = 0; sweep < 40; ++sweep) {
-    double off = 0, tot = 0;
-    for (int e = lane; e < r * r; e += 32) {
-      const int i = e % r, j = e / r;
-      const double v = A[i][j] * A[i][j];
-      tot += v;
-      if (i != j) off += v;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      off += __shfl_xor_sync(0xffffffffu, off, o);
-      tot += __shfl_xor_sync(0xffffffffu, tot, o);
-    }
-    if (off <= conv * tot || r == 1) break;
-    ++sweeps_done;
-    for (int round = 0; round < nn - 1; ++round) {
-      if (lane < npair) {
-        const int k = lane;
-        const int pa = k, pb = nn - 1 - k;
-        const int a = (pa == 0) ? 0 : 1 + ((pa - 1 + round) % (nn - 1));
-        const int b = 1 + ((pb - 1 + round) % (nn - 1));
-        const int lo = a < b ? a : b, hi = a < b ? b : a;
-        pp[k] = lo; qq[k] = hi;
-        double c = 1.0, sv = 0.0;
-        if (hi < r) {
-          const double apq = A[lo][hi];
-          if (apq != 0.0) {
-            const double tau_ = (A[hi][hi] - A[lo][lo]) / (2.0 * apq);
-            const double tt = (tau_ >= 0 ? 1.0 : -1.0) / (fabs(tau_) + sqrt(1.0 + tau_ * tau_));
-            c = rsqrt(1.0 + tt * tt);
-            sv = tt * c;
-          }
-        }
-        cs[k] = c; sn[k] = sv;
-      }
-      __syncwarp();
-      const int nblk = npair * npair;
-      for (int e = lane; e < nblk + npair * r; e += 32) {
-        if (e < nblk) {
-          const int k1 = e / npair, k2 = e - k1 * npair;
-          const int a1 = pp[k1], b1 = qq[k1], a2 = pp[k2], b2 = qq[k2];
-          const bool h1 = b1 < r, h2 = b2 < r;
-          const double c1 = cs[k1], s1 = sn[k1], c2 = cs[k2], s2 = sn[k2];
-          const double x00 = A[a1][a2];
-          const double x01 = h2 ? A[a1][b2] : 0.0;
-          const double x10 = h1 ? A[b1][a2] : 0.0;
-          const double x11 = (h1 && h2) ? A[b1][b2] : 0.0;
-          const double y00 = c2 * x00 - s2 * x01, y01 = s2 * x00 + c2 * x01;
-          const double y10 = c2 * x10 - s2 * x11, y11 = s2 * x10 + c2 * x11;
-          A[a1][a2] = c1 * y00 - s1 * y10;
-          if (h2) A[a1][b2] = c1 * y01 - s1 * y11;
-          if (h1) A[b1][a2] = s1 * y00 + c1 * y10;
-          if (h1 && h2) A[b1][b2] = s1 * y01 + c1 * y11;
-        } else {
-          const int f = e - nblk;
-          const int k = f / r, iv = f - k * r;
-          const int a = pp[k], b = qq[k];
-          if (b < r) {
-            const double c = cs[k], sv = sn[k];
-            const double vx = V[iv][a], vy = V[iv][b];
-            V[iv][a] = c * vx - sv * vy;
-            V[iv][b] = sv * vx + c * vy;
-          }
-        }
-      }
-      __syncwarp();
-    }
-  }
-  double* lam = lams[warp];
-  int* order = ords[warp];
-  if (lane < r) lam[lane] = A[lane][lane];
-  __syncwarp();
-  if (lane < r) {
-    int pos = 0;
-    for (int j = 0; j < r; ++j)
-      if (lam[j] > lam[lane] || (lam[j] == lam[lane] && j < lane)) ++pos;
-    order[pos] = lane;
-  }
-  __syncwarp();
-  int k = 0;
-  if (lane == 0) {
-    const double l1 = lam[order[0]];
-    if (l1 > 0.0) {
-      const double s1 = sqrt(l1);
-      for (int j = 0; j < r; ++j) {
-        const double lj = lam[order[j]];
-        if (lj > 0.0 && sqrt(lj) > eps * s1) ++k;
-        else break;
-      }
-    }
-    if (k > kc) {
-      atomicOr(err, ERR_RANKCAP);
-      k = kc;
-    }
-    crank[ti.c_leaf] = k;
-    if (flops) atomicAdd(flops, 9.0 * r * r * r * sweeps_done);
-  }
-  k = __shfl_sync(0xffffffffu, k, 0);
-  for (int e = lane; e < r * k; e += 32) {
-    const int i = e % r, j = e / r;
-    W[i + (int64_t)j * ld] = (T)V[i][order[j]];
-  }
-}
-
 // Float-float numbers (an unevaluated sum hi + lo of two floats, ~48
 // significant bits): the products and sums of the float form's small
 // Jacobi cores, on the FP32 pipe instead of this part's narrow FP64 pipe.
@@ -501,31 +347,73 @@ __device__ __forceinline__ FF ff_rsqrt1p(float t) {
   return ff_add(FF{y, 0.f}, ff_mul(FF{y, 0.f}, FF{0.5f * e.h, 0.5f * e.l}));
 }
 
-// k_eig_warp for float factors: the same rotation sequence, stopping rule
-// and rank selection, with the core and the accumulated eigenvectors held
-// and rotated in float-float (~1e-14 relative, far below what the float
-// factors keep).  Each rotation's angle is taken in float (an angle off by
-// ~1e-7 leaves ~1e-7 of the entry it should zero, which later rotations
-// remove), and its cosine and sine to float-float accuracy from that angle,
-// so that every rotation is orthogonal to ~1e-14 and no FP64 operation
-// remains in the sweep.
-__global__ void __launch_bounds__(NT) k_eig_warp_ff(const TInfo* __restrict__ tis, int tbase,
-                                                    int tend, double eps, int kc, int c_rbuf,
-                                                    float* const* __restrict__ tab,
-                                                    int* const* __restrict__ rtab, int P,
-                                                    int scr_buf, int scr_rbuf, int* err,
-                                                    double* __restrict__ flops) {
+// The Jacobi cores' element type: FP64 for FP64 factors; for float factors
+// float-float, whose products and sums run on the FP32 pipe instead of this
+// part's narrow FP64 pipe (~1e-14 relative, far below what float factors
+// keep).  jm, ja, jn: multiply, add, negate; jd: the value in double.
+template <typename T>
+using JacE = typename std::conditional<std::is_same<T, float>::value, FF, double>::type;
+__device__ __forceinline__ double jm(double a, double b) { return a * b; }
+__device__ __forceinline__ FF jm(FF a, FF b) { return ff_mul(a, b); }
+__device__ __forceinline__ double ja(double a, double b) { return a + b; }
+__device__ __forceinline__ FF ja(FF a, FF b) { return ff_add(a, b); }
+__device__ __forceinline__ double jn(double a) { return -a; }
+__device__ __forceinline__ FF jn(FF a) { return ff_neg(a); }
+__device__ __forceinline__ double jd(double a) { return a; }
+__device__ __forceinline__ double jd(FF a) { return ff_dbl(a); }
+__device__ __forceinline__ void jset(double& a, double x) { a = x; }
+__device__ __forceinline__ void jset(FF& a, double x) { a = ff_of(x); }
+// The rotation (c, s) that zeroes a_pq of the 2 x 2 block [a_pp a_pq; a_pq a_qq].
+// FP64: the textbook formulas.  Float-float: the angle in float (an angle off
+// by ~1e-7 leaves ~1e-7 of the entry, which later rotations remove), its
+// cosine and sine to float-float accuracy from that angle, so the rotation
+// itself is orthogonal to ~1e-14 and no FP64 operation remains in a sweep.
+__device__ __forceinline__ void jrot(double app, double aqq, double apq, double& c, double& s) {
+  c = 1.0;
+  s = 0.0;
+  if (apq != 0.0) {
+    const double tau_ = (aqq - app) / (2.0 * apq);
+    const double t = (tau_ >= 0 ? 1.0 : -1.0) / (fabs(tau_) + sqrt(1.0 + tau_ * tau_));
+    c = rsqrt(1.0 + t * t);
+    s = t * c;
+  }
+}
+__device__ __forceinline__ void jrot(FF app, FF aqq, FF apq, FF& c, FF& s) {
+  c = FF{1.f, 0.f};
+  s = FF{0.f, 0.f};
+  if (apq.h != 0.f) {
+    const float tau_ = (aqq.h - app.h) / (2.f * apq.h);
+    const float t = (tau_ >= 0.f ? 1.f : -1.f) / (fabsf(tau_) + sqrtf(1.f + tau_ * tau_));
+    c = ff_rsqrt1p(t);
+    s = ff_mul(FF{t, 0.f}, c);
+  }
+}
+
+constexpr int EIG_WARP_MAX = 16;   // cores up to this size: one warp each
+
+// The same cyclic Jacobi for small cores (1 < r <= 16), one warp per target,
+// eight targets per CTA: the rotations of a round are computed and applied
+// by the warp's lanes with warp barriers only (same rotation sequence and
+// stopping rule as k_eig).
+template <typename T>
+__global__ void __launch_bounds__(NT) k_eig_warp(const TInfo* __restrict__ tis, int tbase,
+                                                 int tend, double eps, int kc, int c_rbuf,
+                                                 T* const* __restrict__ tab,
+                                                 int* const* __restrict__ rtab, int P,
+                                                 int scr_buf, int scr_rbuf, int* err,
+                                                 double* __restrict__ flops) {
   constexpr int M = EIG_WARP_MAX;
   const int p = blockIdx.y;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int t = tbase + blockIdx.x * (NT / 32) + warp;
-  __shared__ FF As[NT / 32][M][M + 1], Vs[NT / 32][M][M + 1];
-  __shared__ FF css[NT / 32][M / 2], sns[NT / 32][M / 2];
+  using E = JacE<T>;
+  __shared__ E As[NT / 32][M][M + 1], Vs[NT / 32][M][M + 1];
+  __shared__ E css[NT / 32][M / 2], sns[NT / 32][M / 2];
   __shared__ double lams[NT / 32][M];
   __shared__ int pps[NT / 32][M / 2], qqs[NT / 32][M / 2], ords[NT / 32][M];
   if (t >= tend) return;
   const TInfo ti = tis[t];
-  float* scr = tab[scr_buf * P + p];
+  T* scr = tab[scr_buf * P + p];
   int* rs = rtab[scr_rbuf * P + p];
   int* crank = rtab[c_rbuf * P + p];
   if (!scr || !rs || !crank) return;
@@ -536,29 +424,29 @@ __global__ void __launch_bounds__(NT) k_eig_warp_ff(const TInfo* __restrict__ ti
   }
   if (r > M) return;   // k_eig's cores
   const int ld = ti.p;
-  FF (*A)[M + 1] = As[warp];
-  FF (*V)[M + 1] = Vs[warp];
-  FF* cs = css[warp];
-  FF* sn = sns[warp];
+  E (*A)[M + 1] = As[warp];
+  E (*V)[M + 1] = Vs[warp];
+  E* cs = css[warp];
+  E* sn = sns[warp];
   int* pp = pps[warp];
   int* qq = qqs[warp];
   const double* H = reinterpret_cast<const double*>(scr + ti.h_off);
-  float* W = scr + ti.w_off;
+  T* W = scr + ti.w_off;
   for (int e = lane; e < r * r; e += 32) {
     const int i = e % r, j = e / r;
-    A[i][j] = ff_of(0.5 * (H[i + (int64_t)j * ld] + H[j + (int64_t)i * ld]));
-    V[i][j] = FF{(i == j) ? 1.f : 0.f, 0.f};
+    jset(A[i][j], 0.5 * (H[i + (int64_t)j * ld] + H[j + (int64_t)i * ld]));
+    jset(V[i][j], (i == j) ? 1.0 : 0.0);
   }
   __syncwarp();
   const int nn = (r + 1) & ~1;
   const int npair = nn / 2;
   int sweeps_done = 0;
-  const double conv = 1e-16;
+  const double conv = sizeof(T) == 8 ? 1e-30 : 1e-16;
   for (int sweep = 0; sweep < 40; ++sweep) {
     double off = 0, tot = 0;
     for (int e = lane; e < r * r; e += 32) {
       const int i = e % r, j = e / r;
-      const double a = ff_dbl(A[i][j]);
+      const double a = jd(A[i][j]);
       const double v = a * a;
       tot += v;
       if (i != j) off += v;
@@ -578,16 +466,10 @@ __global__ void __launch_bounds__(NT) k_eig_warp_ff(const TInfo* __restrict__ ti
         const int b = 1 + ((pb - 1 + round) % (nn - 1));
         const int lo = a < b ? a : b, hi = a < b ? b : a;
         pp[k] = lo; qq[k] = hi;
-        FF c{1.f, 0.f}, sv{0.f, 0.f};
-        if (hi < r) {
-          const float apq = A[lo][hi].h;
-          if (apq != 0.f) {
-            const float tau_ = (A[hi][hi].h - A[lo][lo].h) / (2.f * apq);
-            const float tt = (tau_ >= 0.f ? 1.f : -1.f) / (fabsf(tau_) + sqrtf(1.f + tau_ * tau_));
-            c = ff_rsqrt1p(tt);
-            sv = ff_mul(FF{tt, 0.f}, c);
-          }
-        }
+        E c, sv;
+        jset(c, 1.0);
+        jset(sv, 0.0);
+        if (hi < r) jrot(A[lo][lo], A[hi][hi], A[lo][hi], c, sv);
         cs[k] = c; sn[k] = sv;
       }
       __syncwarp();
@@ -597,29 +479,28 @@ __global__ void __launch_bounds__(NT) k_eig_warp_ff(const TInfo* __restrict__ ti
           const int k1 = e / npair, k2 = e - k1 * npair;
           const int a1 = pp[k1], b1 = qq[k1], a2 = pp[k2], b2 = qq[k2];
           const bool h1 = b1 < r, h2 = b2 < r;
-          const FF c1 = cs[k1], s1 = sn[k1], c2 = cs[k2], s2 = sn[k2];
-          const FF z{0.f, 0.f};
-          const FF x00 = A[a1][a2];
-          const FF x01 = h2 ? A[a1][b2] : z;
-          const FF x10 = h1 ? A[b1][a2] : z;
-          const FF x11 = (h1 && h2) ? A[b1][b2] : z;
-          const FF y00 = ff_add(ff_mul(c2, x00), ff_neg(ff_mul(s2, x01)));
-          const FF y01 = ff_add(ff_mul(s2, x00), ff_mul(c2, x01));
-          const FF y10 = ff_add(ff_mul(c2, x10), ff_neg(ff_mul(s2, x11)));
-          const FF y11 = ff_add(ff_mul(s2, x10), ff_mul(c2, x11));
-          A[a1][a2] = ff_add(ff_mul(c1, y00), ff_neg(ff_mul(s1, y10)));
-          if (h2) A[a1][b2] = ff_add(ff_mul(c1, y01), ff_neg(ff_mul(s1, y11)));
-          if (h1) A[b1][a2] = ff_add(ff_mul(s1, y00), ff_mul(c1, y10));
-          if (h1 && h2) A[b1][b2] = ff_add(ff_mul(s1, y01), ff_mul(c1, y11));
+          const E c1 = cs[k1], s1 = sn[k1], c2 = cs[k2], s2 = sn[k2];
+          E z;
+          jset(z, 0.0);
+          const E x00 = A[a1][a2];
+          const E x01 = h2 ? A[a1][b2] : z;
+          const E x10 = h1 ? A[b1][a2] : z;
+          const E x11 = (h1 && h2) ? A[b1][b2] : z;
+          const E y00 = ja(jm(c2, x00), jn(jm(s2, x01))), y01 = ja(jm(s2, x00), jm(c2, x01));
+          const E y10 = ja(jm(c2, x10), jn(jm(s2, x11))), y11 = ja(jm(s2, x10), jm(c2, x11));
+          A[a1][a2] = ja(jm(c1, y00), jn(jm(s1, y10)));
+          if (h2) A[a1][b2] = ja(jm(c1, y01), jn(jm(s1, y11)));
+          if (h1) A[b1][a2] = ja(jm(s1, y00), jm(c1, y10));
+          if (h1 && h2) A[b1][b2] = ja(jm(s1, y01), jm(c1, y11));
         } else {
           const int f = e - nblk;
           const int k = f / r, iv = f - k * r;
           const int a = pp[k], b = qq[k];
           if (b < r) {
-            const FF c = cs[k], sv = sn[k];
-            const FF vx = V[iv][a], vy = V[iv][b];
-            V[iv][a] = ff_add(ff_mul(c, vx), ff_neg(ff_mul(sv, vy)));
-            V[iv][b] = ff_add(ff_mul(sv, vx), ff_mul(c, vy));
+            const E c = cs[k], sv = sn[k];
+            const E vx = V[iv][a], vy = V[iv][b];
+            V[iv][a] = ja(jm(c, vx), jn(jm(sv, vy)));
+            V[iv][b] = ja(jm(sv, vx), jm(c, vy));
           }
         }
       }
@@ -628,7 +509,7 @@ __global__ void __launch_bounds__(NT) k_eig_warp_ff(const TInfo* __restrict__ ti
   }
   double* lam = lams[warp];
   int* order = ords[warp];
-  if (lane < r) lam[lane] = ff_dbl(A[lane][lane]);
+  if (lane < r) lam[lane] = jd(A[lane][lane]);
   __syncwarp();
   if (lane < r) {
     int pos = 0;
@@ -658,12 +539,13 @@ __global__ void __launch_bounds__(NT) k_eig_warp_ff(const TInfo* __restrict__ ti
   k = __shfl_sync(0xffffffffu, k, 0);
   for (int e = lane; e < r * k; e += 32) {
     const int i = e % r, j = e / r;
-    W[i + (int64_t)j * ld] = (float)ff_dbl(V[i][order[j]]);
+    W[i + (int64_t)j * ld] = (T)jd(V[i][order[j]]);
   }
 }
 
 // Cyclic Jacobi (round-robin parallel order) on the r x r symmetric core H
-// (cores with r > 16; k_eig_warp takes the smaller ones).
+// (cores with r > 16; k_eig_warp takes the smaller ones), in the element
+// type JacE<T> (FP64, or float-float for float factors).
 template <typename T>
 __global__ void __launch_bounds__(NT) k_eig(const TInfo* __restrict__ tis, int tbase, double eps,
                                             int kc, int c_rbuf, T* const* __restrict__ tab,
@@ -678,10 +560,12 @@ __global__ void __launch_bounds__(NT) k_eig(const TInfo* __restrict__ tis, int t
   const int r = rs[ti.r_ri];
   const int ld = ti.p;
   if (r <= EIG_WARP_MAX) return;   // k_eig_warp's cores (and the empty bases)
+  using E = JacE<T>;
+  static_assert(sizeof(E) == sizeof(double), "the shared layout holds 8-byte elements");
   extern __shared__ double dsm[];
-  double (*A)[CMAX + 1] = reinterpret_cast<double (*)[CMAX + 1]>(dsm);
-  double (*V)[CMAX + 1] = reinterpret_cast<double (*)[CMAX + 1]>(dsm + CMAX * (CMAX + 1));
-  __shared__ double cs[CMAX / 2 + 1], sn[CMAX / 2 + 1];
+  E (*A)[CMAX + 1] = reinterpret_cast<E (*)[CMAX + 1]>(dsm);
+  E (*V)[CMAX + 1] = reinterpret_cast<E (*)[CMAX + 1]>(dsm + CMAX * (CMAX + 1));
+  __shared__ E cs[CMAX / 2 + 1], sn[CMAX / 2 + 1];
   __shared__ int pp[CMAX / 2 + 1], qq[CMAX / 2 + 1];
   __shared__ double red[NT];
   __shared__ int order[CMAX];
@@ -691,8 +575,8 @@ __global__ void __launch_bounds__(NT) k_eig(const TInfo* __restrict__ tis, int t
   T* W = scr + ti.w_off;
   for (int e = threadIdx.x; e < r * r; e += NT) {
     int i = e % r, j = e / r;
-    A[i][j] = 0.5 * ((double)H[i + (int64_t)j * ld] + (double)H[j + (int64_t)i * ld]);
-    V[i][j] = (i == j) ? 1.0 : 0.0;
+    jset(A[i][j], 0.5 * ((double)H[i + (int64_t)j * ld] + (double)H[j + (int64_t)i * ld]));
+    jset(V[i][j], (i == j) ? 1.0 : 0.0);
   }
   __syncthreads();
   const int nn = (r + 1) & ~1;   // even number of players (r may get a dummy)
@@ -705,7 +589,8 @@ __global__ void __launch_bounds__(NT) k_eig(const TInfo* __restrict__ tis, int t
       const int i = threadIdx.x & 63;
       if (i < r)
         for (int j = threadIdx.x >> 6; j < r; j += 4) {
-          const double v = A[i][j] * A[i][j];
+          const double a = jd(A[i][j]);
+          const double v = a * a;
           tot += v;
           if (i != j) off += v;
         }
@@ -736,16 +621,10 @@ __global__ void __launch_bounds__(NT) k_eig(const TInfo* __restrict__ tis, int t
         const int b = 1 + ((pb - 1 + round) % (nn - 1));
         int lo = a < b ? a : b, hi = a < b ? b : a;
         pp[k] = lo; qq[k] = hi;
-        double c = 1.0, s = 0.0;
-        if (hi < r) {
-          double apq = A[lo][hi];
-          if (apq != 0.0) {
-            double tau_ = (A[hi][hi] - A[lo][lo]) / (2.0 * apq);
-            double t = (tau_ >= 0 ? 1.0 : -1.0) / (fabs(tau_) + sqrt(1.0 + tau_ * tau_));
-            c = rsqrt(1.0 + t * t);
-            s = t * c;
-          }
-        }
+        E c, s;
+        jset(c, 1.0);
+        jset(s, 0.0);
+        if (hi < r) jrot(A[lo][lo], A[hi][hi], A[lo][hi], c, s);
         cs[k] = c; sn[k] = s;
       }
       __syncthreads();
@@ -761,26 +640,28 @@ __global__ void __launch_bounds__(NT) k_eig(const TInfo* __restrict__ tis, int t
           const int k1 = e / npair, k2 = e - k1 * npair;
           const int a1 = pp[k1], b1 = qq[k1], a2 = pp[k2], b2 = qq[k2];
           const bool h1 = b1 < r, h2 = b2 < r;
-          const double c1 = cs[k1], s1 = sn[k1], c2 = cs[k2], s2 = sn[k2];
-          const double x00 = A[a1][a2];
-          const double x01 = h2 ? A[a1][b2] : 0.0;
-          const double x10 = h1 ? A[b1][a2] : 0.0;
-          const double x11 = (h1 && h2) ? A[b1][b2] : 0.0;
-          const double y00 = c2 * x00 - s2 * x01, y01 = s2 * x00 + c2 * x01;
-          const double y10 = c2 * x10 - s2 * x11, y11 = s2 * x10 + c2 * x11;
-          A[a1][a2] = c1 * y00 - s1 * y10;
-          if (h2) A[a1][b2] = c1 * y01 - s1 * y11;
-          if (h1) A[b1][a2] = s1 * y00 + c1 * y10;
-          if (h1 && h2) A[b1][b2] = s1 * y01 + c1 * y11;
+          const E c1 = cs[k1], s1 = sn[k1], c2 = cs[k2], s2 = sn[k2];
+          E z;
+          jset(z, 0.0);
+          const E x00 = A[a1][a2];
+          const E x01 = h2 ? A[a1][b2] : z;
+          const E x10 = h1 ? A[b1][a2] : z;
+          const E x11 = (h1 && h2) ? A[b1][b2] : z;
+          const E y00 = ja(jm(c2, x00), jn(jm(s2, x01))), y01 = ja(jm(s2, x00), jm(c2, x01));
+          const E y10 = ja(jm(c2, x10), jn(jm(s2, x11))), y11 = ja(jm(s2, x10), jm(c2, x11));
+          A[a1][a2] = ja(jm(c1, y00), jn(jm(s1, y10)));
+          if (h2) A[a1][b2] = ja(jm(c1, y01), jn(jm(s1, y11)));
+          if (h1) A[b1][a2] = ja(jm(s1, y00), jm(c1, y10));
+          if (h1 && h2) A[b1][b2] = ja(jm(s1, y01), jm(c1, y11));
         } else {
           const int f = e - nblk;
           const int k = f / r, iv = f - k * r;
           const int a = pp[k], b = qq[k];
           if (b < r) {
-            const double c = cs[k], s = sn[k];
-            const double vx = V[iv][a], vy = V[iv][b];
-            V[iv][a] = c * vx - s * vy;
-            V[iv][b] = s * vx + c * vy;
+            const E c = cs[k], s = sn[k];
+            const E vx = V[iv][a], vy = V[iv][b];
+            V[iv][a] = ja(jm(c, vx), jn(jm(s, vy)));
+            V[iv][b] = ja(jm(s, vx), jm(c, vy));
           }
         }
       }
@@ -788,7 +669,7 @@ __global__ void __launch_bounds__(NT) k_eig(const TInfo* __restrict__ tis, int t
     }
   }
   // sort eigenvalues descending (rank by counting; ties by index)
-  for (int i = threadIdx.x; i < r; i += NT) lam[i] = A[i][i];
+  for (int i = threadIdx.x; i < r; i += NT) lam[i] = jd(A[i][i]);
   __syncthreads();
   for (int i = threadIdx.x; i < r; i += NT) {
     int pos = 0;
@@ -820,7 +701,7 @@ __global__ void __launch_bounds__(NT) k_eig(const TInfo* __restrict__ tis, int t
   const int k = kkeep;
   for (int e = threadIdx.x; e < r * k; e += NT) {
     int i = e % r, j = e / r;
-    W[i + (int64_t)j * ld] = (T)V[i][order[j]];
+    W[i + (int64_t)j * ld] = (T)jd(V[i][order[j]]);
   }
 }
 
@@ -1303,14 +1184,9 @@ void launch_eig(const Plan& pl, int tbeg, int tend, double eps, int kc, int c_ro
     for (int t0 = 0; t0 < nt; t0 += 65535 * per) {
       const int cnt = std::min(65535 * per, nt - t0);
       dim3 grid((cnt + per - 1) / per, P);
-      if constexpr (std::is_same<T, float>::value)
-        k_eig_warp_ff<<<grid, NT, 0, st>>>((const TInfo*)pl.d_targets, tbeg + t0, tbeg + t0 + cnt,
-                                           eps, kc, c_role, d_tab, d_rtab, P, 3 * pl.nroles,
-                                           pl.nroles, d_err, d_fl);
-      else
-        k_eig_warp<T><<<grid, NT, 0, st>>>((const TInfo*)pl.d_targets, tbeg + t0, tbeg + t0 + cnt,
-                                           eps, kc, c_role, d_tab, d_rtab, P, 3 * pl.nroles,
-                                           pl.nroles, d_err, d_fl);
+      k_eig_warp<T><<<grid, NT, 0, st>>>((const TInfo*)pl.d_targets, tbeg + t0, tbeg + t0 + cnt,
+                                         eps, kc, c_role, d_tab, d_rtab, P, 3 * pl.nroles,
+                                         pl.nroles, d_err, d_fl);
       ACR_LAUNCHED(1);
     }
   }
