@@ -137,18 +137,28 @@ def oracle_scale():
 
 
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "grouped_gemm_dram_codi_n64.md")
-GEMM_SOURCE = os.path.join(ROOT, "paper_1712_08872_gb300", "csrc", "acr_gemm_kernels.cu")
+# the grouped-GEMM family's sources: its kernels and the device helpers they inline
+GEMM_SOURCES = [os.path.join(ROOT, "paper_1712_08872_gb300", "csrc", f)
+                for f in ("acr_gemm_kernels.cu", "acr_gemm_tc.cu", "acr_device.h", "acr_tc.h")]
+
+
+def gemm_source_sha():
+    """SHA-256 over the grouped-GEMM family's source files, in order."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in GEMM_SOURCES:
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
 
 
 def gemm_traffic_per_flop():
     """DRAM bytes per algorithmic flop of the grouped-GEMM kernels, from the
     committed ncu summary, or None when the kernel source has changed since
     those counters were taken."""
-    import hashlib
     try:
         txt = open(TRAFFIC_FILE).read()
-        with open(GEMM_SOURCE, "rb") as fh:
-            sha = hashlib.sha256(fh.read()).hexdigest()
+        sha = gemm_source_sha()
     except OSError:
         return None, "no capture"
     bpf = rec = None
@@ -236,10 +246,14 @@ def profile_setup(args):
     prec = acr.ACR_FP64 if args.fp64 else acr.ACR_FP32
     stream = torch.cuda.current_stream()
     table = None
-    if args.tuned:
+    if args.gemm_table:
+        table = [int(v) for v in args.gemm_table.split(",")] + [0] * 16
+        table = table[:16]
+    elif args.tuned:
         table = acr.acr_autotune_gemm(n, coef, spec["eps"], 2.0, spec["leaf"], prec,
                                       args.rank_cap, stream)[0]
-        print("kernel shapes per stage:", table[:13])
+    if table is not None:
+        print("kernel shapes per stage:", ",".join(str(v) for v in table[:13]))
     h = acr.acr_setup(n, coef, spec["eps"], 2.0, spec["leaf"], prec, args.rank_cap, stream,
                       acr.ACR_FLAG_PROFILE, table)
     p = acr.acr_get_profile(h)
@@ -250,8 +264,8 @@ def profile_setup(args):
              inf.max_rank, inf.factor_bytes / 1e9))
     for k in ("gemm", "orth", "eig", "leaf_inv", "other"):
         st = getattr(p, k)
-        print("  %-9s launches %7d  %9.1f ms  %8.3f TFLOP/s"
-              % (k, st.launches, st.ms, st.flops / max(st.ms, 1e-9) / 1e9))
+        print("  %-9s launches %7d  %9.1f ms  %8.3f TFLOP/s  %.4f GFLOP"
+              % (k, st.launches, st.ms, st.flops / max(st.ms, 1e-9) / 1e9, st.flops / 1e9))
     for i, nm in enumerate(p.STAGES):
         print("    %-14s %9.1f ms  %10.3f GFLOP  %8.3f TFLOP/s"
               % (nm, p.stage_ms[i], p.stage_flops[i] / 1e9,
@@ -329,6 +343,8 @@ def main():
     ap.add_argument("--fp64", action="store_true", help="with --profile-setup: FP64 factors")
     ap.add_argument("--tuned", action="store_true",
                     help="with --profile-setup: GEMM kernel shapes from acr_autotune_gemm")
+    ap.add_argument("--gemm-table", default="",
+                    help="with --profile-setup: GEMM kernel shape per stage, comma-separated")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

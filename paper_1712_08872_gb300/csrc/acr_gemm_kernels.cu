@@ -131,142 +131,168 @@ __global__ void __launch_bounds__(NT, MINB) k_ggemm(const GGroup* __restrict__ g
     __syncthreads();
   };
 
+  // items in batches of 32, each resolved by one thread of warp 0 (the
+  // chains of dependent loads of a batch in flight at once) into a shared
+  // table that the whole CTA then walks
+  struct ItemR {
+    const T* A;
+    const T* B;
+    int k, rows, aflags, bflags, lda, ldb, row_off, seed, omega_row0;
+    Acc cf;
+  };
+  __shared__ ItemR sit[32];
   int kfill = 0;
-  for (int it = G.ib; it < G.ie; ++it) {
-    const GItem I = items[it];
-    if (I.guard0 >= 0 && !tab[I.guard0 * P + p]) continue;
-    if (I.guard1 >= 0 && !tab[I.guard1 * P + p]) continue;
-    const T* A = nullptr;
-    const T* B = nullptr;
-    if (I.abuf >= 0) { A = tab[I.abuf * P + p]; if (!A) continue; A += I.aoff; }
-    if (I.bbuf >= 0) { B = tab[I.bbuf * P + p]; if (!B) continue; B += I.boff; }
-    const int k = dimv(I.k_st, I.k_rb, I.k_ri, rtab, P, p);
-    const int rows = dimv(I.r_st, I.r_rb, I.r_ri, rtab, P, p);
-    if (k <= 0 || rows <= 0) continue;
-    const Acc cf = (Acc)coefs[I.coef];
-    const int r0 = I.row_off;
-    if ((I.aflags & FL_IDENT) || (I.bflags & FL_IDENT)) {
-      // C(r0+i, j) += cf * B(i, j)  or  cf * A(i, j): straight into the accumulators
-      fl += (long long)rows * n;
-      const bool ai = I.aflags & FL_IDENT;
-      if (thin) {
-#pragma unroll
-        for (int a = 0; a < 4; ++a) {
-          const int i = ty + 16 * a - r0;
-          if (i < 0 || i >= rows) continue;
-#pragma unroll
-          for (int b = 0; b < 2; ++b) {
-            const int j = tx + 16 * b;
-            if (b < thinNB && j < n)
-              acc[a * 2 + b] += cf * (ai ? (Acc)B[i + (int64_t)j * I.ldb] : (Acc)A[i + (int64_t)j * I.lda]);
-          }
-        }
-      } else if (blocked) {
-#pragma unroll
-        for (int a = 0; a < 4; ++a) {
-          const int i = ty + 16 * a - r0;
-          if (i < 0 || i >= rows) continue;
-#pragma unroll
-          for (int b = 0; b < 4; ++b) {
-            const int j = tx + 16 * b;
-            if (j < n)
-              acc[a * 4 + b] += cf * (ai ? (Acc)B[i + (int64_t)j * I.ldb] : (Acc)A[i + (int64_t)j * I.lda]);
-          }
-        }
-      } else if (slice == 0) {
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          if (q >= Q) break;
-          const int o = lane + q * OL;
-          if (o >= nout) break;
-          const int i = o % m - r0, j = o / m;
-          if (i < 0 || i >= rows) continue;
-          acc[q] += cf * (ai ? (Acc)B[i + (int64_t)j * I.ldb] : (Acc)A[i + (int64_t)j * I.lda]);
-        }
+  for (int base = G.ib; base < G.ie; base += 32) {
+    const int cnt = min(32, G.ie - base);
+    __syncthreads();   // the previous batch's table is read by every thread
+    if (threadIdx.x < cnt) {
+      const GItem J = items[base + threadIdx.x];
+      ItemR R{};
+      bool ok = !(J.guard0 >= 0 && !tab[J.guard0 * P + p]) &&
+                !(J.guard1 >= 0 && !tab[J.guard1 * P + p]);
+      if (ok && J.abuf >= 0) { R.A = tab[J.abuf * P + p]; ok = R.A != nullptr; if (ok) R.A += J.aoff; }
+      if (ok && J.bbuf >= 0) { R.B = tab[J.bbuf * P + p]; ok = R.B != nullptr; if (ok) R.B += J.boff; }
+      if (ok) {
+        R.k = dimv(J.k_st, J.k_rb, J.k_ri, rtab, P, p);
+        R.rows = dimv(J.r_st, J.r_rb, J.r_ri, rtab, P, p);
+        R.cf = (Acc)coefs[J.coef];
       }
-      continue;
+      R.aflags = J.aflags; R.bflags = J.bflags; R.lda = J.lda; R.ldb = J.ldb;
+      R.row_off = J.row_off; R.seed = J.seed; R.omega_row0 = J.omega_row0;
+      sit[threadIdx.x] = R;
     }
-    fl += 2LL * rows * n * k;
-    const bool at = I.aflags & FL_T, bt = I.bflags & FL_T, bo = I.bflags & FL_OMEGA;
-    const bool full = (r0 == 0 && rows >= m);
-    // a whole 64 x 64 dense leaf (contiguous, 16-byte aligned): staged with
-    // vector loads and shift indexing once it fits the chunk entirely
-    const bool blockA = (rows == 64 && r0 == 0 && k == 64 && I.lda == 64 && KC >= 64 &&
-                         (reinterpret_cast<uintptr_t>(A) & 15) == 0);
-    const bool blockB = (!bo && !bt && n == 64 && k == 64 && I.ldb == 64 && KC >= 64 &&
-                         (reinterpret_cast<uintptr_t>(B) & 15) == 0);
-    if ((blockA || blockB) && kfill + 64 > KC) {
-      compute(kfill);
-      kfill = 0;
-    }
-    for (int k0 = 0; k0 < k;) {
-      const int t = min(k - k0, KC - kfill);
-      // A panel -> As[(kfill + kk) * lda_s + r0 + i], zero elsewhere in those columns
-      if (blockA && t == 64) {
-        constexpr int V = 16 / sizeof(T);
-        for (int e0 = threadIdx.x * V; e0 < 4096; e0 += NT * V) {
-          T v[V];
-          *reinterpret_cast<uint4*>(v) = *reinterpret_cast<const uint4*>(A + e0);
+    __syncthreads();
+    for (int qi = 0; qi < cnt; ++qi) {
+      const ItemR I = sit[qi];
+      const int k = I.k, rows = I.rows;
+      if (k <= 0 || rows <= 0) continue;
+      const T* A = I.A;
+      const T* B = I.B;
+      const Acc cf = I.cf;
+      const int r0 = I.row_off;
+      if ((I.aflags & FL_IDENT) || (I.bflags & FL_IDENT)) {
+        // C(r0+i, j) += cf * B(i, j)  or  cf * A(i, j): straight into the accumulators
+        fl += (long long)rows * n;
+        const bool ai = I.aflags & FL_IDENT;
+        if (thin) {
 #pragma unroll
-          for (int q = 0; q < V; ++q) {
-            const int e = e0 + q;
-            // column-major block: e = i + 64 l  (A)  or  e = l + 64 i  (A^T)
-            const int i = at ? (e >> 6) : (e & 63), kk = at ? (e & 63) : (e >> 6);
-            As[(kfill + kk) * lda_s + i] = cf * (Acc)v[q];
+          for (int a = 0; a < 4; ++a) {
+            const int i = ty + 16 * a - r0;
+            if (i < 0 || i >= rows) continue;
+#pragma unroll
+            for (int b = 0; b < 2; ++b) {
+              const int j = tx + 16 * b;
+              if (b < thinNB && j < n)
+                acc[a * 2 + b] += cf * (ai ? (Acc)B[i + (int64_t)j * I.ldb] : (Acc)A[i + (int64_t)j * I.lda]);
+            }
+          }
+        } else if (blocked) {
+#pragma unroll
+          for (int a = 0; a < 4; ++a) {
+            const int i = ty + 16 * a - r0;
+            if (i < 0 || i >= rows) continue;
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+              const int j = tx + 16 * b;
+              if (j < n)
+                acc[a * 4 + b] += cf * (ai ? (Acc)B[i + (int64_t)j * I.ldb] : (Acc)A[i + (int64_t)j * I.lda]);
+            }
+          }
+        } else if (slice == 0) {
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            if (q >= Q) break;
+            const int o = lane + q * OL;
+            if (o >= nout) break;
+            const int i = o % m - r0, j = o / m;
+            if (i < 0 || i >= rows) continue;
+            acc[q] += cf * (ai ? (Acc)B[i + (int64_t)j * I.ldb] : (Acc)A[i + (int64_t)j * I.lda]);
           }
         }
-      } else {
-      if (!full)
-        for (int e = threadIdx.x; e < t * m; e += NT) {
-          const int kk = e / m, i = e - kk * m;
-          if (i < r0 || i >= r0 + rows) As[(kfill + kk) * lda_s + i] = Acc(0);
-        }
-      if (at) {
-        for (int e = threadIdx.x; e < rows * t; e += NT) {
-          const int i = e / t, kk = e - i * t;
-          As[(kfill + kk) * lda_s + r0 + i] = cf * (Acc)A[(k0 + kk) + (int64_t)i * I.lda];
-        }
-      } else {
-        for (int e = threadIdx.x; e < rows * t; e += NT) {
-          const int kk = e / rows, i = e - kk * rows;
-          As[(kfill + kk) * lda_s + r0 + i] = cf * (Acc)A[i + (int64_t)(k0 + kk) * I.lda];
-        }
+        continue;
       }
-      }
-      // B panel -> Bs[(kfill + kk) * ldb_s + j]
-      if (blockB && t == 64) {
-        constexpr int V = 16 / sizeof(T);
-        for (int e0 = threadIdx.x * V; e0 < 4096; e0 += NT * V) {
-          T v[V];
-          *reinterpret_cast<uint4*>(v) = *reinterpret_cast<const uint4*>(B + e0);
-#pragma unroll
-          for (int q = 0; q < V; ++q) {
-            const int e = e0 + q;   // e = l + 64 j
-            Bs[(kfill + (e & 63)) * ldb_s + (e >> 6)] = (Acc)v[q];
-          }
-        }
-      } else if (bo) {
-        for (int e = threadIdx.x; e < t * n; e += NT) {
-          const int kk = e / n, j = e - kk * n;
-          Bs[(kfill + kk) * ldb_s + j] =
-              (Acc)omega((uint32_t)I.seed, (uint32_t)(I.omega_row0 + k0 + kk), (uint32_t)j);
-        }
-      } else if (bt) {
-        for (int e = threadIdx.x; e < t * n; e += NT) {
-          const int kk = e / n, j = e - kk * n;
-          Bs[(kfill + kk) * ldb_s + j] = (Acc)B[j + (int64_t)(k0 + kk) * I.ldb];
-        }
-      } else {
-        for (int e = threadIdx.x; e < t * n; e += NT) {
-          const int j = e / t, kk = e - j * t;
-          Bs[(kfill + kk) * ldb_s + j] = (Acc)B[(k0 + kk) + (int64_t)j * I.ldb];
-        }
-      }
-      kfill += t;
-      k0 += t;
-      if (kfill == KC) {
+      fl += 2LL * rows * n * k;
+      const bool at = I.aflags & FL_T, bt = I.bflags & FL_T, bo = I.bflags & FL_OMEGA;
+      const bool full = (r0 == 0 && rows >= m);
+      // a whole 64 x 64 dense leaf (contiguous, 16-byte aligned): staged with
+      // vector loads and shift indexing once it fits the chunk entirely
+      const bool blockA = (rows == 64 && r0 == 0 && k == 64 && I.lda == 64 && KC >= 64 &&
+                           (reinterpret_cast<uintptr_t>(A) & 15) == 0);
+      const bool blockB = (!bo && !bt && n == 64 && k == 64 && I.ldb == 64 && KC >= 64 &&
+                           (reinterpret_cast<uintptr_t>(B) & 15) == 0);
+      if ((blockA || blockB) && kfill + 64 > KC) {
         compute(kfill);
         kfill = 0;
+      }
+      for (int k0 = 0; k0 < k;) {
+        const int t = min(k - k0, KC - kfill);
+        // A panel -> As[(kfill + kk) * lda_s + r0 + i], zero elsewhere in those columns
+        if (blockA && t == 64) {
+          constexpr int V = 16 / sizeof(T);
+          for (int e0 = threadIdx.x * V; e0 < 4096; e0 += NT * V) {
+            T v[V];
+            *reinterpret_cast<uint4*>(v) = *reinterpret_cast<const uint4*>(A + e0);
+#pragma unroll
+            for (int q = 0; q < V; ++q) {
+              const int e = e0 + q;
+              // column-major block: e = i + 64 l  (A)  or  e = l + 64 i  (A^T)
+              const int i = at ? (e >> 6) : (e & 63), kk = at ? (e & 63) : (e >> 6);
+              As[(kfill + kk) * lda_s + i] = cf * (Acc)v[q];
+            }
+          }
+        } else {
+        if (!full)
+          for (int e = threadIdx.x; e < t * m; e += NT) {
+            const int kk = e / m, i = e - kk * m;
+            if (i < r0 || i >= r0 + rows) As[(kfill + kk) * lda_s + i] = Acc(0);
+          }
+        if (at) {
+          for (int e = threadIdx.x; e < rows * t; e += NT) {
+            const int i = e / t, kk = e - i * t;
+            As[(kfill + kk) * lda_s + r0 + i] = cf * (Acc)A[(k0 + kk) + (int64_t)i * I.lda];
+          }
+        } else {
+          for (int e = threadIdx.x; e < rows * t; e += NT) {
+            const int kk = e / rows, i = e - kk * rows;
+            As[(kfill + kk) * lda_s + r0 + i] = cf * (Acc)A[i + (int64_t)(k0 + kk) * I.lda];
+          }
+        }
+        }
+        // B panel -> Bs[(kfill + kk) * ldb_s + j]
+        if (blockB && t == 64) {
+          constexpr int V = 16 / sizeof(T);
+          for (int e0 = threadIdx.x * V; e0 < 4096; e0 += NT * V) {
+            T v[V];
+            *reinterpret_cast<uint4*>(v) = *reinterpret_cast<const uint4*>(B + e0);
+#pragma unroll
+            for (int q = 0; q < V; ++q) {
+              const int e = e0 + q;   // e = l + 64 j
+              Bs[(kfill + (e & 63)) * ldb_s + (e >> 6)] = (Acc)v[q];
+            }
+          }
+        } else if (bo) {
+          for (int e = threadIdx.x; e < t * n; e += NT) {
+            const int kk = e / n, j = e - kk * n;
+            Bs[(kfill + kk) * ldb_s + j] =
+                (Acc)omega((uint32_t)I.seed, (uint32_t)(I.omega_row0 + k0 + kk), (uint32_t)j);
+          }
+        } else if (bt) {
+          for (int e = threadIdx.x; e < t * n; e += NT) {
+            const int kk = e / n, j = e - kk * n;
+            Bs[(kfill + kk) * ldb_s + j] = (Acc)B[j + (int64_t)(k0 + kk) * I.ldb];
+          }
+        } else {
+          for (int e = threadIdx.x; e < t * n; e += NT) {
+            const int j = e / t, kk = e - j * t;
+            Bs[(kfill + kk) * ldb_s + j] = (Acc)B[(k0 + kk) + (int64_t)j * I.ldb];
+          }
+        }
+        kfill += t;
+        k0 += t;
+        if (kfill == KC) {
+          compute(kfill);
+          kfill = 0;
+        }
       }
     }
   }
@@ -669,6 +695,35 @@ __global__ void __launch_bounds__(NT, sizeof(Acc) == 4 ? 4 : 1) k_gdot_warp(cons
   C += G.coff;
   const Acc beta = G.beta >= 0 ? (Acc)coefs[G.beta] : Acc(0);
   long long fl = 0;
+  // the group's items (up to 32: every inner-product group in practice)
+  // resolved once, lane q taking item ib + q, into the warp's shared table,
+  // which every tile pass then reads; longer groups resolve per pass
+  struct ItemR {
+    const T* A;
+    const T* B;
+    int k, rows, lda, ldb, seed, omega_row0, bo;
+    Acc cf;
+  };
+  __shared__ ItemR sit[NT / 32][32];
+  const int nit = G.ie - G.ib;
+  const bool tabled = nit <= 32;
+  if (tabled && lane < nit) {
+    const GItem J = items[G.ib + lane];
+    ItemR R{};
+    bool ok = !(J.guard0 >= 0 && !tab[J.guard0 * P + p]) &&
+              !(J.guard1 >= 0 && !tab[J.guard1 * P + p]);
+    if (ok) { R.A = tab[J.abuf * P + p]; ok = R.A != nullptr; if (ok) R.A += J.aoff; }
+    R.bo = (J.bflags & FL_OMEGA) ? 1 : 0;
+    if (ok && !R.bo) { R.B = tab[J.bbuf * P + p]; ok = R.B != nullptr; if (ok) R.B += J.boff; }
+    if (ok) {
+      R.k = dimv(J.k_st, J.k_rb, J.k_ri, rtab, P, p);
+      R.rows = dimv(J.r_st, J.r_rb, J.r_ri, rtab, P, p);
+      R.cf = (Acc)coefs[J.coef];
+    }
+    R.lda = J.lda; R.ldb = J.ldb; R.seed = J.seed; R.omega_row0 = J.omega_row0;
+    sit[warp][lane] = R;
+  }
+  __syncwarp();
   for (int i0 = 0; i0 < m; i0 += 4) {
     for (int j0 = 0; j0 < n; j0 += 8) {
       Acc acc[4][8];
@@ -677,24 +732,35 @@ __global__ void __launch_bounds__(NT, sizeof(Acc) == 4 ? 4 : 1) k_gdot_warp(cons
 #pragma unroll
         for (int c = 0; c < 8; ++c) acc[r][c] = Acc(0);
       for (int it = G.ib; it < G.ie; ++it) {
-        const GItem I = items[it];
-        if (I.guard0 >= 0 && !tab[I.guard0 * P + p]) continue;
-        if (I.guard1 >= 0 && !tab[I.guard1 * P + p]) continue;
-        const T* A = tab[I.abuf * P + p];
-        if (!A) continue;
-        A += I.aoff;
-        const bool bo = I.bflags & FL_OMEGA;
-        const T* B = nullptr;
-        if (!bo) {
-          B = tab[I.bbuf * P + p];
-          if (!B) continue;
-          B += I.boff;
+        ItemR I;
+        if (tabled) {
+          I = sit[warp][it - G.ib];
+        } else {
+          const GItem J = items[it];
+          if (J.guard0 >= 0 && !tab[J.guard0 * P + p]) continue;
+          if (J.guard1 >= 0 && !tab[J.guard1 * P + p]) continue;
+          I.A = tab[J.abuf * P + p];
+          if (!I.A) continue;
+          I.A += J.aoff;
+          I.bo = (J.bflags & FL_OMEGA) ? 1 : 0;
+          I.B = nullptr;
+          if (!I.bo) {
+            I.B = tab[J.bbuf * P + p];
+            if (!I.B) continue;
+            I.B += J.boff;
+          }
+          I.k = dimv(J.k_st, J.k_rb, J.k_ri, rtab, P, p);
+          I.rows = dimv(J.r_st, J.r_rb, J.r_ri, rtab, P, p);
+          I.cf = (Acc)coefs[J.coef];
+          I.lda = J.lda; I.ldb = J.ldb; I.seed = J.seed; I.omega_row0 = J.omega_row0;
         }
-        const int k = dimv(I.k_st, I.k_rb, I.k_ri, rtab, P, p);
-        const int rows = dimv(I.r_st, I.r_rb, I.r_ri, rtab, P, p);
+        const int k = I.k, rows = I.rows;
         if (k <= 0 || rows <= 0) continue;
+        const T* A = I.A;
+        const T* B = I.B;
+        const bool bo = I.bo != 0;
         if (i0 == 0 && j0 == 0) fl += 2LL * rows * n * k;
-        const Acc cf = (Acc)coefs[I.coef];
+        const Acc cf = I.cf;
         const T* ar[4];
 #pragma unroll
         for (int r = 0; r < 4; ++r) ar[r] = (i0 + r < rows) ? A + (int64_t)(i0 + r) * I.lda : nullptr;
