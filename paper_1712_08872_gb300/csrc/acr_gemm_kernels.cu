@@ -695,35 +695,6 @@ __global__ void __launch_bounds__(NT, sizeof(Acc) == 4 ? 4 : 1) k_gdot_warp(cons
   C += G.coff;
   const Acc beta = G.beta >= 0 ? (Acc)coefs[G.beta] : Acc(0);
   long long fl = 0;
-  // the group's items (up to 32: every inner-product group in practice)
-  // resolved once, lane q taking item ib + q, into the warp's shared table,
-  // which every tile pass then reads; longer groups resolve per pass
-  struct ItemR {
-    const T* A;
-    const T* B;
-    int k, rows, lda, ldb, seed, omega_row0, bo;
-    Acc cf;
-  };
-  __shared__ ItemR sit[NT / 32][32];
-  const int nit = G.ie - G.ib;
-  const bool tabled = nit <= 32;
-  if (tabled && lane < nit) {
-    const GItem J = items[G.ib + lane];
-    ItemR R{};
-    bool ok = !(J.guard0 >= 0 && !tab[J.guard0 * P + p]) &&
-              !(J.guard1 >= 0 && !tab[J.guard1 * P + p]);
-    if (ok) { R.A = tab[J.abuf * P + p]; ok = R.A != nullptr; if (ok) R.A += J.aoff; }
-    R.bo = (J.bflags & FL_OMEGA) ? 1 : 0;
-    if (ok && !R.bo) { R.B = tab[J.bbuf * P + p]; ok = R.B != nullptr; if (ok) R.B += J.boff; }
-    if (ok) {
-      R.k = dimv(J.k_st, J.k_rb, J.k_ri, rtab, P, p);
-      R.rows = dimv(J.r_st, J.r_rb, J.r_ri, rtab, P, p);
-      R.cf = (Acc)coefs[J.coef];
-    }
-    R.lda = J.lda; R.ldb = J.ldb; R.seed = J.seed; R.omega_row0 = J.omega_row0;
-    sit[warp][lane] = R;
-  }
-  __syncwarp();
   for (int i0 = 0; i0 < m; i0 += 4) {
     for (int j0 = 0; j0 < n; j0 += 8) {
       Acc acc[4][8];
@@ -732,35 +703,24 @@ __global__ void __launch_bounds__(NT, sizeof(Acc) == 4 ? 4 : 1) k_gdot_warp(cons
 #pragma unroll
         for (int c = 0; c < 8; ++c) acc[r][c] = Acc(0);
       for (int it = G.ib; it < G.ie; ++it) {
-        ItemR I;
-        if (tabled) {
-          I = sit[warp][it - G.ib];
-        } else {
-          const GItem J = items[it];
-          if (J.guard0 >= 0 && !tab[J.guard0 * P + p]) continue;
-          if (J.guard1 >= 0 && !tab[J.guard1 * P + p]) continue;
-          I.A = tab[J.abuf * P + p];
-          if (!I.A) continue;
-          I.A += J.aoff;
-          I.bo = (J.bflags & FL_OMEGA) ? 1 : 0;
-          I.B = nullptr;
-          if (!I.bo) {
-            I.B = tab[J.bbuf * P + p];
-            if (!I.B) continue;
-            I.B += J.boff;
-          }
-          I.k = dimv(J.k_st, J.k_rb, J.k_ri, rtab, P, p);
-          I.rows = dimv(J.r_st, J.r_rb, J.r_ri, rtab, P, p);
-          I.cf = (Acc)coefs[J.coef];
-          I.lda = J.lda; I.ldb = J.ldb; I.seed = J.seed; I.omega_row0 = J.omega_row0;
+        const GItem I = items[it];
+        if (I.guard0 >= 0 && !tab[I.guard0 * P + p]) continue;
+        if (I.guard1 >= 0 && !tab[I.guard1 * P + p]) continue;
+        const T* A = tab[I.abuf * P + p];
+        if (!A) continue;
+        A += I.aoff;
+        const bool bo = I.bflags & FL_OMEGA;
+        const T* B = nullptr;
+        if (!bo) {
+          B = tab[I.bbuf * P + p];
+          if (!B) continue;
+          B += I.boff;
         }
-        const int k = I.k, rows = I.rows;
+        const int k = dimv(I.k_st, I.k_rb, I.k_ri, rtab, P, p);
+        const int rows = dimv(I.r_st, I.r_rb, I.r_ri, rtab, P, p);
         if (k <= 0 || rows <= 0) continue;
-        const T* A = I.A;
-        const T* B = I.B;
-        const bool bo = I.bo != 0;
         if (i0 == 0 && j0 == 0) fl += 2LL * rows * n * k;
-        const Acc cf = I.cf;
+        const Acc cf = (Acc)coefs[I.coef];
         const T* ar[4];
 #pragma unroll
         for (int r = 0; r < 4; ++r) ar[r] = (i0 + r < rows) ? A + (int64_t)(i0 + r) * I.lda : nullptr;
