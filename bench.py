@@ -43,9 +43,9 @@ def load_peaks():
     return {"hbm_gbs": FALLBACK_HBM_GBS, "sm_max_mhz": 2070.0}, "fallback"
 
 
-# FP32 CUDA-core peak of the part: 152 SMs x 128 FP32 lanes x 2 flop/FMA
-def fp32_alu_peak_tflops(mhz):
-    return 152 * 128 * 2 * mhz * 1e6 / 1e12
+# FP32 CUDA-core peak of the part: SMs (queried) x 128 FP32 lanes x 2 flop/FMA
+def fp32_alu_peak_tflops(mhz, sms=152):
+    return sms * 128 * 2 * mhz * 1e6 / 1e12
 
 
 class ClockSampler:
@@ -490,13 +490,14 @@ def main():
     ds = stats[dom]
     if dom == "gemm":
         achieved = ds.flops / (ds.ms / 1000.0) / 1e12
-        peak = fp32_alu_peak_tflops(peaks.get("sm_max_mhz", 2070.0))
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        peak = fp32_alu_peak_tflops(peaks.get("sm_max_mhz", 2070.0), sms)
         bpf, tsrc = gemm_traffic_per_flop()
         traffic = bpf * ds.flops / ds.launches if (bpf is not None and ds.launches) else None
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic, "traffic_unit": "bytes per launch",
                 "traffic_source": tsrc, "kernel": "k_ggemm/k_gdot<float> (grouped GEMM family)",
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock",
+                "peak_source": "derived: %d SMs x 128 FP32 lanes x 2 x max SM clock" % sms,
                 "launches": ds.launches, "ms_total": ds.ms}
     else:
         achieved = ds.flops / (ds.ms / 1000.0) / 1e12

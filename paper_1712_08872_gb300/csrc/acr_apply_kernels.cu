@@ -588,7 +588,7 @@ __global__ void __launch_bounds__(256) k_lr_proj32(MatvecDev mv, T* const* __res
 
 void launch_to_bf16(const float* in, void* out, int64_t count, cudaStream_t st) {
   if (count <= 0) return;
-  const int blocks = (int)std::min<int64_t>((count + 255) / 256, 152 * 16);
+  const int blocks = (int)std::min<int64_t>((count + 255) / 256, (int64_t)device_sm_count() * 16);
   k_to_bf16<<<blocks, 256, 0, st>>>(in, (__nv_bfloat16*)out, count);
   ACR_LAUNCHED(1);
 }
@@ -676,7 +676,7 @@ template void launch_lr_proj<__nv_bfloat16>(const MatvecDev&, __nv_bfloat16* con
 void launch_permute(const double* in, double* out, const int* perm, int n2, int nplanes,
                     bool to_cluster, cudaStream_t st) {
   int64_t total = (int64_t)n2 * nplanes;
-  int blocks = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
+  int blocks = (int)std::min<int64_t>((total + 255) / 256, (int64_t)device_sm_count() * 16);
   k_permute<<<blocks, 256, 0, st>>>(in, out, perm, n2, total, to_cluster);
   ACR_LAUNCHED(1);
 }

@@ -35,6 +35,20 @@ void count_launches(int64_t k) { g_launches.fetch_add(k, std::memory_order_relax
 static std::atomic<int64_t> g_allocs{0};
 void count_allocs(int64_t k) { g_allocs.fetch_add(k, std::memory_order_relaxed); }
 
+int device_sm_count() {
+  static std::atomic<int> cache[64];   // 0: not queried yet
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) dev = 0;
+  const int slot = (dev >= 0 && dev < 64) ? dev : 0;
+  int n = cache[slot].load(std::memory_order_relaxed);
+  if (n <= 0) {
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
+      n = 1;
+    cache[slot].store(n, std::memory_order_relaxed);
+  }
+  return n;
+}
+
 namespace {
 
 struct AcrError {

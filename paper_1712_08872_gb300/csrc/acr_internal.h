@@ -20,6 +20,10 @@ void count_launches(int64_t k);
 // Process-wide count of device and pinned-host allocations made by the library.
 void count_allocs(int64_t k);
 
+// Streaming multiprocessors of the current device (queried once per device);
+// grid-stride kernels size their grids as a multiple of it.
+int device_sm_count();
+
 // Device-side error word bits (written by kernels, read by the host).
 enum : int { ERR_PIVOT = 1, ERR_RANKCAP = 2, ERR_GROWTH = 4, ERR_TIMEOUT = 8, ERR_SHAPE = 16 };
 

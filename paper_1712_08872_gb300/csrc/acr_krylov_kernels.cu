@@ -256,8 +256,9 @@ __global__ void k_baxpby(double* __restrict__ Y, const double* __restrict__ X,
 }
 
 inline int grid_for(int64_t N) {
+  const int64_t cap = (int64_t)device_sm_count() * 16;
   int64_t b = (N + 255) / 256;
-  return (int)(b < 152 * 16 ? (b < 1 ? 1 : b) : 152 * 16);
+  return (int)(b < cap ? (b < 1 ? 1 : b) : cap);
 }
 
 }  // namespace

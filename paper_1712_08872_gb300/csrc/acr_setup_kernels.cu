@@ -28,6 +28,90 @@ namespace {
 // ---------------------------------------------------------------- cores
 constexpr int CMAX = 64;   // largest sketch / core dimension
 
+// Float-float numbers (an unevaluated sum hi + lo of two floats, ~48
+// significant bits): the products and sums of the float form's small
+// Jacobi cores, on the FP32 pipe instead of this part's narrow FP64 pipe.
+struct FF {
+  float h, l;
+};
+__device__ __forceinline__ FF ff_of(double x) {
+  const float h = (float)x;
+  return FF{h, (float)(x - (double)h)};
+}
+__device__ __forceinline__ double ff_dbl(FF a) { return (double)a.h + (double)a.l; }
+// a * b: exact product of the high parts plus the cross terms, renormalised
+__device__ __forceinline__ FF ff_mul(FF a, FF b) {
+  const float p = a.h * b.h;
+  float e = fmaf(a.h, b.h, -p);
+  e = fmaf(a.h, b.l, e);
+  e = fmaf(a.l, b.h, e);
+  const float s = p + e;
+  return FF{s, e - (s - p)};
+}
+// a + b: TwoSum of the high parts, low parts added, renormalised
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+  const float s = a.h + b.h;
+  const float bp = s - a.h;
+  float e = (a.h - (s - bp)) + (b.h - bp);
+  e += a.l + b.l;
+  const float r = s + e;
+  return FF{r, e - (r - s)};
+}
+__device__ __forceinline__ FF ff_neg(FF a) { return FF{-a.h, -a.l}; }
+// (1 + t^2)^(-1/2) to float-float accuracy: one Newton step y + y (1 - x y^2) / 2
+// from the float estimate
+__device__ __forceinline__ FF ff_rsqrt1p(float t) {
+  const float p = t * t;
+  const FF x = ff_add(FF{1.f, 0.f}, FF{p, fmaf(t, t, -p)});
+  const float y = rsqrtf(x.h);
+  const FF xy2 = ff_mul(x, ff_mul(FF{y, 0.f}, FF{y, 0.f}));
+  const FF e = ff_add(FF{1.f, 0.f}, ff_neg(xy2));
+  return ff_add(FF{y, 0.f}, ff_mul(FF{y, 0.f}, FF{0.5f * e.h, 0.5f * e.l}));
+}
+
+// The Jacobi cores' element type: FP64 for FP64 factors; for float factors
+// float-float, whose products and sums run on the FP32 pipe instead of this
+// part's narrow FP64 pipe (~1e-14 relative, far below what float factors
+// keep).  jm, ja, jn: multiply, add, negate; jd: the value in double.
+template <typename T>
+using JacE = typename std::conditional<std::is_same<T, float>::value, FF, double>::type;
+__device__ __forceinline__ double jm(double a, double b) { return a * b; }
+__device__ __forceinline__ FF jm(FF a, FF b) { return ff_mul(a, b); }
+__device__ __forceinline__ double ja(double a, double b) { return a + b; }
+__device__ __forceinline__ FF ja(FF a, FF b) { return ff_add(a, b); }
+__device__ __forceinline__ double jn(double a) { return -a; }
+__device__ __forceinline__ FF jn(FF a) { return ff_neg(a); }
+__device__ __forceinline__ double jd(double a) { return a; }
+__device__ __forceinline__ double jd(FF a) { return ff_dbl(a); }
+__device__ __forceinline__ void jset(double& a, double x) { a = x; }
+__device__ __forceinline__ void jset(FF& a, double x) { a = ff_of(x); }
+// The rotation (c, s) that zeroes a_pq of the 2 x 2 block [a_pp a_pq; a_pq a_qq].
+// FP64: the textbook formulas.  Float-float: the angle in float (an angle off
+// by ~1e-7 leaves ~1e-7 of the entry, which later rotations remove), its
+// cosine and sine to float-float accuracy from that angle, so the rotation
+// itself is orthogonal to ~1e-14 and no FP64 operation remains in a sweep.
+__device__ __forceinline__ void jrot(double app, double aqq, double apq, double& c, double& s) {
+  c = 1.0;
+  s = 0.0;
+  if (apq != 0.0) {
+    const double tau_ = (aqq - app) / (2.0 * apq);
+    const double t = (tau_ >= 0 ? 1.0 : -1.0) / (fabs(tau_) + sqrt(1.0 + tau_ * tau_));
+    c = rsqrt(1.0 + t * t);
+    s = t * c;
+  }
+}
+__device__ __forceinline__ void jrot(FF app, FF aqq, FF apq, FF& c, FF& s) {
+  c = FF{1.f, 0.f};
+  s = FF{0.f, 0.f};
+  if (apq.h != 0.f) {
+    const float tau_ = (aqq.h - app.h) / (2.f * apq.h);
+    const float t = (tau_ >= 0.f ? 1.f : -1.f) / (fabsf(tau_) + sqrtf(1.f + tau_ * tau_));
+    c = ff_rsqrt1p(t);
+    s = ff_mul(FF{t, 0.f}, c);
+  }
+}
+
+
 // Pivoted Cholesky of G (pd x pd): G = P L L^T P^T, stop when the largest
 // remaining diagonal <= tau^2 * max diag(G) (truncating pass).  Writes
 // T (p x r, ld p) with Q = Y T orthonormal, and r.
@@ -303,89 +387,6 @@ __global__ void __launch_bounds__(NT) k_pchol(const TInfo* __restrict__ tis, int
   if (threadIdx.x == 0) {
     rs[ti.r_ri] = r;
     if (flops) atomicAdd(flops, (double)pd * r * r - 2.0 * r * r * r / 3.0 + (double)r * r * r / 3.0);
-  }
-}
-
-// Float-float numbers (an unevaluated sum hi + lo of two floats, ~48
-// significant bits): the products and sums of the float form's small
-// Jacobi cores, on the FP32 pipe instead of this part's narrow FP64 pipe.
-struct FF {
-  float h, l;
-};
-__device__ __forceinline__ FF ff_of(double x) {
-  const float h = (float)x;
-  return FF{h, (float)(x - (double)h)};
-}
-__device__ __forceinline__ double ff_dbl(FF a) { return (double)a.h + (double)a.l; }
-// a * b: exact product of the high parts plus the cross terms, renormalised
-__device__ __forceinline__ FF ff_mul(FF a, FF b) {
-  const float p = a.h * b.h;
-  float e = fmaf(a.h, b.h, -p);
-  e = fmaf(a.h, b.l, e);
-  e = fmaf(a.l, b.h, e);
-  const float s = p + e;
-  return FF{s, e - (s - p)};
-}
-// a + b: TwoSum of the high parts, low parts added, renormalised
-__device__ __forceinline__ FF ff_add(FF a, FF b) {
-  const float s = a.h + b.h;
-  const float bp = s - a.h;
-  float e = (a.h - (s - bp)) + (b.h - bp);
-  e += a.l + b.l;
-  const float r = s + e;
-  return FF{r, e - (r - s)};
-}
-__device__ __forceinline__ FF ff_neg(FF a) { return FF{-a.h, -a.l}; }
-// (1 + t^2)^(-1/2) to float-float accuracy: one Newton step y + y (1 - x y^2) / 2
-// from the float estimate
-__device__ __forceinline__ FF ff_rsqrt1p(float t) {
-  const float p = t * t;
-  const FF x = ff_add(FF{1.f, 0.f}, FF{p, fmaf(t, t, -p)});
-  const float y = rsqrtf(x.h);
-  const FF xy2 = ff_mul(x, ff_mul(FF{y, 0.f}, FF{y, 0.f}));
-  const FF e = ff_add(FF{1.f, 0.f}, ff_neg(xy2));
-  return ff_add(FF{y, 0.f}, ff_mul(FF{y, 0.f}, FF{0.5f * e.h, 0.5f * e.l}));
-}
-
-// The Jacobi cores' element type: FP64 for FP64 factors; for float factors
-// float-float, whose products and sums run on the FP32 pipe instead of this
-// part's narrow FP64 pipe (~1e-14 relative, far below what float factors
-// keep).  jm, ja, jn: multiply, add, negate; jd: the value in double.
-template <typename T>
-using JacE = typename std::conditional<std::is_same<T, float>::value, FF, double>::type;
-__device__ __forceinline__ double jm(double a, double b) { return a * b; }
-__device__ __forceinline__ FF jm(FF a, FF b) { return ff_mul(a, b); }
-__device__ __forceinline__ double ja(double a, double b) { return a + b; }
-__device__ __forceinline__ FF ja(FF a, FF b) { return ff_add(a, b); }
-__device__ __forceinline__ double jn(double a) { return -a; }
-__device__ __forceinline__ FF jn(FF a) { return ff_neg(a); }
-__device__ __forceinline__ double jd(double a) { return a; }
-__device__ __forceinline__ double jd(FF a) { return ff_dbl(a); }
-__device__ __forceinline__ void jset(double& a, double x) { a = x; }
-__device__ __forceinline__ void jset(FF& a, double x) { a = ff_of(x); }
-// The rotation (c, s) that zeroes a_pq of the 2 x 2 block [a_pp a_pq; a_pq a_qq].
-// FP64: the textbook formulas.  Float-float: the angle in float (an angle off
-// by ~1e-7 leaves ~1e-7 of the entry, which later rotations remove), its
-// cosine and sine to float-float accuracy from that angle, so the rotation
-// itself is orthogonal to ~1e-14 and no FP64 operation remains in a sweep.
-__device__ __forceinline__ void jrot(double app, double aqq, double apq, double& c, double& s) {
-  c = 1.0;
-  s = 0.0;
-  if (apq != 0.0) {
-    const double tau_ = (aqq - app) / (2.0 * apq);
-    const double t = (tau_ >= 0 ? 1.0 : -1.0) / (fabs(tau_) + sqrt(1.0 + tau_ * tau_));
-    c = rsqrt(1.0 + t * t);
-    s = t * c;
-  }
-}
-__device__ __forceinline__ void jrot(FF app, FF aqq, FF apq, FF& c, FF& s) {
-  c = FF{1.f, 0.f};
-  s = FF{0.f, 0.f};
-  if (apq.h != 0.f) {
-    const float tau_ = (aqq.h - app.h) / (2.f * apq.h);
-    const float t = (tau_ >= 0.f ? 1.f : -1.f) / (fabsf(tau_) + sqrtf(1.f + tau_ * tau_));
-    c = ff_rsqrt1p(t);
-    s = ff_mul(FF{t, 0.f}, c);
   }
 }
 
@@ -971,25 +972,42 @@ __global__ void __launch_bounds__(LTH) k_leaf_inv_f(float* const* __restrict__ d
     float dprev = INFINITY;
     for (int it = 0; it < 4 && !done && !fallback; ++it) {
       ++steps;
-      // R = I - A0 X from exact products and compensated sums
-      if (ti < n)
-        for (int j = tj; j < n; j += CS) {
-          float sh = 0.f, sl = 0.f;
-          for (int l = 0; l < n; ++l) ff_fma(sh, sl, A0[ti][l], X[l][j]);
-          R[ti][j] = ((ti == j ? 1.f : 0.f) - sh) - sl;
+      // R = I - A0 X from exact products and compensated sums; the thread's
+      // CMAX / CS entries advance together (independent chains, one load of
+      // A0 per step; columns beyond n are computed and dropped)
+      constexpr int NQ = CMAX / CS;
+      if (ti < n) {
+        float sh[NQ], sl[NQ];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) { sh[q] = 0.f; sl[q] = 0.f; }
+        for (int l = 0; l < n; ++l) {
+          const float a = A0[ti][l];
+#pragma unroll
+          for (int q = 0; q < NQ; ++q) ff_fma(sh[q], sl[q], a, X[l][tj + CS * q]);
         }
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+          const int j = tj + CS * q;
+          if (j < n) R[ti][j] = ((ti == j ? 1.f : 0.f) - sh[q]) - sl[q];
+        }
+      }
       __syncthreads();
       // correction D = X R; X += D
-      float d[CMAX / CS];
+      float d[NQ];
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) d[q] = 0.f;
+      if (ti < n)
+        for (int l = 0; l < n; ++l) {
+          const float x = X[ti][l];
+#pragma unroll
+          for (int q = 0; q < NQ; ++q) d[q] = fmaf(x, R[l][tj + CS * q], d[q]);
+        }
       float dmax = 0.f;
 #pragma unroll
-      for (int q = 0; q < CMAX / CS; ++q) {
+      for (int q = 0; q < NQ; ++q) {
         const int j = tj + CS * q;
-        float v = 0.f;
         if (ti < n && j < n)
-          for (int l = 0; l < n; ++l) v = fmaf(X[ti][l], R[l][j], v);
-        d[q] = v;
-        dmax = (fabsf(v) <= 3.0e38f) ? fmaxf(dmax, fabsf(v)) : INFINITY;
+          dmax = (fabsf(d[q]) <= 3.0e38f) ? fmaxf(dmax, fabsf(d[q])) : INFINITY;
       }
       __syncthreads();   // every read of X is done
       float xmax = 0.f;
