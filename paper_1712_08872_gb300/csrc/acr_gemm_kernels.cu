@@ -356,8 +356,8 @@ __global__ void __launch_bounds__(NT, MINB) k_ggemm(const GGroup* __restrict__ g
 
 // Warp-per-group form of k_ggemm for float operands and row panels
 // (m <= 64 output rows): one warp owns one group's m x n output, lane l
-// rows l and l + 32, NB = 8 columns at a time (more columns: further passes
-// over the items; 8 keeps the kernel at 80 registers, 3 CTAs per SM).  Per item, a K-chunk of B (times the item's coefficient) is
+// rows l and l + 32, NB columns at a time (more columns: further passes over
+// the items).  Per item, a K-chunk of B (times the item's coefficient) is
 // staged in the warp's own shared slice; A is read straight from global
 // memory, four K-steps of loads in flight, each lane its two rows.  No
 // block-wide barrier: a CTA's 8 warps run 8 independent groups, so the
@@ -460,16 +460,18 @@ __device__ __forceinline__ void gwarp_panel(const GGroup& G, const GItem* __rest
           // stay far inside 32 bits: K-chunks of at most 32 columns)
           const float* p0 = a0 + (int64_t)k0 * astep;
           const float* p1 = a1 + (int64_t)k0 * astep;
+          // K-steps of A loads in flight (fewer for wide panels: registers)
+          constexpr int UK = NB >= 32 ? 2 : 4;
           int kk = 0;
-          for (; kk + 4 <= kt; kk += 4) {
-            float x0[4], x1[4];
+          for (; kk + UK <= kt; kk += UK) {
+            float x0[UK], x1[UK];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < UK; ++u) {
               x0[u] = v0 ? p0[(kk + u) * astep] : 0.f;
               x1[u] = v1 ? p1[(kk + u) * astep] : 0.f;
             }
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < UK; ++u) {
 #pragma unroll
               for (int q = 0; q < NB / 4; ++q) {
                 const float4 b = *reinterpret_cast<const float4*>(Bs + (kk + u) * LDB + 4 * q);
@@ -510,14 +512,17 @@ __device__ __forceinline__ void gwarp_panel(const GGroup& G, const GItem* __rest
   }
 }
 
-__global__ void __launch_bounds__(NT, 3) k_gwarp(const GGroup* __restrict__ groups,
-                                                 const GItem* __restrict__ items,
-                                                 float* const* __restrict__ tab,
-                                                 const int* const* __restrict__ rtab, int P,
-                                                 int gbeg, int gend,
-                                                 const double* __restrict__ coefs,
-                                                 double* __restrict__ flops, int* err) {
-  __shared__ __align__(16) float bsm[NT / 32][32 * 12];   // KCH x (NB + 4), NB = 8
+// NB output columns per pass: 8 (80 registers, 3 CTAs per SM) or 32 (one
+// pass for the sketch width, 2 CTAs per SM)
+template <int NB, int MINB>
+__global__ void __launch_bounds__(NT, MINB) k_gwarp(const GGroup* __restrict__ groups,
+                                                    const GItem* __restrict__ items,
+                                                    float* const* __restrict__ tab,
+                                                    const int* const* __restrict__ rtab, int P,
+                                                    int gbeg, int gend,
+                                                    const double* __restrict__ coefs,
+                                                    double* __restrict__ flops, int* err) {
+  __shared__ __align__(16) float bsm[NT / 32][32 * (NB + 4)];   // KCH x (NB + 4) per warp
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int g = gbeg + blockIdx.x * (NT / 32) + warp;
   const int p = blockIdx.y;
@@ -534,7 +539,7 @@ __global__ void __launch_bounds__(NT, 3) k_gwarp(const GGroup* __restrict__ grou
   }
   C += G.coff;
   long long fl = 0;
-  gwarp_panel<8>(G, items, tab, rtab, P, p, m, n, C, coefs, bsm[warp], fl);
+  gwarp_panel<NB>(G, items, tab, rtab, P, p, m, n, C, coefs, bsm[warp], fl);
   if (flops && lane == 0 && fl > 0) atomicAdd(flops, (double)fl);
 }
 
@@ -897,7 +902,8 @@ void launch_ggemm(const Plan& pl, int gbeg, int gend, T* const* d_tab, const int
                   int variant, int* d_err, int nwide) {
   int ng = gend - gbeg;
   if (ng <= 0 || P <= 0) return;
-  if ((variant == 2 || variant == 3) && nwide > 0 && sizeof(T) == 4 && !tag_is_dot(tag)) {
+  if ((variant == 2 || variant == 3 || variant == 4) && nwide > 0 && sizeof(T) == 4 &&
+      !tag_is_dot(tag)) {
     // the stage's wide groups (64-column outputs: dense products) in the
     // staged CTA kernel (shape 2) or on the tensor cores (shape 3), the rest
     // one warp per group
@@ -907,7 +913,8 @@ void launch_ggemm(const Plan& pl, int gbeg, int gend, T* const* d_tab, const int
                       d_err);
     else
       launch_ggemm<T>(pl, gbeg, gbeg + w, d_tab, d_rtab, P, d_coefs, st, d_fl, tag, 0, d_err, 0);
-    launch_ggemm<T>(pl, gbeg + w, gend, d_tab, d_rtab, P, d_coefs, st, d_fl, tag, 2, d_err, 0);
+    launch_ggemm<T>(pl, gbeg + w, gend, d_tab, d_rtab, P, d_coefs, st, d_fl, tag,
+                    variant == 4 ? 4 : 2, d_err, 0);
     return;
   }
   if (variant == 3) variant = 2;   // no wide groups: shape 3 is shape 2
@@ -924,16 +931,21 @@ void launch_ggemm(const Plan& pl, int gbeg, int gend, T* const* d_tab, const int
     // kernels; for float it gives the staged kernel 3 CTAs per SM and 80
     // registers (no spills) instead of 4 CTAs and 64 registers, for double
     // half the staging per K-step.  Variant 2 (float, non-dot stages) runs
-    // one warp per group (k_gwarp); variant 3 as 2, with the wide groups on
-    // the tensor cores.
+    // one warp per group (k_gwarp, 8 columns per pass); variant 3 as 2, with
+    // the wide groups on the tensor cores; variant 4 as 2 with 32 columns per
+    // pass.
     const bool warp_dot = (tag == TAG_M || (sizeof(T) == 4 && (tag == TAG_S || tag == TAG_P)));
     if (sizeof(T) == 4 && (tag == TAG_G || tag == TAG_G2 || tag == TAG_H)) {
       k_gram_ff<<<grid, NT, 0, st>>>(gr, it, (float* const*)d_tab, d_rtab, P, gbeg + g0, d_fl);
-    } else if (variant == 2 && sizeof(T) == 4 && d_err && !tag_is_dot(tag)) {
+    } else if ((variant == 2 || variant == 4) && sizeof(T) == 4 && d_err && !tag_is_dot(tag)) {
       const int cnt = std::min(maxg, ng - g0);
       dim3 gw((cnt + NT / 32 - 1) / (NT / 32), P);
-      k_gwarp<<<gw, NT, 0, st>>>(gr, it, (float* const*)d_tab, d_rtab, P, gbeg + g0,
-                                 gbeg + g0 + cnt, d_coefs, d_fl, d_err);
+      if (variant == 4)
+        k_gwarp<32, 2><<<gw, NT, 0, st>>>(gr, it, (float* const*)d_tab, d_rtab, P, gbeg + g0,
+                                          gbeg + g0 + cnt, d_coefs, d_fl, d_err);
+      else
+        k_gwarp<8, 3><<<gw, NT, 0, st>>>(gr, it, (float* const*)d_tab, d_rtab, P, gbeg + g0,
+                                         gbeg + g0 + cnt, d_coefs, d_fl, d_err);
     } else if (tag_is_dot(tag) && (warp_dot != (variant == 1))) {
       const int cnt = std::min(maxg, ng - g0);
       dim3 gw((cnt + NT / 32 - 1) / (NT / 32), P);
