@@ -81,7 +81,7 @@ typedef struct {
   int32_t rank_cap;      /* 1..48; 0 selects the default (32) */
   int32_t flags;         /* ACR_FLAG_* bits */
   int32_t gemm_variant[16]; /* kernel shape per setup GEMM stage (index = the stage numbering of
-                               acr_profile.stage_ms), 0..4 (acr_autotune_gemm); all 0 is the
+                               acr_profile.stage_ms), 0..5 (acr_autotune_gemm); all 0 is the
                                default shape set; other values read as 0 */
 } acr_options;
 
@@ -215,10 +215,11 @@ acr_status acr_autotune_leaf(const acr_grid* grid, const double* coef, const acr
  * non-inner-product stages): one warp per group, groups with 64-column
  * outputs on the shape-0 kernel; shape 3: as 2 with those groups on the
  * tcgen05 tensor cores (split-TF32 operands); shape 4: as 2 with 32 output
- * columns per pass instead of 8.  variant_out (host, 16 int32) receives the
- * table to put in acr_options.gemm_variant; stage_ms_out (host, 80 doubles,
- * may be NULL) the measured stage times, shape 0, 1, 2, 3, then 4.
- * Errors: as acr_setup. */
+ * columns per pass instead of 8; shape 5 (float factors, inner-product
+ * stages): 8 x 8 output tiles per warp pass instead of 4 x 8.  variant_out
+ * (host, 16 int32) receives the table to put in acr_options.gemm_variant;
+ * stage_ms_out (host, 96 doubles, may be NULL) the measured stage times,
+ * shape 0 to shape 5.  Errors: as acr_setup. */
 acr_status acr_autotune_gemm(const acr_grid* grid, const double* coef, const acr_options* opt,
                              int32_t* variant_out, double* stage_ms_out, cudaStream_t stream);
 

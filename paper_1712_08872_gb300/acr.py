@@ -242,17 +242,17 @@ def acr_kappa_gradient(n, kappa, lam, u, grad, stream=None):
 
 
 def acr_autotune_gemm(n, coef, eps, eta, leaf, precision, rank_cap, stream=None):
-    """Per-stage kernel shapes of the setup GEMMs by five profiled setups.
+    """Per-stage kernel shapes of the setup GEMMs by six profiled setups.
     Returns (table of 16 ints for gemm_variant, then the stage ms of shapes
-    0 to 4, one list each)."""
+    0 to 5, one list each)."""
     N = n ** 3
     opt = _options(eps, eta, leaf, precision, rank_cap, 0)
     var = (ctypes.c_int32 * 16)()
-    ms = (ctypes.c_double * 80)()
+    ms = (ctypes.c_double * 96)()
     _check(load_library().acr_autotune_gemm(ctypes.byref(_grid(n)), _dev(coef, 7 * N, "coef"),
                                              ctypes.byref(opt), var, ms, _stream(stream)),
            "acr_autotune_gemm")
-    return (list(var),) + tuple(list(ms[16 * v:16 * v + 16]) for v in range(5))
+    return (list(var),) + tuple(list(ms[16 * v:16 * v + 16]) for v in range(6))
 
 
 def acr_setup(n, coef, eps, eta, leaf, precision=ACR_FP64, rank_cap=0, stream=None, flags=0,

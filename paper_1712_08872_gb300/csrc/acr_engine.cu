@@ -214,7 +214,7 @@ class Engine : public EngineBase {
       : eps(eps_), eta(eta_), leaf(leaf_), kc(kc_), bf16(bf16_ && std::is_same<T, float>::value),
         count(count_) {
     for (int t = 0; t < 16; ++t)
-      gemm_variant[t] = variants && variants[t] >= 0 && variants[t] <= 4 ? variants[t] : 0;
+      gemm_variant[t] = variants && variants[t] >= 0 && variants[t] <= 5 ? variants[t] : 0;
     profiling = (flags_ & ACR_FLAG_PROFILE) != 0;
     n = n_;
     n2 = n * n;
@@ -2425,7 +2425,7 @@ void acr_destroy(acr_handle* h) {
 acr_status acr_autotune_gemm(const acr_grid* grid, const double* coef, const acr_options* opt,
                              int32_t* variant_out, double* stage_ms_out, cudaStream_t stream) {
   if (!grid_ok(grid) || !coef || !opt || !variant_out) return ACR_ERR_INVALID_ARG;
-  constexpr int NV = 5;
+  constexpr int NV = 6;
   double ms[NV][16] = {};
   for (int v = 0; v < NV; ++v) {
     acr_options o = *opt;

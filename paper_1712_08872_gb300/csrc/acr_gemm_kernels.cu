@@ -679,8 +679,10 @@ __global__ void __launch_bounds__(NT) k_gdot(const GGroup* __restrict__ groups,
 // groups (U^T V, Z^T Omega, X^T Q): eight groups per CTA, each warp walks
 // its group's output in 4 x 8 tiles with lanes striding the contraction;
 // no shared memory, no barriers.
-template <typename T, typename Acc>
-__global__ void __launch_bounds__(NT, sizeof(Acc) == 4 ? 4 : 1) k_gdot_warp(const GGroup* __restrict__ groups,
+// TM output rows per tile (4, or 8: one pass over the items covers ranks up
+// to 8 and every sketch column is generated once per row tile)
+template <typename T, typename Acc, int TM>
+__global__ void __launch_bounds__(NT, sizeof(Acc) == 4 ? (TM == 4 ? 4 : 2) : 1) k_gdot_warp(const GGroup* __restrict__ groups,
                                                   const GItem* __restrict__ items,
                                                   T* const* __restrict__ tab,
                                                   const int* const* __restrict__ rtab, int P,
@@ -700,11 +702,11 @@ __global__ void __launch_bounds__(NT, sizeof(Acc) == 4 ? 4 : 1) k_gdot_warp(cons
   C += G.coff;
   const Acc beta = G.beta >= 0 ? (Acc)coefs[G.beta] : Acc(0);
   long long fl = 0;
-  for (int i0 = 0; i0 < m; i0 += 4) {
+  for (int i0 = 0; i0 < m; i0 += TM) {
     for (int j0 = 0; j0 < n; j0 += 8) {
-      Acc acc[4][8];
+      Acc acc[TM][8];
 #pragma unroll
-      for (int r = 0; r < 4; ++r)
+      for (int r = 0; r < TM; ++r)
 #pragma unroll
         for (int c = 0; c < 8; ++c) acc[r][c] = Acc(0);
       for (int it = G.ib; it < G.ie; ++it) {
@@ -726,13 +728,13 @@ __global__ void __launch_bounds__(NT, sizeof(Acc) == 4 ? 4 : 1) k_gdot_warp(cons
         if (k <= 0 || rows <= 0) continue;
         if (i0 == 0 && j0 == 0) fl += 2LL * rows * n * k;
         const Acc cf = (Acc)coefs[I.coef];
-        const T* ar[4];
+        const T* ar[TM];
 #pragma unroll
-        for (int r = 0; r < 4; ++r) ar[r] = (i0 + r < rows) ? A + (int64_t)(i0 + r) * I.lda : nullptr;
+        for (int r = 0; r < TM; ++r) ar[r] = (i0 + r < rows) ? A + (int64_t)(i0 + r) * I.lda : nullptr;
         for (int l = lane; l < k; l += 32) {
-          Acc av[4], bv[8];
+          Acc av[TM], bv[8];
 #pragma unroll
-          for (int r = 0; r < 4; ++r) av[r] = ar[r] ? cf * (Acc)ar[r][l] : Acc(0);
+          for (int r = 0; r < TM; ++r) av[r] = ar[r] ? cf * (Acc)ar[r][l] : Acc(0);
           if (bo) {
             const uint32_t row = (uint32_t)(I.omega_row0 + l);
 #pragma unroll
@@ -747,33 +749,37 @@ __global__ void __launch_bounds__(NT, sizeof(Acc) == 4 ? 4 : 1) k_gdot_warp(cons
               bv[c] = (j0 + c < n) ? (Acc)B[l + (int64_t)(j0 + c) * I.ldb] : Acc(0);
           }
 #pragma unroll
-          for (int r = 0; r < 4; ++r)
+          for (int r = 0; r < TM; ++r)
 #pragma unroll
             for (int c = 0; c < 8; ++c) acc[r][c] += av[r] * bv[c];
         }
       }
-      // transposing reduction: 32 sums over the 32 lanes, lane e ending with
-      // element e (recursive halving, 31 shuffles instead of 32 x 5)
-      Acc v[32];
+      // transposing reduction per 32 tile elements (element e = row e % TM,
+      // column e / TM): 32 sums over the 32 lanes, lane e ending with element
+      // e (recursive halving, 31 shuffles instead of 32 x 5)
 #pragma unroll
-      for (int e = 0; e < 32; ++e) v[e] = acc[e & 3][e >> 2];
+      for (int h = 0; h < TM / 4; ++h) {
+        Acc v[32];
 #pragma unroll
-      for (int sft = 16; sft > 0; sft >>= 1) {
-        const bool up = (lane & sft) != 0;
+        for (int e = 0; e < 32; ++e) v[e] = acc[(32 * h + e) % TM][(32 * h + e) / TM];
 #pragma unroll
-        for (int e = 0; e < sft; ++e) {
-          const Acc keep = up ? v[e + sft] : v[e];
-          const Acc send = up ? v[e] : v[e + sft];
-          v[e] = keep + __shfl_xor_sync(0xffffffffu, send, sft);
+        for (int sft = 16; sft > 0; sft >>= 1) {
+          const bool up = (lane & sft) != 0;
+#pragma unroll
+          for (int e = 0; e < sft; ++e) {
+            const Acc keep = up ? v[e + sft] : v[e];
+            const Acc send = up ? v[e] : v[e + sft];
+            v[e] = keep + __shfl_xor_sync(0xffffffffu, send, sft);
+          }
         }
-      }
-      const Acc mine = v[0];
-      const int i = i0 + (lane & 3), j = j0 + (lane >> 2);
-      if (i < m && j < n) {
-        T* c = C + i + (int64_t)j * G.ldc;
-        Acc v = mine;
-        if (G.beta >= 0) v += beta * (Acc)(*c);
-        *c = (T)v;
+        const int e = 32 * h + lane;
+        const int i = i0 + e % TM, j = j0 + e / TM;
+        if (i < m && j < n) {
+          T* c = C + i + (int64_t)j * G.ldc;
+          Acc w = v[0];
+          if (G.beta >= 0) w += beta * (Acc)(*c);
+          *c = (T)w;
+        }
       }
     }
   }
@@ -933,7 +939,7 @@ void launch_ggemm(const Plan& pl, int gbeg, int gend, T* const* d_tab, const int
     // half the staging per K-step.  Variant 2 (float, non-dot stages) runs
     // one warp per group (k_gwarp, 8 columns per pass); variant 3 as 2, with
     // the wide groups on the tensor cores; variant 4 as 2 with 32 columns per
-    // pass.
+    // pass; variant 5 (float, inner-product stages) 8 x 8 warp tiles.
     const bool warp_dot = (tag == TAG_M || (sizeof(T) == 4 && (tag == TAG_S || tag == TAG_P)));
     if (sizeof(T) == 4 && (tag == TAG_G || tag == TAG_G2 || tag == TAG_H)) {
       k_gram_ff<<<grid, NT, 0, st>>>(gr, it, (float* const*)d_tab, d_rtab, P, gbeg + g0, d_fl);
@@ -946,11 +952,16 @@ void launch_ggemm(const Plan& pl, int gbeg, int gend, T* const* d_tab, const int
       else
         k_gwarp<8, 3><<<gw, NT, 0, st>>>(gr, it, (float* const*)d_tab, d_rtab, P, gbeg + g0,
                                          gbeg + g0 + cnt, d_coefs, d_fl, d_err);
+    } else if (tag_is_dot(tag) && variant == 5 && sizeof(T) == 4) {
+      const int cnt = std::min(maxg, ng - g0);
+      dim3 gw((cnt + NT / 32 - 1) / (NT / 32), P);
+      k_gdot_warp<T, Acc, 8><<<gw, NT, 0, st>>>(gr, it, d_tab, d_rtab, P, gbeg + g0,
+                                                gbeg + g0 + cnt, d_coefs, d_fl);
     } else if (tag_is_dot(tag) && (warp_dot != (variant == 1))) {
       const int cnt = std::min(maxg, ng - g0);
       dim3 gw((cnt + NT / 32 - 1) / (NT / 32), P);
-      k_gdot_warp<T, Acc><<<gw, NT, 0, st>>>(gr, it, d_tab, d_rtab, P, gbeg + g0, gbeg + g0 + cnt,
-                                             d_coefs, d_fl);
+      k_gdot_warp<T, Acc, 4><<<gw, NT, 0, st>>>(gr, it, d_tab, d_rtab, P, gbeg + g0,
+                                                gbeg + g0 + cnt, d_coefs, d_fl);
     } else if (tag_is_dot(tag))
       k_gdot<T, Acc><<<grid, NT, 0, st>>>(gr, it, d_tab, d_rtab, P, gbeg + g0, d_coefs, d_fl);
     else if (variant == 1 && sizeof(Acc) == 4)

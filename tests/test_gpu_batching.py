@@ -199,27 +199,28 @@ def test_32_rhs_tensor_core_apply(acr, parity_log, prec, trans):
 
 
 def test_gemm_shape_autotuner(acr, parity_log):
-    """acr_autotune_gemm times the five kernel-shape sets stage by stage and
+    """acr_autotune_gemm times the six kernel-shape sets stage by stage and
     returns, per stage, the fastest; a setup with the table (the same
     products, other tilings, chunkings and kernels) gives the default
     setup's apply to the FP32 parity bound, and so do tables of all 1s, all
     2s (every non-inner-product stage one warp per group), all 3s (the
-    dense-output groups on the tcgen05 tensor cores) and all 4s (warp per
-    group, 32 columns per pass); the all-2s, -3s and -4s applies also meet
-    the oracle's FP32 bound, element by element too."""
+    dense-output groups on the tcgen05 tensor cores), all 4s (warp per
+    group, 32 columns per pass) and all 5s (8 x 8 inner-product tiles); the
+    all-2s to all-5s applies also meet the oracle's FP32 bound, element by
+    element too."""
     n = 32
     st, coef = _codi(acr, n)
     table, *shape_ms = acr.acr_autotune_gemm(n, coef, 1e-2, 2.0, 64, acr.ACR_FP32, 24)
-    assert len(shape_ms) == 5
-    assert all(v in (0, 1, 2, 3, 4) for v in table)
+    assert len(shape_ms) == 6
+    assert all(v in range(6) for v in table)
     assert all(sum(ms) > 0 for ms in shape_ms)
     for t in range(13):
-        ms = [shape_ms[v][t] for v in range(5)]
-        assert table[t] == min(range(5), key=lambda v: (ms[v], v))
+        ms = [shape_ms[v][t] for v in range(6)]
+        assert table[t] == min(range(6), key=lambda v: (ms[v], v))
     fh = uniform_rhs(n, 9)
     f = T(fh)
     zs = []
-    for var in (None, table, [1] * 16, [2] * 16, [3] * 16, [4] * 16):
+    for var in (None, table, [1] * 16, [2] * 16, [3] * 16, [4] * 16, [5] * 16):
         h = acr.acr_setup(n, coef, 1e-2, 2.0, 64, acr.ACR_FP32, 24, gemm_variant=var)
         z = torch.empty_like(f)
         acr.acr_apply(h, f, z)
@@ -231,12 +232,12 @@ def test_gemm_shape_autotuner(acr, parity_log):
     zo = cr_apply(F, fh)
     z32 = cr_apply(F32, fh)
     tol = max(1e-5, 5 * rel(z32, zo))
-    e_or = [rel(zs[v], zo) for v in (3, 4, 5)]
+    e_or = [rel(zs[v], zo) for v in (3, 4, 5, 6)]
     scale = np.abs(zo).max()
-    emax = [np.abs(zs[v] - zo).max() / scale for v in (3, 4, 5)]
+    emax = [np.abs(zs[v] - zo).max() / scale for v in (3, 4, 5, 6)]
     tol_max = max(1e-5, 5 * np.abs(z32 - zo).max() / scale)
     parity_log(test="gemm_shapes", n=n, table=table[:13], err_vs_default=errs,
-               err2_vs_oracle_shapes234=e_or, errmax_vs_oracle_shapes234=emax, tol=tol,
+               err2_vs_oracle_shapes2345=e_or, errmax_vs_oracle_shapes2345=emax, tol=tol,
                tol_max=tol_max)
     assert max(errs) <= 1e-5, errs
     assert max(e_or) <= tol, (e_or, tol)
