@@ -375,10 +375,11 @@ class Handle:
     """Owning wrapper of an acr_setup handle."""
 
     def __init__(self, n, coef, eps, eta, leaf, precision=ACR_FP64, rank_cap=0, stream=None,
-                 flags=0):
+                 flags=0, gemm_variant=None):
         self.n = n
         self.h = None
-        self.h = acr_setup(n, coef, eps, eta, leaf, precision, rank_cap, stream, flags)
+        self.h = acr_setup(n, coef, eps, eta, leaf, precision, rank_cap, stream, flags,
+                           gemm_variant)
 
     def apply(self, r, z, stream=None, nrhs=1):
         acr_apply(self.h, r, z, nrhs, stream)

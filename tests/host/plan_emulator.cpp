@@ -393,6 +393,25 @@ OpDesc product_op(int cnode, int crole, int anode, int arole, int bnode, int bro
 
 }  // namespace
 
+// Structural invariants of a built plan: every GEMM stage's first nwide
+// groups have a static 64-column output and no later group does; max_p is
+// the widest target sketch.  Returns the number of violations.
+int check_plan_order(const Plan& pl) {
+  int bad = 0;
+  for (const Stage& sg : pl.stages) {
+    if (sg.kind != ST_GEMM) continue;
+    for (int g = sg.beg; g < sg.end; ++g) {
+      const GGroup& G = pl.groups[g];
+      const bool wide = G.n_rb < 0 && G.n_st >= 64;
+      if (wide != (g < sg.beg + sg.nwide)) ++bad;
+    }
+  }
+  int mp = 0;
+  for (const TInfo& ti : pl.targets) mp = std::max(mp, ti.p);
+  if (mp != pl.max_p) ++bad;
+  return bad;
+}
+
 int main(int argc, char** argv) {
   const int n = argc > 1 ? std::atoi(argv[1]) : 16;
   const double eta = argc > 2 ? std::atof(argv[2]) : 2.0;
@@ -459,6 +478,9 @@ int main(int argc, char** argv) {
     execute(pm, {&X, &T2}, 1, eps);
     allow_cap = false;
     report("merged plans = separate plans", rel(to_dense(T2), to_dense(T1)), 1e-13);
+    const int bad = check_plan_order(pl) + check_plan_order(pa) + check_plan_order(pb) +
+                    check_plan_order(pm);
+    report("stage order: wide groups first", (double)bad, 0.0);
     if (pm.stages.size() >= pa.stages.size() + pb.stages.size()) {
       std::printf("merging did not share stages\n");
       fail = true;

@@ -1,9 +1,10 @@
 """Host logic: the plan builder's formatted operations, executed on the CPU
 in FP64 by tests/host/plan_emulator.cpp (which links the product's
 acr_plan.cpp and acr_structure.cpp), reproduce exact results on operands
-whose result fits the block structure, merged plans equal separate ones,
-and the apply's per-chunk index lists reproduce H x and H^T x.  No GPU
-involved."""
+whose result fits the block structure, merged plans equal separate ones
+(and every plan keeps its GEMM stages' 64-column-output groups first, as
+the launcher's kernel split assumes), and the apply's per-chunk index lists
+reproduce H x and H^T x.  No GPU involved."""
 import os
 import shutil
 import subprocess
@@ -33,4 +34,4 @@ def test_plans_reproduce_exact_operations(emulator, n, eta, leaf):
     r = subprocess.run([emulator, str(n), str(eta), str(leaf)], capture_output=True, text=True,
                        timeout=300)
     assert r.returncode == 0, r.stdout + r.stderr
-    assert r.stdout.count(" ok") == 7, r.stdout
+    assert r.stdout.count(" ok") == 8, r.stdout
