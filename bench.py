@@ -250,8 +250,10 @@ def profile_setup(args):
         table = [int(v) for v in args.gemm_table.split(",")] + [0] * 16
         table = table[:16]
     elif args.tuned:
-        table = acr.acr_autotune_gemm(n, coef, spec["eps"], 2.0, spec["leaf"], prec,
-                                      args.rank_cap, stream)[0]
+        table, *shape_ms = acr.acr_autotune_gemm(n, coef, spec["eps"], 2.0, spec["leaf"], prec,
+                                                 args.rank_cap, stream)
+        for v, ms in enumerate(shape_ms):
+            print("  shape %d stage ms:" % v, [round(x, 1) for x in ms[:13]])
     if table is not None:
         print("kernel shapes per stage:", ",".join(str(v) for v in table[:13]))
     h = acr.acr_setup(n, coef, spec["eps"], 2.0, spec["leaf"], prec, args.rank_cap, stream,
