@@ -57,10 +57,15 @@ typedef enum {
  * multiplied in float with float accumulation.  BF16: the setup runs exactly
  * as in FP32; when it ends every stored factor (dense leaves, U, V) is
  * rounded to bfloat16 (round to nearest even), halving the factor memory and
- * the bytes an apply reads; the apply multiplies in float.  In every form
- * the dense leaf inverses, the small recompression cores and the Krylov
- * iteration are FP64.  (Reduced-precision storage is not in the paper, whose
- * H-arithmetic is double precision throughout, Sec. 5.) */
+ * the bytes an apply reads; the apply multiplies in float.  The Krylov
+ * iteration is FP64 in every form, and so are the Grams that decide ranks
+ * (FP64-accurate float-float sums in the float forms).  The dense leaf
+ * inverses and the small recompression cores are FP64 in the FP64 form; in
+ * the float forms the leaf inverses are float eliminations refined to float
+ * accuracy (FP64 elimination when refinement cannot get there), the Jacobi
+ * cores run in float-float and the pivoted Cholesky in FP64.
+ * (Reduced-precision storage is not in the paper, whose H-arithmetic is
+ * double precision throughout, Sec. 5.) */
 typedef enum { ACR_FP64 = 0, ACR_FP32 = 1, ACR_BF16 = 2 } acr_precision;
 
 typedef enum { ACR_PCG = 0, ACR_GMRES = 1 } acr_krylov;
@@ -129,8 +134,8 @@ typedef struct {
 typedef struct {
   acr_kernel_stat gemm;      /* grouped small GEMMs (k_ggemm) */
   acr_kernel_stat orth;      /* pivoted-Cholesky cores (k_pchol), FP64 */
-  acr_kernel_stat eig;       /* Jacobi recompression cores (k_eig), FP64 */
-  acr_kernel_stat leaf_inv;  /* dense leaf inverses (k_leaf_inv), FP64 */
+  acr_kernel_stat eig;       /* Jacobi recompression cores (k_eig; float-float for float factors) */
+  acr_kernel_stat leaf_inv;  /* dense leaf inverses (k_leaf_inv; refined float for float factors) */
   acr_kernel_stat other;     /* conversion, scaling */
   /* grouped-GEMM time and counted flops per plan stage: 0 inner products
    * U^T V of phase 1, 1 term factors (H-matrix x block products, dense

@@ -21,11 +21,12 @@
 //     the sum in factored form and recompresses it: a sketch Y = S Omega of
 //     the stacked sum S (exact range when the stacked rank fits the sketch),
 //     Q = orth(Y) by pivoted Cholesky of Y^T Y, B^T = S^T Q, the small core
-//     (B^T)^T B^T = W diag(sigma^2) W^T by FP64 Jacobi, rank k = #{sigma_i >
+//     (B^T)^T B^T = W diag(sigma^2) W^T by Jacobi (FP64, or float-float for
+//     float factors), rank k = #{sigma_i >
 //     eps sigma_1}, and U = Q W_k, V = B^T W_k (phase 2).
 //
 // Every step is a batch of grouped small GEMMs (GGroup / GItem) or a batch
-// of small FP64 cores (TInfo), all indexed through per-plane pointer
+// of small cores (TInfo: pivoted Cholesky, Jacobi), all indexed through per-plane pointer
 // tables, so one plan serves every plane of a CR level.
 #pragma once
 #include <cstdint>
