@@ -49,7 +49,7 @@ typedef enum {
   ACR_ERR_RANK_CAP = 5,      /* a truncated block needed more than the rank cap */
   ACR_ERR_NOT_CONVERGED = 6, /* Krylov hit maxit above rtol */
   ACR_ERR_TIMEOUT = 7,       /* a bounded device wait ran out */
-  ACR_ERR_UNSUPPORTED = 8    /* valid request this build does not handle (e.g. unbalanced cluster tree) */
+  ACR_ERR_UNSUPPORTED = 8    /* valid request the library does not handle (e.g. unbalanced cluster tree) */
 } acr_status;
 
 /* Arithmetic form of the H-matrix factors and of the setup / apply
